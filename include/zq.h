@@ -1,0 +1,158 @@
+/*
+ * zq.h -- C ABI of libzq: hierarchical orthogonal-complement products
+ * Q~v and Q~^T w for rigid bodies on a GB300 (sm_103a).
+ *
+ * Method: F. Fang, J. Huang, G. Huber, J. A. McCammon, B. Zhang,
+ * "Hierarchical Orthogonal Matrix Generation and Matrix-Vector
+ * Multiplications in Rigid Body Simulations", arXiv 1708.08427.
+ *
+ * A rigid body of n beads at positions r_i has the 6 x 3n Z-matrix
+ * Z = [I ... I; A_1 ... A_n], A_i f = r_i x f (Sec. 1, Eq. 1.2).  Q~ is the
+ * (3n-6) x 3n matrix whose rows are an orthonormal basis of the orthogonal
+ * complement of the row space of Z (Problem Statement, Sec. 1).  For m
+ * bodies Q~ = diag(Q~^1, ..., Q~^m) (Sec. 1).  Q~ is never formed: a bead
+ * tree (Sec. 2.1) carries one small orthogonal transform per node (Sec. 3,
+ * Eq. 3.5), applied upward for Q~v (Algorithm 2, Eqs. 4.2-4.3) and
+ * downward for Q~^T w (Algorithm 3, Theorem 4.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Bodies.  m bodies; body j owns beads [off[j], off[j+1]) of the bead
+ *   arrays, off[0] = 0, off[m] = N, every body has at least 3 beads.
+ *   N <= 700,000,000.  The offsets are a HOST array (the launch plan
+ *   depends on them).
+ * Coordinates.  Three DEVICE arrays x, y, z of N doubles (structure of
+ *   arrays), in the caller's bead order.
+ * Bead vectors (inputs of Q~, outputs of Q~^T).  Mathematically the
+ *   paper's ordering f = [f_1; ...; f_N] (component 3i + a = axis a of
+ *   bead i).  Physically three planes: axis a of bead i of column c sits at
+ *   v[c*ldv + a*N + i], ldv >= 3N.  DEVICE memory.
+ * Residue vectors (outputs of Q~, inputs of Q~^T).  R = 3N - 6m values per
+ *   column: body j's residues start at sum_{i<j} (3 n_i - 6); inside a body
+ *   the nodes are ordered by split position (the node whose left subtree
+ *   ends at sorted bead g), and inside a node by the rows 4..k of its
+ *   transform G.  Column c starts at out[c*ldo], ldo >= R.  DEVICE memory.
+ * Tree.  Sec. 2.1 with the readings fixed by the oracle: the root box is
+ *   each body's bounding box normalised to side 1; each coordinate is
+ *   quantised to 21 bits (q = min(floor((p-lo)/(hi-lo) * 2^21), 2^21-1),
+ *   q = 0 when hi == lo); bisection takes z, then y, then x at each octree
+ *   level, most significant bit first; empty boxes are pruned; beads in
+ *   the same 21-bit cell are separated by the bits of their body-local
+ *   index; leaves are single beads.  Left child = lower half.
+ * Precision.  Transforms are always built in FP64 (Eq. 3.5 LQ by
+ *   Householder reflections, LAPACK dgeqrf convention; Case I by the closed
+ *   form of Eqs. 3.9-3.10); an FP32 copy is kept for the FP32 applies.
+ * Streams.  Every call is asynchronous on the context's stream unless noted.
+ * Ownership.  The caller owns all coordinate, vector and offset buffers;
+ *   the context owns the tree, the transforms and its scratch.  Apply calls
+ *   never allocate.
+ * Errors.  No exceptions cross the ABI.  Argument errors return at once;
+ *   errors found on the device (non-finite coordinates, coincident beads)
+ *   are recorded and returned by zq_sync.
+ */
+#ifndef ZQ_H
+#define ZQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct zq_ctx zq_ctx;
+
+typedef enum {
+  ZQ_OK = 0,
+  ZQ_EINVAL = 1,        /* bad argument (NULL, sizes, n_j < 3, bad offsets) */
+  ZQ_ENOMEM = 2,        /* device allocation failed */
+  ZQ_ECUDA = 3,         /* a CUDA call failed; the context is unusable */
+  ZQ_ESTATE = 4,        /* called out of order (apply before build) */
+  ZQ_ENONFINITE = 5,    /* a coordinate is NaN or infinite (from zq_sync) */
+  ZQ_WDEGENERATE = 6    /* warning: two beads of a body coincide; the result
+                           is orthonormal but Q~ misses a direction */
+} zq_status;
+
+typedef enum { ZQ_FP64 = 0, ZQ_FP32 = 1 } zq_prec;
+
+/* Human-readable name of a status code (static storage). */
+const char *zq_status_string(zq_status s);
+
+/* Create a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream).  The stream
+ * must outlive the context. */
+zq_status zq_create(zq_ctx **ctx, int device, void *cuda_stream);
+
+/* Release all device memory of the context.  Synchronises its stream. */
+zq_status zq_destroy(zq_ctx *ctx);
+
+/* Tree of m bodies (Sec. 2.1; readings above).  off: HOST, m+1 entries.
+ * x, y, z: DEVICE, N doubles each.  tile_beads: beads per thread-block
+ * tile of the sweeps (performance only, results do not depend on it;
+ * 0 = default 2048; 64 <= tile_beads <= 4096).  Allocates the context's
+ * buffers on the first call and whenever m or N grows; a later call with
+ * the same sizes reuses them.  Asynchronous; bad coordinates are reported
+ * by zq_sync. */
+zq_status zq_build_tree_batched(zq_ctx *ctx, int64_t m, const int64_t *off, const double *x,
+                                const double *y, const double *z, int32_t tile_beads);
+
+/* Single-body form: m = 1, off = {0, n}. */
+zq_status zq_build_tree(zq_ctx *ctx, int64_t n, const double *x, const double *y,
+                        const double *z, int32_t tile_beads);
+
+/* Node transforms in FP64 from the coordinates (Sec. 3: centroids,
+ * sqrt(n_x/n), sqrt(n_y/n), the LQ of [R22 S22 sqrt(n_x n/n_y) R21] of
+ * Eq. 3.5, Case I closed form Eqs. 3.9-3.10, Case II Eqs. 3.11-3.13).
+ * x, y, z: DEVICE, the same bodies and bead order as the tree (the beads
+ * may have moved: the tree is kept).  Writes both the FP64 and the FP32
+ * copy.  Asynchronous; coincident beads are reported by zq_sync. */
+zq_status zq_build_transforms(zq_ctx *ctx, const double *x, const double *y, const double *z);
+
+/* out = Q~ v for k columns (upward pass, Algorithm 2, Eqs. 4.2-4.3).
+ * prec selects double (ZQ_FP64: v, out are double*) or float (ZQ_FP32:
+ * float*).  v: DEVICE bead-vector planes (ldv >= 3N); out: DEVICE residue
+ * vectors (ldo >= R).  Does not allocate.  ZQ_ESTATE before the first
+ * zq_build_transforms. */
+zq_status zq_apply_Q(zq_ctx *ctx, zq_prec prec, int64_t k, const void *v, int64_t ldv, void *out,
+                     int64_t ldo);
+
+/* out = Q~^T w for k columns (downward pass with a zero root Velocity-set,
+ * Algorithm 3, Theorem 4.3, Eqs. 4.6-4.7).  w: DEVICE residue vectors
+ * (ldw >= R); out: DEVICE bead-vector planes (ldo >= 3N).  Does not
+ * allocate. */
+zq_status zq_apply_QT(zq_ctx *ctx, zq_prec prec, int64_t k, const void *w, int64_t ldw,
+                      void *out, int64_t ldo);
+
+/* Wait for the context's stream; return the first deferred device error
+ * (ZQ_ENONFINITE, ZQ_WDEGENERATE) recorded since the last zq_sync, then
+ * clear it. */
+zq_status zq_sync(zq_ctx *ctx);
+
+/* Sizes of the current tree: N beads, m bodies, R = 3N - 6m residues,
+ * number of internal nodes N - m. */
+zq_status zq_sizes(const zq_ctx *ctx, int64_t *N, int64_t *m, int64_t *R, int64_t *nodes);
+
+/* Tree export (synchronous; HOST arrays), for checking the tree bit by bit.
+ *   perm[N]            sorted position -> bead index (global).
+ * Per internal node id q in [0, N - m) (body j's node with split position
+ * g has id off[j] - j + g):
+ *   left[q], right[q]  child codes: >= 0 internal node id, < 0 a leaf at
+ *                      sorted position -1 - code;
+ *   first[q]           sorted position of the node's first bead;
+ *   count[q]           beads below the node;
+ *   height[q]          1 + the larger child height (leaves: 0);
+ *   roff[q]            residue offset (global).
+ * Any pointer may be NULL to skip that array. */
+zq_status zq_get_tree(zq_ctx *ctx, int32_t *perm, int32_t *left, int32_t *right, int32_t *first,
+                      int32_t *count, int32_t *height, int32_t *roff);
+
+/* FP64 node data export (synchronous; HOST arrays, N - m rows each, NULL
+ * skips): centroid[3*q + a]; T22[6*q + i] packed lower triangle
+ * (L00, L10, L11, L20, L21, L22). */
+zq_status zq_get_nodes(zq_ctx *ctx, double *centroid, double *T22);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZQ_H */

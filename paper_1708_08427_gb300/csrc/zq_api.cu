@@ -1,0 +1,301 @@
+// zq_api.cu -- the C ABI declared in include/zq.h.
+#include <new>
+
+#include "zq_internal.cuh"
+
+using zq::Ctx;
+
+struct zq_ctx {
+  Ctx c;
+};
+
+namespace {
+
+template <typename T>
+zq_status grow(T** p, int64_t count) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  if (cudaMalloc(reinterpret_cast<void**>(p), (size_t)count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    return ZQ_ENOMEM;
+  }
+  return ZQ_OK;
+}
+
+void free_all(Ctx& c) {
+  void* ps[] = {c.off, c.small_d, c.top_d, c.aabb, c.root, c.key, c.skey, c.perm, c.key_tmp,
+                c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height, c.parent,
+                c.flag, c.roff, c.scan_tmp, c.tiles, c.top, c.counters, c.st64, c.rec64, c.rec32,
+                c.x64, c.x32};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  Ctx fresh;
+  fresh.device = c.device;
+  fresh.stream = c.stream;
+  fresh.num_sms = c.num_sms;
+  c = fresh;
+}
+
+#define ZQ_TRY(expr)                  \
+  do {                                \
+    zq_status _s = (expr);            \
+    if (_s != ZQ_OK) return _s;       \
+  } while (0)
+
+zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
+  if (N > c.cap_N || m > c.cap_m) {
+    const int64_t nodes = N;  // >= N - m
+    ZQ_TRY(grow(&c.off, m + 1));
+    ZQ_TRY(grow(&c.small_d, m));
+    ZQ_TRY(grow(&c.top_d, m));
+    ZQ_TRY(grow(&c.aabb, 6 * m));
+    ZQ_TRY(grow(&c.root, m));
+    ZQ_TRY(grow(&c.key, N));
+    ZQ_TRY(grow(&c.skey, N));
+    ZQ_TRY(grow(&c.perm, N));
+    ZQ_TRY(grow(&c.key_tmp, N));
+    ZQ_TRY(grow(&c.perm_tmp, N));
+    ZQ_TRY(grow(&c.lcp, nodes));
+    ZQ_TRY(grow(&c.cl, nodes));
+    ZQ_TRY(grow(&c.cr, nodes));
+    ZQ_TRY(grow(&c.first, nodes));
+    ZQ_TRY(grow(&c.cnt, nodes));
+    ZQ_TRY(grow(&c.height, nodes));
+    ZQ_TRY(grow(&c.parent, nodes));
+    ZQ_TRY(grow(&c.flag, nodes));
+    ZQ_TRY(grow(&c.roff, nodes));
+    ZQ_TRY(grow(&c.scan_tmp, zq::scan_tmp_words(nodes)));
+    ZQ_TRY(grow(&c.tiles, nodes));
+    ZQ_TRY(grow(&c.top, nodes));
+    ZQ_TRY(grow(&c.counters, 4));
+    ZQ_TRY(grow(&c.st64, nodes * zq::kState));
+    ZQ_TRY(grow(&c.rec64, nodes * zq::kRec));
+    ZQ_TRY(grow(&c.rec32, nodes * zq::kRec));
+    ZQ_TRY(grow(&c.x64, nodes * 6));
+    ZQ_TRY(grow(&c.x32, nodes * 6));
+    ZQ_CUDA_TRY(cudaMemsetAsync(c.counters, 0, 4 * sizeof(int32_t), c.stream));
+    c.cap_N = N;
+    c.cap_m = m;
+  }
+  if (hist_words > c.sort_hist_cap) {
+    ZQ_TRY(grow(&c.sort_hist, hist_words));
+    c.sort_hist_cap = hist_words;
+  }
+  return ZQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* zq_status_string(zq_status s) {
+  switch (s) {
+    case ZQ_OK: return "ok";
+    case ZQ_EINVAL: return "invalid argument";
+    case ZQ_ENOMEM: return "device allocation failed";
+    case ZQ_ECUDA: return "CUDA error";
+    case ZQ_ESTATE: return "call out of order";
+    case ZQ_ENONFINITE: return "non-finite coordinate";
+    case ZQ_WDEGENERATE: return "coincident beads (degenerate node)";
+  }
+  return "unknown status";
+}
+
+zq_status zq_create(zq_ctx** ctx, int device, void* cuda_stream) {
+  if (!ctx) return ZQ_EINVAL;
+  *ctx = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return ZQ_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return ZQ_ECUDA;
+  zq_ctx* h = new (std::nothrow) zq_ctx();
+  if (!h) return ZQ_ENOMEM;
+  h->c.device = device;
+  h->c.stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaDeviceGetAttribute(&h->c.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete h;
+    return ZQ_ECUDA;
+  }
+  *ctx = h;
+  return ZQ_OK;
+}
+
+zq_status zq_destroy(zq_ctx* ctx) {
+  if (!ctx) return ZQ_EINVAL;
+  cudaSetDevice(ctx->c.device);
+  cudaStreamSynchronize(ctx->c.stream);
+  free_all(ctx->c);
+  delete ctx;
+  return ZQ_OK;
+}
+
+zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, const double* x,
+                                const double* y, const double* z, int32_t tile_beads) {
+  if (!ctx || !off || !x || !y || !z || m < 1) return ZQ_EINVAL;
+  if (tile_beads == 0) tile_beads = zq::kDefaultTile;
+  if (tile_beads < 64 || tile_beads > zq::kMaxTile) return ZQ_EINVAL;
+  if (off[0] != 0) return ZQ_EINVAL;
+  int64_t max_big = 0;
+  for (int64_t j = 0; j < m; ++j) {
+    const int64_t n = off[j + 1] - off[j];
+    if (n < 3 || n > INT32_MAX) return ZQ_EINVAL;
+    if (n > zq::kSmallSortMax && n > max_big) max_big = n;
+  }
+  const int64_t N = off[m];
+  if (N > 700000000LL) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  const int64_t nblk = (max_big + 4095) / 4096;
+  const int64_t hist_words = 16 * nblk + zq::scan_tmp_words(16 * nblk);
+  ZQ_TRY(ensure_capacity(c, N, m, hist_words));
+  c.N = N;
+  c.m = m;
+  c.nodes = N - m;
+  c.R = 3 * N - 6 * m;
+  c.tile = tile_beads;
+  c.have_tree = false;
+  c.have_xform = false;
+  c.off_h.assign(off, off + m + 1);
+  c.small_bodies.clear();
+  c.big_bodies.clear();
+  c.top_bodies.clear();
+  c.max_small = 0;
+  for (int64_t j = 0; j < m; ++j) {
+    const int64_t n = off[j + 1] - off[j];
+    if (n <= zq::kSmallSortMax) {
+      c.small_bodies.push_back((int32_t)j);
+      if (n > c.max_small) c.max_small = (int32_t)n;
+    } else {
+      c.big_bodies.push_back((int32_t)j);
+    }
+    if (n > c.tile) c.top_bodies.push_back((int32_t)j);
+  }
+  ZQ_CUDA_TRY(cudaMemcpyAsync(c.off, off, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+  if (!c.small_bodies.empty())
+    ZQ_CUDA_TRY(cudaMemcpyAsync(c.small_d, c.small_bodies.data(), c.small_bodies.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, c.stream));
+  if (!c.top_bodies.empty())
+    ZQ_CUDA_TRY(cudaMemcpyAsync(c.top_d, c.top_bodies.data(), c.top_bodies.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, c.stream));
+  // the host vectors are read by the copies above: keep them alive until then
+  ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  ZQ_TRY(zq::launch_tree(c, x, y, z));
+  c.have_tree = true;
+  return ZQ_OK;
+}
+
+zq_status zq_build_tree(zq_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+                        int32_t tile_beads) {
+  const int64_t off[2] = {0, n};
+  return zq_build_tree_batched(ctx, 1, off, x, y, z, tile_beads);
+}
+
+zq_status zq_build_transforms(zq_ctx* ctx, const double* x, const double* y, const double* z) {
+  if (!ctx || !x || !y || !z) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_tree) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  ZQ_TRY(zq::launch_build(c, x, y, z));
+  c.have_xform = true;
+  return ZQ_OK;
+}
+
+zq_status zq_apply_Q(zq_ctx* ctx, zq_prec prec, int64_t k, const void* v, int64_t ldv, void* out,
+                     int64_t ldo) {
+  if (!ctx || !v || !out || k < 1) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_xform) return ZQ_ESTATE;
+  if (ldv < 3 * c.N || ldo < c.R) return ZQ_EINVAL;
+  const size_t es = prec == ZQ_FP64 ? sizeof(double) : sizeof(float);
+  for (int64_t col = 0; col < k; ++col) {
+    const char* vi = static_cast<const char*>(v) + (size_t)col * ldv * es;
+    char* oi = static_cast<char*>(out) + (size_t)col * ldo * es;
+    ZQ_TRY(zq::launch_apply_Q(c, prec, vi, ldv, oi));
+  }
+  return ZQ_OK;
+}
+
+zq_status zq_apply_QT(zq_ctx* ctx, zq_prec prec, int64_t k, const void* w, int64_t ldw, void* out,
+                      int64_t ldo) {
+  if (!ctx || !w || !out || k < 1) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_xform) return ZQ_ESTATE;
+  if (ldw < c.R || ldo < 3 * c.N) return ZQ_EINVAL;
+  const size_t es = prec == ZQ_FP64 ? sizeof(double) : sizeof(float);
+  for (int64_t col = 0; col < k; ++col) {
+    const char* wi = static_cast<const char*>(w) + (size_t)col * ldw * es;
+    char* oi = static_cast<char*>(out) + (size_t)col * ldo * es;
+    ZQ_TRY(zq::launch_apply_QT(c, prec, wi, oi, ldo));
+  }
+  return ZQ_OK;
+}
+
+zq_status zq_sync(zq_ctx* ctx) {
+  if (!ctx) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  ZQ_CUDA_TRY(cudaGetLastError());
+  if (!c.counters) return ZQ_OK;
+  int32_t err = 0;
+  ZQ_CUDA_TRY(cudaMemcpy(&err, c.counters + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemset(c.counters + 2, 0, sizeof(int32_t)));
+  if (err & zq::kErrNonFinite) return ZQ_ENONFINITE;
+  if (err & zq::kErrDegenerate) return ZQ_WDEGENERATE;
+  return ZQ_OK;
+}
+
+zq_status zq_sizes(const zq_ctx* ctx, int64_t* N, int64_t* m, int64_t* R, int64_t* nodes) {
+  if (!ctx) return ZQ_EINVAL;
+  const Ctx& c = ctx->c;
+  if (!c.have_tree) return ZQ_ESTATE;
+  if (N) *N = c.N;
+  if (m) *m = c.m;
+  if (R) *R = c.R;
+  if (nodes) *nodes = c.nodes;
+  return ZQ_OK;
+}
+
+zq_status zq_get_tree(zq_ctx* ctx, int32_t* perm, int32_t* left, int32_t* right, int32_t* first,
+                      int32_t* count, int32_t* height, int32_t* roff) {
+  if (!ctx) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_tree) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  const size_t nb = (size_t)c.nodes * sizeof(int32_t);
+  if (perm) ZQ_CUDA_TRY(cudaMemcpy(perm, c.perm, c.N * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (left) ZQ_CUDA_TRY(cudaMemcpy(left, c.cl, nb, cudaMemcpyDeviceToHost));
+  if (right) ZQ_CUDA_TRY(cudaMemcpy(right, c.cr, nb, cudaMemcpyDeviceToHost));
+  if (first) ZQ_CUDA_TRY(cudaMemcpy(first, c.first, nb, cudaMemcpyDeviceToHost));
+  if (count) ZQ_CUDA_TRY(cudaMemcpy(count, c.cnt, nb, cudaMemcpyDeviceToHost));
+  if (roff) ZQ_CUDA_TRY(cudaMemcpy(roff, c.roff, nb, cudaMemcpyDeviceToHost));
+  if (height) {
+    std::vector<uint8_t> h((size_t)c.nodes);
+    ZQ_CUDA_TRY(cudaMemcpy(h.data(), c.height, (size_t)c.nodes, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < c.nodes; ++i) height[i] = h[(size_t)i];
+  }
+  return ZQ_OK;
+}
+
+zq_status zq_get_nodes(zq_ctx* ctx, double* centroid, double* T22) {
+  if (!ctx) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_xform) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  std::vector<double> st((size_t)c.nodes * zq::kState);
+  ZQ_CUDA_TRY(cudaMemcpy(st.data(), c.st64, st.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int64_t q = 0; q < c.nodes; ++q) {
+    const double* s = st.data() + (size_t)q * zq::kState;
+    if (centroid)
+      for (int a = 0; a < 3; ++a) centroid[3 * q + a] = s[a];
+    if (T22)
+      for (int a = 0; a < 6; ++a) T22[6 * q + a] = s[3 + a];
+  }
+  return ZQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// zq_scan.cu -- exclusive prefix sum of int32 (residue offsets, list
+// compaction).  Three launches: per-block totals, one block scanning the
+// totals with a running carry, per-block scan plus carry.
+#include "zq_internal.cuh"
+
+namespace zq {
+
+namespace {
+
+constexpr int kThreads = 1024;
+constexpr int kItems = 4;
+constexpr int kTileN = kThreads * kItems;
+
+__device__ inline int32_t warp_incl_scan(int32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int32_t t = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread over the block; returns the prefix
+// and writes the block total to *total.
+__device__ inline int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t inc = warp_incl_scan(v);
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+    int32_t wi = warp_incl_scan(w);
+    sh[lane] = wi - w;
+    if (lane == 31) sh[32] = wi;
+  }
+  __syncthreads();
+  int32_t r = inc - v + sh[warp];
+  *total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_block_totals(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ tot) {
+  __shared__ int32_t sh[33];
+  int64_t base = (int64_t)blockIdx.x * kTileN + (int64_t)threadIdx.x * kItems;
+  int32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i)
+    if (base + i < n) s += in[base + i];
+  int32_t t;
+  block_excl_scan(s, sh, &t);
+  if (threadIdx.x == 0) tot[blockIdx.x] = t;
+}
+
+__global__ void k_scan_totals(int32_t* __restrict__ tot, int64_t nb, int32_t* __restrict__ total) {
+  __shared__ int32_t sh[33];
+  int32_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    int64_t i = b0 + threadIdx.x;
+    int32_t v = (i < nb) ? tot[i] : 0;
+    int32_t t;
+    int32_t e = block_excl_scan(v, sh, &t);
+    if (i < nb) tot[i] = carry + e;
+    carry += t;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_block_scan(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ tot,
+                             int32_t* __restrict__ out) {
+  __shared__ int32_t sh[33];
+  int64_t base = (int64_t)blockIdx.x * kTileN + (int64_t)threadIdx.x * kItems;
+  int32_t v[kItems];
+  int32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    v[i] = (base + i < n) ? in[base + i] : 0;
+    s += v[i];
+  }
+  int32_t t;
+  int32_t e = block_excl_scan(s, sh, &t) + tot[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    if (base + i < n) out[base + i] = e;
+    e += v[i];
+  }
+}
+
+}  // namespace
+
+int64_t scan_tmp_words(int64_t n) { return (n + kTileN - 1) / kTileN + 1; }
+
+// out[i] = sum_{k<i} in[k]; *total (device, may be NULL) = sum of all.
+// in and out may alias.  tmp: scan_tmp_words(n) ints of device scratch.
+zq_status launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                                int32_t* total, cudaStream_t s) {
+  if (n <= 0) {
+    if (total) ZQ_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(int32_t), s));
+    return ZQ_OK;
+  }
+  int64_t nb = (n + kTileN - 1) / kTileN;
+  k_block_totals<<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp);
+  k_scan_totals<<<1, kThreads, 0, s>>>(tmp, nb, total);
+  k_block_scan<<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp, out);
+  ZQ_CUDA_TRY(cudaGetLastError());
+  return ZQ_OK;
+}
+
+}  // namespace zq

@@ -1,0 +1,203 @@
+"""ctypes binding of libzq (include/zq.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module turns
+torch tensors into device pointers and sizes, and C status codes into
+exceptions.  The library must have been built (``__graft_entry__.build()``
+or ``python paper_1708_08427_gb300/build.py``); importing this module
+without it raises -- there is no CPU fallback.
+
+Layouts (see include/zq.h): bead vectors are planes (k, 3, N) of the
+caller's bead order; residue vectors are (k, R) with R = 3N - 6m.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libzq.so"
+
+ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE = range(7)
+ZQ_FP64, ZQ_FP32 = 0, 1
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class ZQError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {_lib().zq_status_string(code).decode()} (status {code})")
+
+
+_L: ctypes.CDLL | None = None
+
+
+def _lib() -> ctypes.CDLL:
+    global _L
+    if _L is None:
+        if not _LIB_PATH.exists():
+            raise ImportError(f"libzq.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(str(_LIB_PATH))
+        L.zq_status_string.restype = ctypes.c_char_p
+        L.zq_status_string.argtypes = [ctypes.c_int]
+        L.zq_create.restype = ctypes.c_int
+        L.zq_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp]
+        L.zq_destroy.restype = ctypes.c_int
+        L.zq_destroy.argtypes = [_vp]
+        L.zq_build_tree_batched.restype = ctypes.c_int
+        L.zq_build_tree_batched.argtypes = [_vp, _i64, _i64p, _vp, _vp, _vp, ctypes.c_int32]
+        L.zq_build_tree.restype = ctypes.c_int
+        L.zq_build_tree.argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_int32]
+        L.zq_build_transforms.restype = ctypes.c_int
+        L.zq_build_transforms.argtypes = [_vp, _vp, _vp, _vp]
+        for name in ("zq_apply_Q", "zq_apply_QT"):
+            f = getattr(L, name)
+            f.restype = ctypes.c_int
+            f.argtypes = [_vp, ctypes.c_int, _i64, _vp, _i64, _vp, _i64]
+        L.zq_sync.restype = ctypes.c_int
+        L.zq_sync.argtypes = [_vp]
+        L.zq_sizes.restype = ctypes.c_int
+        L.zq_sizes.argtypes = [_vp, _i64p, _i64p, _i64p, _i64p]
+        L.zq_get_tree.restype = ctypes.c_int
+        L.zq_get_tree.argtypes = [_vp] + [_i32p] * 7
+        L.zq_get_nodes.restype = ctypes.c_int
+        L.zq_get_nodes.argtypes = [_vp, _f64p, _f64p]
+        _L = L
+    return _L
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def _check(code: int, where: str, allow=(ZQ_OK,)):
+    if code not in allow:
+        raise ZQError(code, where)
+    return code
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def _np_i32(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(_i32p)
+
+
+class Context:
+    """Owns a zq_ctx: tree, transforms and scratch on one device/stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self._torch = torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = _vp()
+        _check(_lib().zq_create(ctypes.byref(h), device, _vp(stream.cuda_stream)), "zq_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().zq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ builds
+    def build_tree_batched(self, off, x, y, z, tile_beads: int = 0):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        self._off = off
+        m = off.shape[0] - 1
+        for t in (x, y, z):
+            assert t.is_cuda and t.dtype == self._torch.float64 and t.is_contiguous()
+        _check(_lib().zq_build_tree_batched(self._h, m, off.ctypes.data_as(_i64p), _ptr(x), _ptr(y),
+                                            _ptr(z), int(tile_beads)), "zq_build_tree_batched")
+
+    def build_tree(self, x, y, z, tile_beads: int = 0):
+        self.build_tree_batched(np.array([0, x.shape[0]], np.int64), x, y, z, tile_beads)
+
+    def build_transforms(self, x, y, z):
+        _check(_lib().zq_build_transforms(self._h, _ptr(x), _ptr(y), _ptr(z)), "zq_build_transforms")
+
+    # ------------------------------------------------------------ applies
+    def sizes(self):
+        N, m, R, nodes = _i64(), _i64(), _i64(), _i64()
+        _check(_lib().zq_sizes(self._h, ctypes.byref(N), ctypes.byref(m), ctypes.byref(R),
+                               ctypes.byref(nodes)), "zq_sizes")
+        return int(N.value), int(m.value), int(R.value), int(nodes.value)
+
+    @staticmethod
+    def _prec(t):
+        import torch
+
+        if t.dtype == torch.float64:
+            return ZQ_FP64
+        if t.dtype == torch.float32:
+            return ZQ_FP32
+        raise TypeError("vectors must be float32 or float64")
+
+    def apply_Q(self, v, out=None):
+        """v: (3, N) or (k, 3, N) device tensor -> (R,) or (k, R)."""
+        N, m, R, _ = self.sizes()
+        squeeze = v.dim() == 2
+        vv = v.reshape(-1, 3 * N)
+        assert vv.is_contiguous() and v.is_cuda
+        k = vv.shape[0]
+        if out is None:
+            out = self._torch.empty((k, R), dtype=v.dtype, device=v.device)
+        oo = out.reshape(k, R)
+        _check(_lib().zq_apply_Q(self._h, self._prec(v), k, _ptr(vv), 3 * N, _ptr(oo), R), "zq_apply_Q")
+        return out.reshape(R) if squeeze and out.dim() == 2 else out
+
+    def apply_QT(self, w, out=None):
+        """w: (R,) or (k, R) device tensor -> (3, N) or (k, 3, N)."""
+        N, m, R, _ = self.sizes()
+        squeeze = w.dim() == 1
+        ww = w.reshape(-1, R)
+        assert ww.is_contiguous() and w.is_cuda
+        k = ww.shape[0]
+        if out is None:
+            out = self._torch.empty((k, 3, N), dtype=w.dtype, device=w.device)
+        _check(_lib().zq_apply_QT(self._h, self._prec(w), k, _ptr(ww), R, _ptr(out), 3 * N), "zq_apply_QT")
+        return out.reshape(3, N) if squeeze else out
+
+    def sync(self, allow_degenerate: bool = False):
+        allow = (ZQ_OK, ZQ_WDEGENERATE) if allow_degenerate else (ZQ_OK,)
+        return _check(_lib().zq_sync(self._h), "zq_sync", allow)
+
+    # ------------------------------------------------------------ exports
+    def get_tree(self) -> dict:
+        N, m, R, nodes = self.sizes()
+        perm = np.empty(N, np.int32)
+        arrs = {k: np.empty(nodes, np.int32) for k in ("left", "right", "first", "count", "height", "roff")}
+        _check(_lib().zq_get_tree(self._h, _np_i32(perm), _np_i32(arrs["left"]), _np_i32(arrs["right"]),
+                                  _np_i32(arrs["first"]), _np_i32(arrs["count"]), _np_i32(arrs["height"]),
+                                  _np_i32(arrs["roff"])), "zq_get_tree")
+        return dict(perm=perm, **arrs)
+
+    def get_nodes(self):
+        N, m, R, nodes = self.sizes()
+        c = np.empty((nodes, 3))
+        L = np.empty((nodes, 6))
+        _check(_lib().zq_get_nodes(self._h, c.ctypes.data_as(_f64p), L.ctypes.data_as(_f64p)),
+               "zq_get_nodes")
+        return c, L
+
+
+# raw C entry points, same names as include/zq.h
+def __getattr__(name):
+    if name.startswith("zq_"):
+        return getattr(_lib(), name)
+    raise AttributeError(name)

@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tree and index construction: bit-exact.  FP64 transforms and sweeps:
+relative error <= 1e-12; FP32 sweeps: <= 1e-5 (per body, 2-norm relative to
+the oracle's result).  Sizes span several tiles and ragged tails; edge
+cases: 3-bead bodies, flat and far-off bodies, coincident beads, bodies that
+need the device radix sort, the largest tile, and the full-size workloads.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_08427_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {np.float64: 1e-12, np.float32: 1e-5}
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _zq():
+    from paper_1708_08427_gb300 import zq
+
+    return zq
+
+
+def make_ctx(bt, tile=0):
+    dev = _dev()
+    zq = _zq()
+    x, y, z = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (bt.x, bt.y, bt.z))
+    ctx = zq.Context(0)
+    ctx.build_tree_batched(bt.off, x, y, z, tile)
+    ctx.build_transforms(x, y, z)
+    return ctx, (x, y, z)
+
+
+def oracle_bodies(bt):
+    return [oracle.Body(*bt.body(j)) for j in range(bt.m)]
+
+
+def oracle_tree_global(bt, bodies):
+    """The oracle's per-body trees in the library's global numbering."""
+    N, m = bt.N, bt.m
+    perm = np.empty(N, np.int32)
+    nodes = N - m
+    out = {k: np.empty(nodes, np.int64) for k in ("left", "right", "first", "count", "height", "roff")}
+    rbase = 0
+    for j, B in enumerate(bodies):
+        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
+        nb = o - j
+        t = B.tree()
+        perm[o:o + n] = t["perm"] + o
+        sl = slice(nb, nb + n - 1)
+
+        def glob(code):
+            return np.where(code >= 0, code + nb, -1 - (o + (-1 - code)))
+
+        out["left"][sl] = glob(t["left"])
+        out["right"][sl] = glob(t["right"])
+        out["first"][sl] = t["first"] + o
+        out["count"][sl] = t["last"] - t["first"] + 1
+        out["height"][sl] = t["height"]
+        out["roff"][sl] = t["roff"] + rbase
+        rbase += 3 * n - 6
+    return perm, out
+
+
+def check_tree(ctx, bt, bodies):
+    g = ctx.get_tree()
+    perm, ref = oracle_tree_global(bt, bodies)
+    np.testing.assert_array_equal(g["perm"], perm)
+    for k in ("left", "right", "first", "count", "height", "roff"):
+        np.testing.assert_array_equal(g[k], ref[k], err_msg=k)
+
+
+def check_nodes(ctx, bt, bodies):
+    c, L = ctx.get_nodes()
+    worst = 0.0
+    for j, B in enumerate(bodies):
+        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
+        nb = o - j
+        for gsp in range(n - 1):
+            nd = B.node(gsp)
+            Lo = nd["L"][np.tril_indices(3)]
+            scale = max(np.abs(Lo).max(), 1e-300)
+            worst = max(worst, np.abs(L[nb + gsp] - Lo).max() / scale)
+            cs = max(np.abs(nd["c"]).max(), 1.0)
+            worst = max(worst, np.abs(c[nb + gsp] - nd["c"]).max() / cs)
+    assert worst <= 1e-12, worst
+    return worst
+
+
+def rel_err_per_body(got, ref, bt, kind):
+    errs = []
+    ro = 0
+    for j in range(bt.m):
+        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
+        if kind == "res":
+            a, b = got[..., ro:ro + 3 * n - 6], ref[..., ro:ro + 3 * n - 6]
+        else:
+            a, b = got[..., 3 * o:3 * (o + n)], ref[..., 3 * o:3 * (o + n)]
+        ro += 3 * n - 6
+        errs.append(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    return np.array(errs)
+
+
+def check_apply(ctx, bt, dtype, k=1, seed=0):
+    dev = _dev()
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((k, 3, bt.N))
+    w = rng.standard_normal((k, bt.n_residues))
+    qv = ctx.apply_Q(torch.from_numpy(v).to(dev, getattr(torch, np.dtype(dtype).name)))
+    qtw = ctx.apply_QT(torch.from_numpy(w).to(dev, getattr(torch, np.dtype(dtype).name)))
+    ctx.sync(allow_degenerate=True)
+    qv = qv.double().cpu().numpy()
+    qtw = qtw.double().cpu().numpy()
+    worst = 0.0
+    for c in range(k):
+        rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*v[c]), w[c])
+        e1 = rel_err_per_body(qv[c], rq, bt, "res")
+        e2 = rel_err_per_body(W.interleave(*qtw[c]), rqt, bt, "bead")
+        worst = max(worst, e1.max(), e2.max())
+    assert worst <= TOL[dtype], (dtype, worst)
+    return worst
+
+
+# --------------------------------------------------------------- cases
+
+
+def test_single_body_256_sixteen_vectors():
+    """n = 256 shell of radius 2 with N(0, 0.05^2) jitter, 16 right-hand
+    sides; bisection tree exact, FP64 and FP32 sweeps."""
+    bt = W.shell_body(256, radius=2.0, sigma=0.05, seed=0)
+    ctx, _ = make_ctx(bt, tile=64)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    check_nodes(ctx, bt, bodies)
+    check_apply(ctx, bt, np.float64, k=16, seed=1)
+    check_apply(ctx, bt, np.float32, k=16, seed=1)
+
+
+@pytest.mark.parametrize("tile", [64, 512, 4096])
+def test_batch_ragged_tiles(tile):
+    """Bodies from 3 to 700 beads: many tiles per body for small tiles,
+    nodes above the tiles, 3-bead bodies."""
+    bt = W.shell_batch(m=60, nmin=3, nmax=700, seed=4)
+    ctx, _ = make_ctx(bt, tile=tile)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    check_nodes(ctx, bt, bodies)
+    check_apply(ctx, bt, np.float64, seed=2)
+    check_apply(ctx, bt, np.float32, seed=3)
+
+
+def test_results_do_not_depend_on_tile():
+    bt = W.shell_batch(m=20, nmin=50, nmax=2000, seed=8)
+    dev = _dev()
+    rng = np.random.default_rng(5)
+    v = torch.from_numpy(rng.standard_normal((3, bt.N))).to(dev)
+    w = torch.from_numpy(rng.standard_normal(bt.n_residues)).to(dev)
+    outs = []
+    for tile in (64, 300, 2048):
+        ctx, _ = make_ctx(bt, tile=tile)
+        outs.append((ctx.apply_Q(v).cpu(), ctx.apply_QT(w).cpu(),
+                     ctx.apply_Q(v.float()).cpu(), ctx.apply_QT(w.float()).cpu()))
+        ctx.sync()
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
+
+
+def test_large_body_radix_sort_path():
+    """A body above the per-block sort limit (device radix sort) and above
+    the tile size (nodes above the tiles)."""
+    bt = W.ellipsoid_body(n=20000, seed=3)
+    ctx, _ = make_ctx(bt, tile=512)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    check_nodes(ctx, bt, bodies)
+    check_apply(ctx, bt, np.float64)
+    check_apply(ctx, bt, np.float32)
+
+
+def _batch_from_points(bodies_pts):
+    off = np.zeros(len(bodies_pts) + 1, np.int64)
+    off[1:] = np.cumsum([p.shape[0] for p in bodies_pts])
+    P = np.concatenate(bodies_pts)
+    return W.Batch(off, P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy())
+
+
+def test_edge_geometries():
+    rng = np.random.default_rng(12)
+    pts = [
+        rng.uniform(-1, 1, (3, 3)),                                   # smallest body
+        np.c_[rng.uniform(-1, 1, (40, 2)), np.full(40, 0.3)],         # flat (z = const)
+        rng.uniform(-1, 1, (50, 3)) + [1e3, -2e3, 5e2],               # far from the origin
+        np.c_[np.linspace(0, 1, 30), rng.normal(0, 1e-6, 30), rng.normal(0, 1e-6, 30)],  # near-collinear
+        np.r_[rng.uniform(0, 1, (20, 3)), np.full((4, 3), 0.5)],      # beads sharing one cell
+    ]
+    bt = _batch_from_points(pts)
+    ctx, _ = make_ctx(bt, tile=64)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    check_apply(ctx, bt, np.float64)
+
+
+def test_coincident_beads_warn():
+    rng = np.random.default_rng(1)
+    p = rng.uniform(0, 1, (10, 3))
+    p[7] = p[3]
+    bt = _batch_from_points([p])
+    zq = _zq()
+    ctx, _ = make_ctx(bt, tile=64)
+    assert ctx.sync(allow_degenerate=True) == zq.ZQ_WDEGENERATE
+    check_tree(ctx, bt, oracle_bodies(bt))
+    check_apply(ctx, bt, np.float64)
+
+
+def test_non_finite_coordinates_reported():
+    zq = _zq()
+    bt = W.shell_body(64, seed=2)
+    bt.x[5] = np.nan
+    with pytest.raises(zq.ZQError) as ei:
+        ctx, _ = make_ctx(bt, tile=64)
+        ctx.sync()
+    assert ei.value.code == zq.ZQ_ENONFINITE
+
+
+def test_argument_errors():
+    zq = _zq()
+    dev = _dev()
+    ctx = zq.Context(0)
+    x = torch.zeros(2, dtype=torch.float64, device=dev)
+    with pytest.raises(zq.ZQError) as ei:
+        ctx.build_tree_batched(np.array([0, 2]), x, x, x)
+    assert ei.value.code == zq.ZQ_EINVAL
+    v = torch.zeros((3, 4), dtype=torch.float64, device=dev)
+    with pytest.raises(zq.ZQError) as ei:
+        ctx.apply_Q(v)
+    assert ei.value.code == zq.ZQ_ESTATE
+
+
+# --------------------------------------------------------- full sizes
+
+
+def test_full_size_batched_shells():
+    """2000 bodies, log-uniform 50..5000 beads: every output against the
+    oracle (FP32 sweeps, FP64 transforms), tree bit-exact."""
+    bt = W.shell_batch(m=2000, seed=0)
+    ctx, _ = make_ctx(bt)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    del bodies
+    check_apply(ctx, bt, np.float32, seed=7)
+    check_apply(ctx, bt, np.float64, seed=7)
+
+
+def test_full_size_ellipsoid():
+    """One body of 2^20 beads: tree bit-exact, sweeps against the oracle."""
+    bt = W.ellipsoid_body(n=1 << 20, seed=0)
+    ctx, _ = make_ctx(bt)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    del bodies
+    check_apply(ctx, bt, np.float32, seed=9)
+    check_apply(ctx, bt, np.float64, seed=9)
