@@ -151,6 +151,14 @@ zq_status zq_get_tree(zq_ctx *ctx, int32_t *perm, int32_t *left, int32_t *right,
  * (L00, L10, L11, L20, L21, L22). */
 zq_status zq_get_nodes(zq_ctx *ctx, double *centroid, double *T22);
 
+/* Node-transform export (synchronous; HOST array of (N - m) * 28 doubles):
+ * per node q, rec[28*q + i]: [0] sqrt(n_x/n), [1] sqrt(n_y/n), [2..4] the
+ * Householder factors tau_1..3 of Eq. 3.5's LQ (G = H_3 H_2 H_1,
+ * H_j = I - tau_j v_j v_j^T, v_j(j) = 1, v_j zero above j), then the
+ * reflector entries below the unit entry: v_1(2..k), v_2(3..k), v_3(4..k)
+ * for k = 6, 9; for Case I (k = 3) entries 5..13 hold G row-major. */
+zq_status zq_get_records(zq_ctx *ctx, double *rec);
+
 #ifdef __cplusplus
 }
 #endif

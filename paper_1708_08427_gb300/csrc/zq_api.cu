@@ -298,4 +298,15 @@ zq_status zq_get_nodes(zq_ctx* ctx, double* centroid, double* T22) {
   return ZQ_OK;
 }
 
+zq_status zq_get_records(zq_ctx* ctx, double* rec) {
+  if (!ctx || !rec) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_xform) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  ZQ_CUDA_TRY(cudaMemcpy(rec, c.rec64, (size_t)c.nodes * zq::kRec * sizeof(double),
+                         cudaMemcpyDeviceToHost));
+  return ZQ_OK;
+}
+
 }  // extern "C"

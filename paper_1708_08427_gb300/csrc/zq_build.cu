@@ -8,7 +8,10 @@
 //   M = [T22_x | T22_y | K] (3 x k; a leaf child has no T22 block, Case II),
 //   M = [T22_p 0] G by Householder reflections of M^T (Eq. 3.5; LAPACK
 //       dgeqrf convention: beta_j = -sign(alpha_j) ||x||, no reflection when
-//       the part below the diagonal is exactly zero; T22_p = R^T, G = Q^T).
+//       the part below the diagonal is exactly zero; T22_p = R^T, G = Q^T);
+//       before each reflection, column entries <= 2^-44 ||M||_F are set to
+//       zero, so rank-deficient M (collinear or coincident beads) give a
+//       transform that does not depend on rounding noise.
 // Case I (two leaves, Eqs. 3.9-3.10): G rows g1 = (e_x x d)/|e_x x d|
 // (e_y x d when d has no y, z part), g2 = dhat x g1, g3 = -dhat, and
 // T22_p = sqrt(n_x n_y / n) |d| [g2, -g1, 0]; d = 0 gives G = I, T22 = 0
@@ -148,9 +151,18 @@ __device__ void build_node(const BuildArgs& a, int64_t q) {
     A[k + 1][0] = sk * (-d[2]); A[k + 1][1] = sk * 0.0;    A[k + 1][2] = sk * d[0];
     A[k + 2][0] = sk * d[1];   A[k + 2][1] = sk * (-d[0]); A[k + 2][2] = sk * 0.0;
     k += 3;
+    // entries <= 2^-44 ||M||_F are rounding noise of an exact zero
+    // (rank-deficient M); they are zeroed before each reflection
+    double mn2 = 0.0;
+    for (int i = 0; i < k; ++i)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mn2 += A[i][c] * A[i][c];
+    const double tiny = sqrt(mn2) * 0x1p-44;
     int tail = 5;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
+      for (int i = j; i < k; ++i)
+        if (fabs(A[i][j]) <= tiny) A[i][j] = 0.0;
       double xn2 = 0.0;
       for (int i = j + 1; i < k; ++i) xn2 += A[i][j] * A[i][j];
       if (xn2 != 0.0) {

@@ -67,6 +67,8 @@ def _lib() -> ctypes.CDLL:
         L.zq_get_tree.argtypes = [_vp] + [_i32p] * 7
         L.zq_get_nodes.restype = ctypes.c_int
         L.zq_get_nodes.argtypes = [_vp, _f64p, _f64p]
+        L.zq_get_records.restype = ctypes.c_int
+        L.zq_get_records.argtypes = [_vp, _f64p]
         _L = L
     return _L
 
@@ -194,6 +196,29 @@ class Context:
         _check(_lib().zq_get_nodes(self._h, c.ctypes.data_as(_f64p), L.ctypes.data_as(_f64p)),
                "zq_get_nodes")
         return c, L
+
+    def get_records(self) -> np.ndarray:
+        """FP64 node records, shape (nodes, 28) (layout in include/zq.h)."""
+        N, m, R, nodes = self.sizes()
+        rec = np.empty((nodes, 28))
+        _check(_lib().zq_get_records(self._h, rec.ctypes.data_as(_f64p)), "zq_get_records")
+        return rec
+
+    @staticmethod
+    def record_to_G(rec: np.ndarray, k: int) -> np.ndarray:
+        """Dense k x k transform G from one FP64 record (host-side, for
+        inspection and tests only)."""
+        if k == 3:
+            return rec[5:14].reshape(3, 3).copy()
+        G = np.eye(k)
+        tail = 5
+        for j in range(3):
+            v = np.zeros(k)
+            v[j] = 1.0
+            v[j + 1:] = rec[tail:tail + k - 1 - j]
+            tail += k - 1 - j
+            G = G - rec[2 + j] * np.outer(v, v @ G)
+        return G
 
 
 # raw C entry points, same names as include/zq.h

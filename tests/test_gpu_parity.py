@@ -270,3 +270,18 @@ def test_full_size_ellipsoid():
     del bodies
     check_apply(ctx, bt, np.float32, seed=9)
     check_apply(ctx, bt, np.float64, seed=9)
+
+
+def test_collinear_and_lattice_bodies_match():
+    """Exactly collinear beads and lattice bodies (rank-deficient node
+    matrices everywhere): the FP64 sweeps still match the oracle."""
+    n = 30
+    line = np.c_[np.arange(n) * 0.25, np.arange(n) * 0.5, np.full(n, 1.0)]
+    g = np.arange(64)
+    lattice = np.c_[g % 4, (g // 4) % 4, g // 16].astype(float) * 0.3
+    bt = _batch_from_points([line, lattice])
+    ctx, _ = make_ctx(bt, tile=64)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    check_apply(ctx, bt, np.float64)
+    check_apply(ctx, bt, np.float32)

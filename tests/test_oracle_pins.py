@@ -448,3 +448,38 @@ def test_node_assembly_eq_3_5(seed):
 
 def pair_of(t, p, g):
     return [p[t["perm"][t["first"][g]]], p[t["perm"][t["last"][g]]]]
+
+
+# ----------------------------------------------- rank-deficient nodes (A8)
+
+
+def test_lq_rank_deficient_is_exact_and_valid():
+    """M = [0 | K] (a child whose beads coincide, T22 = 0, next to a bead):
+    rank two.  The third pivot is exactly zero, L G = M, G orthogonal, and
+    the completion rows annihilate M's rows."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        d = rng.standard_normal(3)
+        K = 0.8 * _cross(d)
+        for M in (np.hstack([np.zeros((3, 3)), K]), np.hstack([np.zeros((3, 3)), np.zeros((3, 3)), K])):
+            k = M.shape[1]
+            L, G = oracle.lq(M)
+            assert L[2, 2] == 0.0
+            np.testing.assert_allclose(G @ G.T, np.eye(k), atol=1e-14)
+            np.testing.assert_allclose(np.hstack([L, np.zeros((3, k - 3))]) @ G, M, atol=1e-14)
+            np.testing.assert_allclose(M @ G[3:].T, 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [6, 13, 30])
+def test_collinear_and_lattice_bodies(n):
+    """Exactly collinear beads (rank Z = 5) and a lattice (many collinear
+    triples): rows orthonormal and orthogonal to Z."""
+    line = np.c_[np.arange(n) * 0.25, np.arange(n) * 0.5, np.full(n, 1.0)]
+    g = np.arange(n)
+    lattice = np.c_[g % 3, (g // 3) % 3, g // 9].astype(float)
+    for p in (line, lattice):
+        B = oracle.Body(p[:, 0], p[:, 1], p[:, 2])
+        Qt, _ = B.qgen()
+        Z = z_matrix(p[:, 0], p[:, 1], p[:, 2])
+        np.testing.assert_allclose(Qt @ Qt.T, np.eye(3 * n - 6), atol=1e-13)
+        assert np.abs(Qt @ Z.T).max() <= 1e-12 * np.abs(Z).max()
