@@ -1,0 +1,619 @@
+#!/usr/bin/env python
+"""Benchmark of the batched hierarchical products Q~v and Q~^T w on GB300.
+
+A step is one pass of the whole path over a batch of synthetic rigid bodies
+(all inputs resident in HBM): the bisection tree (Sec. 2.1), the FP64 node
+transforms (Sec. 3, Eq. 3.5), Q~v (Algorithm 2) and Q~^T w (Algorithm 3)
+in FP32, through the C ABI (zq_pipeline); the timed steps are direct
+launches with the dominant kernel bracketed by CUDA events, and the same step
+captured in a CUDA graph is timed beside it.  Default workload: 2000 jittered sphere shells, n_j log-uniform in
+[50, 5000] (radius 0.1 sqrt(n_j), jitter 2.5% of the radius, centres uniform
+in a 100^3 box).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own batch (seed = rank): weak scaling, no
+data-path collective; the barrier and the max over ranks are the only
+communication.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = ("beads/s for batched Q̃v+Q̃ᵀv (FP32 vs FP64 GPU) at stated error; "
+          "% HBM peak")
+FP64_PEAK_NOMINAL = 1.25e12  # FP64 flop/s, GB300 nominal (FP64 FMA counted as 2 flops)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["shells2000", "ellipsoid"], default="shells2000")
+    ap.add_argument("--tile", type=int, default=2048)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 / apply-only / e2e / CPU legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ setup
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x: float, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_workload(name: str, seed: int):
+    from paper_1708_08427_gb300 import workloads as W
+
+    if name == "shells2000":
+        bt = W.shell_batch(m=2000, nmin=50, nmax=5000, seed=seed)
+        desc = ("batched jittered sphere shells: m=2000, n_j log-uniform [50,5000], radius "
+                "0.1*sqrt(n_j), jitter 0.025*radius, centres U[0,100]^3")
+    else:
+        bt = W.ellipsoid_body(n=1 << 20, seed=seed)
+        desc = "one ellipsoid body, n=2^20, semi-axes (3,2,1)*sqrt(n)/100, radial jitter N(0,0.01^2)"
+    return bt, desc
+
+
+# --------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ work model
+
+
+def node_census(ctx):
+    """Counts of internal nodes by transform size k (3, 6, 9)."""
+    t = ctx.get_tree()
+    internal = (t["left"] >= 0).astype(np.int64) + (t["right"] >= 0).astype(np.int64)
+    return {3: int((internal == 0).sum()), 6: int((internal == 1).sum()), 9: int((internal == 2).sum())}
+
+
+def build_flops(k: int) -> int:
+    """FP64 flops of one node transform as the build computes it (sqrt and
+    division count 1; FMA 2).  Geometry: centroid, offset, sqrt(n_x/n),
+    sqrt(n_y/n), sqrt(n_x n_y/n) = 23.  Case I (k = 3): closed form = 29.
+    k = 6, 9: ||M||_F (6k), then per reflector j with m = k - 1 - j entries
+    below the diagonal: norm 2m + 3, tau 2, scaling m + 1, and per remaining
+    column (2 - j of them) 2m + 2 + 3m."""
+    geo = 23
+    if k == 3:
+        return geo + 29
+    f = 6 * k
+    for j in range(3):
+        m = k - 1 - j
+        f += (2 * m + 3) + 2 + (m + 1) + (2 - j) * (5 * m + 2)
+    return geo + f
+
+
+RECORD_FLOATS = {3: 11, 6: 17, 9: 26}  # words of the node record a sweep needs
+
+
+def sweep_bytes(census, N, R, es=4) -> int:
+    """Algorithmic DRAM bytes of one sweep (up or down): the bead-vector
+    planes (3N) and residues (R) once, each node record once (by k), the
+    node structure (two child codes, residue offset: 12 B; height 1 B) and
+    the sorted-position -> bead map (4 B per bead)."""
+    rec = sum(census[k] * RECORD_FLOATS[k] * es for k in census)
+    nodes = sum(census.values())
+    return es * (3 * N + R) + rec + 13 * nodes + 4 * N
+
+
+def kernel_work(name, census, N, R, m, es):
+    """(bound, algorithmic amount per launch, unit)."""
+    if name in ("build_tiles", "build_top"):
+        return "alu", sum(census[k] * build_flops(k) for k in census), "flop"
+    if name in ("up_tiles", "down_tiles"):
+        return "hbm", sweep_bytes(census, N, R, es), "B"
+    if name == "sort_small":
+        return "hbm", 8 * N + 8 * N + 4 * N, "B"
+    if name == "bottom_up":
+        nodes = N - m
+        return "hbm", N * 1 + nodes * (4 * 6 + 1), "B"
+    return "hbm", 24 * N, "B"
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    f = ROOT / "profiles" / "traffic.json"
+    if not f.exists():
+        return None
+    try:
+        d = json.loads(f.read_text())
+        e = d.get(kernel)
+        if not e:
+            return None
+        src = ROOT / e["source"]
+        h = hashlib.sha256(src.read_bytes()).hexdigest()
+        if h != e["sha256"]:
+            return None
+        return float(e["dram_bytes_per_launch"]) * float(e.get("scale", 1.0))
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ our arm
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1708_08427_gb300 import zq
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    bt, desc = make_workload(args.workload, seed=rank)
+    N, m, R = bt.N, bt.m, bt.n_residues
+    stream = torch.cuda.Stream(device=dev)
+    rng = np.random.default_rng(1000 + rank)
+    with torch.cuda.stream(stream):
+        x, y, z = (torch.from_numpy(a).to(dev) for a in (bt.x, bt.y, bt.z))
+        v = torch.from_numpy(rng.standard_normal((3, N))).to(dev, torch.float32)
+        w = torch.from_numpy(rng.standard_normal(R)).to(dev, torch.float32)
+        qv = torch.empty(R, dtype=torch.float32, device=dev)
+        qtw = torch.empty((3, N), dtype=torch.float32, device=dev)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream.synchronize()
+    _XYZ[id(bt)] = (x, y, z)
+    ctx = zq.Context(local, stream=stream)
+
+    def step(prec_t=torch.float32, vv=v, ww=w, oq=qv, oqt=qtw):
+        ctx.pipeline(bt.off, x, y, z, vv, oq, ww, oqt, tile_beads=args.tile)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    ctx.sync()
+    census = node_census(ctx)
+
+    # --- per-kernel time of one step (measurement hook), picks the dominant kernel
+    names = ["aabb", "keys", "sort_small", "sort_radix", "lcp", "bottom_up", "scan", "classify",
+             "build_tiles", "build_top", "up_tiles", "up_top", "down_top", "down_tiles"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e1.record(stream)
+    phases = {}
+    for nm in names:
+        ctx.time_kernel(nm, e0, e1)
+        tot = 0.0
+        e0.record(stream)
+        e1.record(stream)
+        stream.synchronize()
+        reps = 3
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            step()
+            stream.synchronize()
+            tot += e0.elapsed_time(e1)
+        ctx.time_kernel(None)
+        phases[nm] = tot / reps
+    dominant = max(("build_tiles", "up_tiles", "down_tiles", "sort_small", "bottom_up"),
+                   key=lambda k: phases.get(k, 0.0))
+
+    # --- the dominant kernel is bracketed by events in every timed step
+    # (event records captured inside a CUDA graph carry no timing, so the
+    # timed steps are direct launches; the graph replay is timed separately)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    k1.record(stream)
+    stream.synchronize()
+    ctx.time_kernel(dominant, k0, k1)
+    before = ctx.launch_count()
+    step()
+    stream.synchronize()
+    launches_per_step = ctx.launch_count() - before
+    ctx.sync()
+
+    def run_step():
+        step()
+
+    for _ in range(args.warmup):
+        run_step()
+    stream.synchronize()
+
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                    # L2 flush, outside the events
+        s0.record(stream)
+        run_step()
+        s1.record(stream)
+        stream.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        kern_ms.append(k0.elapsed_time(k1))
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ctx.time_kernel(None)
+    ctx.sync()
+
+    t_dev = sum(step_ms) / 1e3
+    t_max = max_over_ranks(world, t_dev, dev)
+    beads_total = sum_over_ranks(world, float(N) * args.steps, dev)
+    value = beads_total / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+
+    bound, work, unit = kernel_work(dominant, census, N, R, m, 4)
+    kavg = statistics.mean(kern_ms) / 1e3
+    if bound == "alu":
+        achieved, peak, runit = work / kavg / 1e12, FP64_PEAK_NOMINAL / 1e12, "TFLOP/s"
+        peak_note = "FP64 nominal 1.25 TFLOP/s (GB300 spec table); measured FMA probe 1.20"
+    else:
+        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        achieved, peak, runit = work / kavg / 1e9, hbm, "GB/s"
+        peak_note = "of measured" if peaks else "of fallback"
+    traffic = traffic_for(dominant)
+    roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
+                "work_per_launch": work, "work_unit": unit, "kernel_ms": 1e3 * kavg}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "beads/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps, f64 transforms",
+        "data": "synthetic (seeded numpy generators; no dataset)",
+        "config": {"workload": desc, "m": m, "N": N, "residues": R, "tile_beads": args.tile,
+                   "graph": False, "prec": "fp32",
+                   "step": "tree + FP64 transforms + Q~v + Q~^T w (one C-ABI call, zq_pipeline)",
+                   "l2": "512 MB buffer written before every step, outside the step events",
+                   "wall_s_timed_region": wall},
+        "roofline": roofline, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+        "phases_ms": phases,
+    }
+
+    if not args.no_graph:
+        out["graph_replay"] = timed(args, step, stream, flush, world, dev, N, graph=True)
+    if not args.no_extras:
+        out["fp64_step"] = fp64_step(args, ctx, bt, stream, flush, rng, world, dev)
+        out["apply"] = apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev)
+        out["e2e"] = e2e(args, ctx, bt, stream, world, dev)
+    if rank == 0 and not args.no_extras:
+        out["cpu_baseline"] = cpu_baseline(bt, args.cpu_seconds)
+    ctx.close()
+    return out
+
+
+def fp64_step(args, ctx, bt, stream, flush, rng, world, dev):
+    """The plain FP64 GPU form: the same step with FP64 sweeps."""
+    import torch
+
+    N, R = bt.N, bt.n_residues
+    v = torch.from_numpy(rng.standard_normal((3, N))).to(dev)
+    w = torch.from_numpy(rng.standard_normal(R)).to(dev)
+    qv = torch.empty(R, dtype=torch.float64, device=dev)
+    qtw = torch.empty((3, N), dtype=torch.float64, device=dev)
+    stream.synchronize()
+
+    def step():
+        ctx.pipeline(bt.off, *xyz_of(ctx, bt, dev), v, qv, w, qtw, tile_beads=args.tile)
+
+    return timed(args, step, stream, flush, world, dev, N, graph=not args.no_graph)
+
+
+_XYZ = {}
+
+
+def xyz_of(ctx, bt, dev):
+    import torch
+
+    key = id(bt)
+    if key not in _XYZ:
+        _XYZ[key] = tuple(torch.from_numpy(a).to(dev) for a in (bt.x, bt.y, bt.z))
+    return _XYZ[key]
+
+
+def timed(args, fn, stream, flush, world, dev, N, graph=True, steps=None):
+    import torch
+
+    steps = steps or max(3, min(args.steps, 10))
+    for _ in range(2):
+        fn()
+    stream.synchronize()
+    g = None
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        stream.synchronize()
+    run = (lambda: g.replay()) if g is not None else fn
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            run()
+    stream.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        s0.record(stream)
+        with torch.cuda.stream(stream):
+            run()
+        s1.record(stream)
+        stream.synchronize()
+        ms.append(s0.elapsed_time(s1))
+    t = max_over_ranks(world, sum(ms) / 1e3, dev)
+    tot = sum_over_ranks(world, float(N) * steps, dev)
+    return {"value": tot / t, "unit": "beads/s", "ms_per_step": 1e3 * t / steps, "steps": steps}
+
+
+def apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev):
+    """Q~v + Q~^T w with the transforms already built (as inside a Krylov
+    solve), FP32 and FP64, with the sweep bytes achieved against HBM."""
+    import torch
+
+    N, R, m = bt.N, bt.n_residues, bt.m
+    res = {}
+    x, y, z = xyz_of(ctx, bt, dev)
+    ctx.pipeline(bt.off, x, y, z, v, qv, w, qtw, tile_beads=args.tile)
+    stream.synchronize()
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    for name, dt, es in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+        vv, ww = v.to(dt), w.to(dt)
+        oq = torch.empty(R, dtype=dt, device=dev)
+        oqt = torch.empty((3, N), dtype=dt, device=dev)
+        stream.synchronize()
+
+        def fn():
+            ctx.apply_Q(vv, oq)
+            ctx.apply_QT(ww, oqt)
+
+        r = timed(args, fn, stream, flush, world, dev, N, graph=not args.no_graph)
+        byt = 2 * sweep_bytes(census, N, R, es)
+        r["hbm_achieved_gbs"] = byt / (r["ms_per_step"] / 1e3) / 1e9
+        r["hbm_frac"] = r["hbm_achieved_gbs"] / hbm
+        r["algorithmic_bytes_per_step"] = byt
+        res[name] = r
+    return res
+
+
+def e2e(args, ctx, bt, stream, world, dev):
+    """The same step through the C ABI with HOST (pinned) buffers: host to
+    device copies of coordinates and vectors, the whole path, and the device
+    to host copies of both results inside the timed region."""
+    import torch
+
+    N, R = bt.N, bt.n_residues
+    rng = np.random.default_rng(7)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hx, hy, hz = pin(bt.x), pin(bt.y), pin(bt.z)
+    hv = pin(rng.standard_normal((3, N)).astype(np.float32))
+    hw = pin(rng.standard_normal(R).astype(np.float32))
+    hq = torch.empty(R, dtype=torch.float32).pin_memory()
+    hqt = torch.empty((3, N), dtype=torch.float32).pin_memory()
+
+    def fn():
+        ctx.pipeline(bt.off, hx, hy, hz, hv, hq, hw, hqt, tile_beads=args.tile, host=True)
+
+    for _ in range(2):
+        fn()
+    ctx.sync()
+    steps = max(3, min(args.steps, 10))
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    ms = []
+    for _ in range(steps):
+        s0.record(stream)
+        fn()
+        s1.record(stream)
+        stream.synchronize()
+        ms.append(s0.elapsed_time(s1))
+    ctx.sync()
+    t = max_over_ranks(world, sum(ms) / 1e3, dev)
+    tot = sum_over_ranks(world, float(N) * steps, dev)
+    return {"value": tot / t, "unit": "beads/s", "ms_per_step": 1e3 * t / steps,
+            "h2d_bytes_per_step": 24 * N + 12 * N + 4 * R, "d2h_bytes_per_step": 4 * R + 12 * N,
+            "steps": steps}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+
+def oracle_sample(bt, seconds: float):
+    """A prefix of the batch sized to about `seconds` of oracle work."""
+    import oracle
+
+    probe = max(1, min(bt.m, 20))
+    t0 = time.perf_counter()
+    n_probe = int(bt.off[probe])
+    _oracle_step(bt, probe, np.random.default_rng(0))
+    dt = time.perf_counter() - t0
+    rate = n_probe / max(dt, 1e-6)
+    target = rate * seconds
+    nb = int(np.searchsorted(bt.off, target))
+    return max(1, min(bt.m, nb)), rate
+
+
+def _oracle_step(bt, nbodies, rng):
+    import oracle
+
+    off = bt.off[:nbodies + 1]
+    n = int(off[-1])
+    f = rng.standard_normal(3 * n)
+    w = rng.standard_normal(3 * n - 6 * nbodies)
+    oracle.batch_apply(off, bt.x[:n], bt.y[:n], bt.z[:n], f, w)
+    return n
+
+
+def cpu_baseline(bt, seconds):
+    nb, _ = oracle_sample(bt, seconds)
+    rng = np.random.default_rng(1)
+    t0 = time.perf_counter()
+    n = _oracle_step(bt, nb, rng)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "beads/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {nb} of {bt.m} bodies ({n} beads): tree + FP64 transforms + Q~v + "
+                      f"Q~^T w, single-threaded C, {dt:.1f} s", "host_cpus": os.cpu_count()}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: the same metric on host cores, each
+    step a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    bt, desc = make_workload(args.workload, seed=0)
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    nb, _ = oracle_sample(bt, per_step)
+    rng = np.random.default_rng(3)
+    for _ in range(args.warmup):
+        _oracle_step(bt, nb, rng)
+    t0 = time.perf_counter()
+    n_tot = 0
+    for _ in range(args.steps):
+        n_tot += _oracle_step(bt, nb, rng)
+    dt = time.perf_counter() - t0
+    val = n_tot / dt
+    return {"metric": METRIC, "value": val, "unit": "beads/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded numpy generators; no dataset)",
+            "config": {"workload": desc, "m": bt.m, "N": bt.N, "sample_bodies": nb},
+            "cpu_baseline": {"value": val, "unit": "beads/s", "kind": "oracle", "cores": 1,
+                             "sample": f"first {nb} of {bt.m} bodies per step, single-threaded C"},
+            "e2e": {"value": val, "unit": "beads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_ours(args, world, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -123,6 +123,40 @@ zq_status zq_apply_Q(zq_ctx *ctx, zq_prec prec, int64_t k, const void *v, int64_
 zq_status zq_apply_QT(zq_ctx *ctx, zq_prec prec, int64_t k, const void *w, int64_t ldw,
                       void *out, int64_t ldo);
 
+/* One step of the whole path for m bodies: the tree (Sec. 2.1), the FP64
+ * node transforms (Sec. 3), then qv = Q~ v and qtw = Q~^T w (Algorithms 2
+ * and 3) for one column each, in the precision `prec` (ZQ_FP32: v, qv, w,
+ * qtw are float*; ZQ_FP64: double*).  Layouts as above (v, qtw: 3 planes of
+ * N; qv, w: R values).  v/qv or w/qtw may both be NULL to skip that product.
+ * flags:
+ *   ZQ_HOST_BUFFERS  x, y, z, v, w, qv, qtw are HOST pointers (pinned for
+ *                    asynchronous copies); the context stages them through
+ *                    device buffers it owns (allocated on first use).
+ *   ZQ_KEEP_TREE     keep the current tree (same bodies, beads moved):
+ *                    only the transforms are rebuilt; m and off must match.
+ * Asynchronous; the results are ready after zq_sync.  When m, off and
+ * tile_beads equal the previous call's, no host synchronisation happens
+ * and the call can be captured into a CUDA graph (device buffers only). */
+#define ZQ_HOST_BUFFERS 1
+#define ZQ_KEEP_TREE 2
+zq_status zq_pipeline(zq_ctx *ctx, zq_prec prec, int64_t m, const int64_t *off, const double *x,
+                      const double *y, const double *z, const void *v, void *qv, const void *w,
+                      void *qtw, int32_t tile_beads, int32_t flags);
+
+/* Measurement hook: while set, every launch of the named kernel is
+ * bracketed by cudaEventRecord(start_event) / cudaEventRecord(stop_event)
+ * (cudaEvent_t handles owned by the caller) on the context's stream, also
+ * inside a CUDA-graph capture.  Names: "aabb", "keys", "sort_small",
+ * "sort_radix", "sort_radix_count", "lcp", "bottom_up", "scan", "classify",
+ * "build_tiles", "build_top", "up_tiles", "up_top", "down_top",
+ * "down_tiles" (a name shared by several launches brackets the last of
+ * them).  name = NULL clears it. */
+zq_status zq_time_kernel(zq_ctx *ctx, const char *name, void *start_event, void *stop_event);
+
+/* Number of kernels this context has launched since it was created (for
+ * launch accounting in measurements). */
+zq_status zq_launch_count(const zq_ctx *ctx, int64_t *launches);
+
 /* Wait for the context's stream; return the first deferred device error
  * (ZQ_ENONFINITE, ZQ_WDEGENERATE) recorded since the last zq_sync, then
  * clear it. */

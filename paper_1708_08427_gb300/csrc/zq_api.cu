@@ -1,4 +1,6 @@
 // zq_api.cu -- the C ABI declared in include/zq.h.
+#include <algorithm>
+#include <cstring>
 #include <new>
 
 #include "zq_internal.cuh"
@@ -27,13 +29,14 @@ void free_all(Ctx& c) {
   void* ps[] = {c.off, c.small_d, c.top_d, c.aabb, c.root, c.key, c.skey, c.perm, c.key_tmp,
                 c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height, c.parent,
                 c.flag, c.roff, c.scan_tmp, c.tiles, c.top, c.counters, c.st64, c.rec64, c.rec32,
-                c.x64, c.x32};
+                c.x64, c.x32, c.stage};
   for (void* p : ps)
     if (p) cudaFree(p);
   Ctx fresh;
   fresh.device = c.device;
   fresh.stream = c.stream;
   fresh.num_sms = c.num_sms;
+  fresh.launches = c.launches;
   c = fresh;
 }
 
@@ -145,6 +148,14 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
   if (N > 700000000LL) return ZQ_EINVAL;
   Ctx& c = ctx->c;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  // Same bodies and tile as the previous tree: reuse the launch plan (no
+  // host synchronisation, so the call can be captured in a CUDA graph).
+  if (c.have_tree && m == c.m && tile_beads == c.tile &&
+      std::equal(off, off + m + 1, c.off_h.begin())) {
+    c.have_xform = false;
+    ZQ_TRY(zq::launch_tree(c, x, y, z));
+    return ZQ_OK;
+  }
   const int64_t nblk = (max_big + 4095) / 4096;
   const int64_t hist_words = 16 * nblk + zq::scan_tmp_words(16 * nblk);
   ZQ_TRY(ensure_capacity(c, N, m, hist_words));
@@ -229,6 +240,84 @@ zq_status zq_apply_QT(zq_ctx* ctx, zq_prec prec, int64_t k, const void* w, int64
     char* oi = static_cast<char*>(out) + (size_t)col * ldo * es;
     ZQ_TRY(zq::launch_apply_QT(c, prec, wi, oi, ldo));
   }
+  return ZQ_OK;
+}
+
+zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
+                      const double* y, const double* z, const void* v, void* qv, const void* w,
+                      void* qtw, int32_t tile_beads, int32_t flags) {
+  if (!ctx || !off || !x || !y || !z || m < 1) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
+  if ((v == nullptr) != (qv == nullptr) || (w == nullptr) != (qtw == nullptr)) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  const bool host = (flags & ZQ_HOST_BUFFERS) != 0;
+  const bool keep = (flags & ZQ_KEEP_TREE) != 0;
+  if (keep && (!c.have_tree || m != c.m || !std::equal(off, off + m + 1, c.off_h.begin())))
+    return ZQ_ESTATE;
+  const int64_t N = off[m], R = 3 * N - 6 * m;
+  const size_t es = prec == ZQ_FP64 ? sizeof(double) : sizeof(float);
+  const double *dx = x, *dy = y, *dz = z;
+  const void *dv = v, *dw = w;
+  void *dqv = qv, *dqtw = qtw;
+  if (host) {
+    // staging layout: x y z (N doubles each) | v (3N) | qtw (3N) | w (R) | qv (R)
+    const int64_t bytes = 3 * N * 8 + (int64_t)es * (6 * N + 2 * R);
+    if (bytes > c.stage_cap) {
+      if (c.stage) cudaFree(c.stage);
+      c.stage = nullptr;
+      c.stage_cap = 0;
+      if (cudaMalloc(&c.stage, (size_t)bytes) != cudaSuccess) return ZQ_ENOMEM;
+      c.stage_cap = bytes;
+    }
+    char* p = static_cast<char*>(c.stage);
+    double* sx = reinterpret_cast<double*>(p);
+    double* sy = sx + N;
+    double* sz = sy + N;
+    char* sv = reinterpret_cast<char*>(sz + N);
+    char* sqtw = sv + 3 * N * es;
+    char* sw = sqtw + 3 * N * es;
+    char* sqv = sw + R * es;
+    ZQ_CUDA_TRY(cudaMemcpyAsync(sx, x, N * 8, cudaMemcpyHostToDevice, c.stream));
+    ZQ_CUDA_TRY(cudaMemcpyAsync(sy, y, N * 8, cudaMemcpyHostToDevice, c.stream));
+    ZQ_CUDA_TRY(cudaMemcpyAsync(sz, z, N * 8, cudaMemcpyHostToDevice, c.stream));
+    if (v) ZQ_CUDA_TRY(cudaMemcpyAsync(sv, v, 3 * N * es, cudaMemcpyHostToDevice, c.stream));
+    if (w) ZQ_CUDA_TRY(cudaMemcpyAsync(sw, w, R * es, cudaMemcpyHostToDevice, c.stream));
+    dx = sx; dy = sy; dz = sz;
+    dv = v ? sv : nullptr;
+    dw = w ? sw : nullptr;
+    dqv = qv ? sqv : nullptr;
+    dqtw = qtw ? sqtw : nullptr;
+  }
+  if (!keep) ZQ_TRY(zq_build_tree_batched(ctx, m, off, dx, dy, dz, tile_beads));
+  ZQ_TRY(zq_build_transforms(ctx, dx, dy, dz));
+  if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
+  if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));
+  if (host) {
+    if (qv) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));
+    if (qtw) ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
+  }
+  return ZQ_OK;
+}
+
+zq_status zq_time_kernel(zq_ctx* ctx, const char* name, void* start_event, void* stop_event) {
+  if (!ctx) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!name) {
+    c.time_name[0] = 0;
+    c.time_ev0 = c.time_ev1 = nullptr;
+    return ZQ_OK;
+  }
+  if (!start_event || !stop_event || std::strlen(name) >= sizeof(c.time_name)) return ZQ_EINVAL;
+  std::strncpy(c.time_name, name, sizeof(c.time_name) - 1);
+  c.time_ev0 = static_cast<cudaEvent_t>(start_event);
+  c.time_ev1 = static_cast<cudaEvent_t>(stop_event);
+  return ZQ_OK;
+}
+
+zq_status zq_launch_count(const zq_ctx* ctx, int64_t* launches) {
+  if (!ctx || !launches) return ZQ_EINVAL;
+  *launches = ctx->c.launches;
   return ZQ_OK;
 }
 

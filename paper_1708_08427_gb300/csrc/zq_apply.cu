@@ -365,10 +365,14 @@ zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out) {
   ApplyArgs<T> a = make_args<T>(c, rec, xs, v, out);
   const size_t smem = tile_smem<T>(c.tile);
   ZQ_CUDA_TRY(cudaFuncSetAttribute(k_up_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  time_begin(c, "up_tiles");
   k_up_tiles<T><<<c.num_sms * 4, kThreads, smem, c.stream>>>(a, c.tile);
+  time_end(c, "up_tiles");
   ZQ_CUDA_TRY(cudaGetLastError());
   if (!c.top_bodies.empty()) {
+    time_begin(c, "up_top");
     k_up_top<T><<<(unsigned)c.top_bodies.size(), kThreads, 0, c.stream>>>(a);
+    time_end(c, "up_top");
     ZQ_CUDA_TRY(cudaGetLastError());
   }
   return ZQ_OK;
@@ -378,12 +382,16 @@ template <typename T>
 zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out) {
   ApplyArgs<T> a = make_args<T>(c, rec, xs, w, out);
   if (!c.top_bodies.empty()) {
+    time_begin(c, "down_top");
     k_down_top<T><<<(unsigned)c.top_bodies.size(), kThreads, 0, c.stream>>>(a);
+    time_end(c, "down_top");
     ZQ_CUDA_TRY(cudaGetLastError());
   }
   const size_t smem = tile_smem<T>(c.tile);
   ZQ_CUDA_TRY(cudaFuncSetAttribute(k_down_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  time_begin(c, "down_tiles");
   k_down_tiles<T><<<c.num_sms * 4, kThreads, smem, c.stream>>>(a, c.tile);
+  time_end(c, "down_tiles");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }

@@ -294,10 +294,14 @@ zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z
   a.st64 = c.st64; a.rec64 = c.rec64; a.rec32 = c.rec32; a.err = c.counters + 2;
   const size_t smem = (size_t)c.tile * sizeof(uint16_t);
   const int grid = c.num_sms * 8;
+  time_begin(c, "build_tiles");
   k_build_tiles<<<grid, kThreads, smem, c.stream>>>(a);
+  time_end(c, "build_tiles");
   ZQ_CUDA_TRY(cudaGetLastError());
   if (!c.top_bodies.empty()) {
+    time_begin(c, "build_top");
     k_build_top<<<(unsigned)c.top_bodies.size(), kThreads, 0, c.stream>>>(a);
+    time_end(c, "build_top");
     ZQ_CUDA_TRY(cudaGetLastError());
   }
   return ZQ_OK;

@@ -81,7 +81,24 @@ struct Ctx {
   // sweep scratch: Info-sets / Velocity-sets of nodes outside the tiles
   double* x64 = nullptr;         // [nodes * 6]
   float* x32 = nullptr;          // [nodes * 6]
+  // staging for host-buffer calls (bytes)
+  void* stage = nullptr;
+  int64_t stage_cap = 0;
+  // kernel timing hook
+  char time_name[32] = {0};
+  cudaEvent_t time_ev0 = nullptr, time_ev1 = nullptr;
+  int64_t launches = 0;  // kernels launched by this context
 };
+
+// Every kernel launch goes through time_begin / time_end: counts the launch
+// and brackets it with the caller's events when it is the timed kernel.
+inline void time_begin(Ctx& c, const char* name) {
+  ++c.launches;
+  if (c.time_ev0 && __builtin_strcmp(c.time_name, name) == 0) cudaEventRecord(c.time_ev0, c.stream);
+}
+inline void time_end(const Ctx& c, const char* name) {
+  if (c.time_ev1 && __builtin_strcmp(c.time_name, name) == 0) cudaEventRecord(c.time_ev1, c.stream);
+}
 
 // --------------------------------------------------------------- helpers
 __host__ __device__ inline bool is_leaf(int32_t code) { return code < 0; }
@@ -128,8 +145,8 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
 // zq_sort.cu
 zq_status launch_sort(Ctx& c);
 // zq_scan.cu
-zq_status launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
-                                int32_t* total, cudaStream_t s);
+zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                                int32_t* total);
 int64_t scan_tmp_words(int64_t n);
 // zq_build.cu
 zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z);

@@ -93,16 +93,23 @@ int64_t scan_tmp_words(int64_t n) { return (n + kTileN - 1) / kTileN + 1; }
 
 // out[i] = sum_{k<i} in[k]; *total (device, may be NULL) = sum of all.
 // in and out may alias.  tmp: scan_tmp_words(n) ints of device scratch.
-zq_status launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
-                                int32_t* total, cudaStream_t s) {
+zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                                int32_t* total) {
+  cudaStream_t s = c.stream;
   if (n <= 0) {
     if (total) ZQ_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(int32_t), s));
     return ZQ_OK;
   }
   int64_t nb = (n + kTileN - 1) / kTileN;
+  time_begin(c, "scan");
   k_block_totals<<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp);
+  time_end(c, "scan");
+  time_begin(c, "scan");
   k_scan_totals<<<1, kThreads, 0, s>>>(tmp, nb, total);
+  time_end(c, "scan");
+  time_begin(c, "scan");
   k_block_scan<<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp, out);
+  time_end(c, "scan");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }

@@ -153,8 +153,10 @@ zq_status launch_sort(Ctx& c) {
     smem = (size_t)P * (sizeof(uint64_t) + sizeof(uint16_t));
     ZQ_CUDA_TRY(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
+    time_begin(c, "sort_small");
     k_sort_small<<<(unsigned)c.small_bodies.size(), kSortThreads, smem, s>>>(c.off, c.small_d, c.key,
                                                                           c.skey, c.perm);
+    time_end(c, "sort_small");
     ZQ_CUDA_TRY(cudaGetLastError());
   }
   for (int32_t j : c.big_bodies) {
@@ -175,11 +177,15 @@ zq_status launch_sort(Ctx& c) {
         kin = c.skey + o; vin = c.perm + o; kout = c.key_tmp + o; vout = c.perm_tmp + o;
       }
       int shift = 4 * pass;
+      time_begin(c, "sort_radix_count");
       k_radix_count<<<(unsigned)nblk, kRadixThreads, 0, s>>>(kin, n, shift, hist, nblk);
-      zq_status st = launch_exclusive_scan(hist, hist, kDigits * nblk, tmp, nullptr, s);
+      time_end(c, "sort_radix_count");
+      zq_status st = launch_exclusive_scan(c, hist, hist, kDigits * nblk, tmp, nullptr);
       if (st != ZQ_OK) return st;
+      time_begin(c, "sort_radix");
       k_radix_scatter<<<(unsigned)nblk, kRadixThreads, 0, s>>>(kin, vin, n, o, shift, hist, nblk,
                                                               kout, vout);
+      time_end(c, "sort_radix");
       ZQ_CUDA_TRY(cudaGetLastError());
     }
   }

@@ -210,25 +210,37 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   int32_t* err = c.counters + 2;
   ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
   ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
+  time_begin(c, "aabb");
   k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.off, c.m, c.N, lo, hi, err);
+  time_end(c, "aabb");
+  time_begin(c, "keys");
   k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.off, c.m, c.N, lo, hi, c.key);
+  time_end(c, "keys");
   ZQ_CUDA_TRY(cudaGetLastError());
   zq_status st = launch_sort(c);
   if (st != ZQ_OK) return st;
+  time_begin(c, "lcp");
   k_lcp<<<blocks(c.nodes), kThreads, 0, s>>>(c.off, c.m, c.nodes, c.skey, c.perm, c.lcp);
+  time_end(c, "lcp");
   ZQ_CUDA_TRY(cudaMemsetAsync(c.flag, 0, c.nodes * sizeof(int32_t), s));
   ZQ_CUDA_TRY(cudaMemsetAsync(c.parent, 0xff, c.nodes * sizeof(int32_t), s));
+  time_begin(c, "bottom_up");
   k_bottom_up<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.m, c.N, c.lcp, c.cl, c.cr, c.first, c.cnt,
                                                c.height, c.parent, c.flag, c.roff, c.root);
+  time_end(c, "bottom_up");
   ZQ_CUDA_TRY(cudaGetLastError());
-  st = launch_exclusive_scan(c.roff, c.roff, c.nodes, c.scan_tmp, nullptr, s);
+  st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
   if (st != ZQ_OK) return st;
   for (int want_top = 0; want_top < 2; ++want_top) {
+    time_begin(c, "classify");
     k_flags<<<blocks(c.nodes), kThreads, 0, s>>>(c.cnt, c.parent, c.nodes, c.tile, want_top, c.flag);
-    st = launch_exclusive_scan(c.flag, c.flag, c.nodes, c.scan_tmp, c.counters + want_top, s);
+    time_end(c, "classify");
+    st = launch_exclusive_scan(c, c.flag, c.flag, c.nodes, c.scan_tmp, c.counters + want_top);
     if (st != ZQ_OK) return st;
+    time_begin(c, "classify");
     k_compact<<<blocks(c.nodes), kThreads, 0, s>>>(c.cnt, c.parent, c.nodes, c.tile, want_top, c.flag,
                                                    want_top ? c.top : c.tiles);
+    time_end(c, "classify");
     ZQ_CUDA_TRY(cudaGetLastError());
   }
   return ZQ_OK;

@@ -20,6 +20,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "_build" / "libzq.so"
 
 ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE = range(7)
 ZQ_FP64, ZQ_FP32 = 0, 1
+ZQ_HOST_BUFFERS, ZQ_KEEP_TREE = 1, 2
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -69,6 +70,13 @@ def _lib() -> ctypes.CDLL:
         L.zq_get_nodes.argtypes = [_vp, _f64p, _f64p]
         L.zq_get_records.restype = ctypes.c_int
         L.zq_get_records.argtypes = [_vp, _f64p]
+        L.zq_pipeline.restype = ctypes.c_int
+        L.zq_pipeline.argtypes = [_vp, ctypes.c_int, _i64, _i64p, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  ctypes.c_int32, ctypes.c_int32]
+        L.zq_time_kernel.restype = ctypes.c_int
+        L.zq_time_kernel.argtypes = [_vp, ctypes.c_char_p, _vp, _vp]
+        L.zq_launch_count.restype = ctypes.c_int
+        L.zq_launch_count.argtypes = [_vp, _i64p]
         _L = L
     return _L
 
@@ -174,6 +182,36 @@ class Context:
             out = self._torch.empty((k, 3, N), dtype=w.dtype, device=w.device)
         _check(_lib().zq_apply_QT(self._h, self._prec(w), k, _ptr(ww), R, _ptr(out), 3 * N), "zq_apply_QT")
         return out.reshape(3, N) if squeeze else out
+
+    def pipeline(self, off, x, y, z, v=None, qv=None, w=None, qtw=None, tile_beads: int = 0,
+                 host: bool = False, keep_tree: bool = False, prec: int | None = None):
+        """One step: tree, FP64 transforms, qv = Q~ v, qtw = Q~^T w.  With
+        host=True all tensors are (pinned) host tensors staged by the
+        library; otherwise device tensors.  off: numpy int64 (m + 1)."""
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        self._off = off
+        m = off.shape[0] - 1
+        ref = v if v is not None else w
+        if prec is None:
+            prec = self._prec(ref)
+        flags = (ZQ_HOST_BUFFERS if host else 0) | (ZQ_KEEP_TREE if keep_tree else 0)
+        p = lambda t: None if t is None else _ptr(t)
+        _check(_lib().zq_pipeline(self._h, prec, m, off.ctypes.data_as(_i64p), _ptr(x), _ptr(y), _ptr(z),
+                                  p(v), p(qv), p(w), p(qtw), int(tile_beads), flags), "zq_pipeline")
+
+    def time_kernel(self, name: str | None, start=None, stop=None):
+        """Bracket launches of kernel `name` with torch.cuda.Event start/stop
+        (events must have been recorded once so their handles exist)."""
+        if name is None:
+            _check(_lib().zq_time_kernel(self._h, None, None, None), "zq_time_kernel")
+            return
+        _check(_lib().zq_time_kernel(self._h, name.encode(), _vp(start.cuda_event), _vp(stop.cuda_event)),
+               "zq_time_kernel")
+
+    def launch_count(self) -> int:
+        n = _i64()
+        _check(_lib().zq_launch_count(self._h, ctypes.byref(n)), "zq_launch_count")
+        return int(n.value)
 
     def sync(self, allow_degenerate: bool = False):
         allow = (ZQ_OK, ZQ_WDEGENERATE) if allow_degenerate else (ZQ_OK,)
