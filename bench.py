@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["shells2000", "ellipsoid"], default="shells2000")
-    ap.add_argument("--tile", type=int, default=2048)
+    ap.add_argument("--cut", type=int, default=15, help="level cut (performance only)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / apply-only / e2e / CPU legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -186,41 +186,42 @@ def node_census(ctx):
     return {3: int((internal == 0).sum()), 6: int((internal == 1).sum()), 9: int((internal == 2).sum())}
 
 
+# FP64 flops of one node transform (sqrt and division count 1, FMA 2), as
+# counted from the algorithm: geometry (1/n, centroid, offset,
+# sqrt(n_x/n), sqrt(n_y/n), sqrt(n_x n_y/n)) 23; Case I closed form 32;
+# Householder LQ restricted to the nonzero pattern of [T22_x | T22_y | K]:
+# k = 6: K 3, ||M||_F 22, reflectors 29 + 30 + 16; k = 9: K 3, ||M||_F 32,
+# reflectors 40 + 44 + 25.
+BUILD_FLOPS = {3: 23 + 32, 6: 23 + 3 + 22 + 29 + 30 + 16, 9: 23 + 3 + 32 + 40 + 44 + 25}
+
+
 def build_flops(k: int) -> int:
-    """FP64 flops of one node transform as the build computes it (sqrt and
-    division count 1; FMA 2).  Geometry: centroid, offset, sqrt(n_x/n),
-    sqrt(n_y/n), sqrt(n_x n_y/n) = 23.  Case I (k = 3): closed form = 29.
-    k = 6, 9: ||M||_F (6k), then per reflector j with m = k - 1 - j entries
-    below the diagonal: norm 2m + 3, tau 2, scaling m + 1, and per remaining
-    column (2 - j of them) 2m + 2 + 3m."""
-    geo = 23
-    if k == 3:
-        return geo + 29
-    f = 6 * k
-    for j in range(3):
-        m = k - 1 - j
-        f += (2 * m + 3) + 2 + (m + 1) + (2 - j) * (5 * m + 2)
-    return geo + f
+    return BUILD_FLOPS[k]
 
 
-RECORD_FLOATS = {3: 11, 6: 17, 9: 26}  # words of the node record a sweep needs
+# words of the node record a sweep needs: Case I alpha, beta, G (11);
+# k = 6: alpha, beta, 3 tau, 2 + 3 + 3 reflector entries (13); k = 9:
+# alpha, beta, 3 tau, 3 + 5 + 6 (19)
+RECORD_FLOATS = {3: 11, 6: 13, 9: 19}
 
 
 def sweep_bytes(census, N, R, es=4) -> int:
     """Algorithmic DRAM bytes of one sweep (up or down): the bead-vector
     planes (3N) and residues (R) once, each node record once (by k), the
-    node structure (two child codes, residue offset: 12 B; height 1 B) and
-    the sorted-position -> bead map (4 B per bead)."""
+    node structure (two child codes and the residue offset, 12 B) and the
+    sorted-position -> bead map (4 B per bead).  The Info-/Velocity-sets
+    that the implementation passes between heights through global memory
+    are not counted (the method needs them only on chip)."""
     rec = sum(census[k] * RECORD_FLOATS[k] * es for k in census)
     nodes = sum(census.values())
-    return es * (3 * N + R) + rec + 13 * nodes + 4 * N
+    return es * (3 * N + R) + rec + 12 * nodes + 4 * N
 
 
 def kernel_work(name, census, N, R, m, es):
     """(bound, algorithmic amount per launch, unit)."""
-    if name in ("build_tiles", "build_top"):
+    if name in ("build_level", "build_tail"):
         return "alu", sum(census[k] * build_flops(k) for k in census), "flop"
-    if name in ("up_tiles", "down_tiles"):
+    if name in ("up_level", "down_level"):
         return "hbm", sweep_bytes(census, N, R, es), "B"
     if name == "sort_small":
         return "hbm", 8 * N + 8 * N + 4 * N, "B"
@@ -276,7 +277,7 @@ def run_ours(args, world, rank, local):
     ctx = zq.Context(local, stream=stream)
 
     def step(prec_t=torch.float32, vv=v, ww=w, oq=qv, oqt=qtw):
-        ctx.pipeline(bt.off, x, y, z, vv, oq, ww, oqt, tile_beads=args.tile)
+        ctx.pipeline(bt.off, x, y, z, vv, oq, ww, oqt, level_cut=args.cut)
 
     for _ in range(max(args.warmup, 1)):
         step()
@@ -284,8 +285,8 @@ def run_ours(args, world, rank, local):
     census = node_census(ctx)
 
     # --- per-kernel time of one step (measurement hook), picks the dominant kernel
-    names = ["aabb", "keys", "sort_small", "sort_radix", "lcp", "bottom_up", "scan", "classify",
-             "build_tiles", "build_top", "up_tiles", "up_top", "down_top", "down_tiles"]
+    names = ["aabb", "keys", "sort_small", "sort_radix", "lcp", "bottom_up", "scan", "schedule",
+             "build_level", "build_tail", "up_level", "up_tail", "down_tail", "down_level"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e1.record(stream)
@@ -305,7 +306,7 @@ def run_ours(args, world, rank, local):
             tot += e0.elapsed_time(e1)
         ctx.time_kernel(None)
         phases[nm] = tot / reps
-    dominant = max(("build_tiles", "up_tiles", "down_tiles", "sort_small", "bottom_up"),
+    dominant = max(("build_level", "up_level", "down_level", "sort_small", "bottom_up", "keys"),
                    key=lambda k: phases.get(k, 0.0))
 
     # --- the dominant kernel is bracketed by events in every timed step
@@ -379,7 +380,7 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps, f64 transforms",
         "data": "synthetic (seeded numpy generators; no dataset)",
-        "config": {"workload": desc, "m": m, "N": N, "residues": R, "tile_beads": args.tile,
+        "config": {"workload": desc, "m": m, "N": N, "residues": R, "level_cut": args.cut,
                    "graph": False, "prec": "fp32",
                    "step": "tree + FP64 transforms + Q~v + Q~^T w (one C-ABI call, zq_pipeline)",
                    "l2": "512 MB buffer written before every step, outside the step events",
@@ -412,7 +413,7 @@ def fp64_step(args, ctx, bt, stream, flush, rng, world, dev):
     stream.synchronize()
 
     def step():
-        ctx.pipeline(bt.off, *xyz_of(ctx, bt, dev), v, qv, w, qtw, tile_beads=args.tile)
+        ctx.pipeline(bt.off, *xyz_of(ctx, bt, dev), v, qv, w, qtw, level_cut=args.cut)
 
     return timed(args, step, stream, flush, world, dev, N, graph=not args.no_graph)
 
@@ -471,7 +472,7 @@ def apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev):
     N, R, m = bt.N, bt.n_residues, bt.m
     res = {}
     x, y, z = xyz_of(ctx, bt, dev)
-    ctx.pipeline(bt.off, x, y, z, v, qv, w, qtw, tile_beads=args.tile)
+    ctx.pipeline(bt.off, x, y, z, v, qv, w, qtw, level_cut=args.cut)
     stream.synchronize()
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -510,7 +511,7 @@ def e2e(args, ctx, bt, stream, world, dev):
     hqt = torch.empty((3, N), dtype=torch.float32).pin_memory()
 
     def fn():
-        ctx.pipeline(bt.off, hx, hy, hz, hv, hq, hw, hqt, tile_beads=args.tile, host=True)
+        ctx.pipeline(bt.off, hx, hy, hz, hv, hq, hw, hqt, level_cut=args.cut, host=True)
 
     for _ in range(2):
         fn()

@@ -87,18 +87,19 @@ zq_status zq_create(zq_ctx **ctx, int device, void *cuda_stream);
 zq_status zq_destroy(zq_ctx *ctx);
 
 /* Tree of m bodies (Sec. 2.1; readings above).  off: HOST, m+1 entries.
- * x, y, z: DEVICE, N doubles each.  tile_beads: beads per thread-block
- * tile of the sweeps (performance only, results do not depend on it;
- * 0 = default 2048; 64 <= tile_beads <= 4096).  Allocates the context's
+ * x, y, z: DEVICE, N doubles each.  level_cut: the nodes of height
+ * 1..level_cut are processed one height at a time across all bodies, the
+ * nodes above it one thread block per body (performance only, results do
+ * not depend on it; 0 = default 15; 1 <= level_cut <= 21).  Allocates the context's
  * buffers on the first call and whenever m or N grows; a later call with
  * the same sizes reuses them.  Asynchronous; bad coordinates are reported
  * by zq_sync. */
 zq_status zq_build_tree_batched(zq_ctx *ctx, int64_t m, const int64_t *off, const double *x,
-                                const double *y, const double *z, int32_t tile_beads);
+                                const double *y, const double *z, int32_t level_cut);
 
 /* Single-body form: m = 1, off = {0, n}. */
 zq_status zq_build_tree(zq_ctx *ctx, int64_t n, const double *x, const double *y,
-                        const double *z, int32_t tile_beads);
+                        const double *z, int32_t level_cut);
 
 /* Node transforms in FP64 from the coordinates (Sec. 3: centroids,
  * sqrt(n_x/n), sqrt(n_y/n), the LQ of [R22 S22 sqrt(n_x n/n_y) R21] of
@@ -134,23 +135,27 @@ zq_status zq_apply_QT(zq_ctx *ctx, zq_prec prec, int64_t k, const void *w, int64
  *                    device buffers it owns (allocated on first use).
  *   ZQ_KEEP_TREE     keep the current tree (same bodies, beads moved):
  *                    only the transforms are rebuilt; m and off must match.
- * Asynchronous; the results are ready after zq_sync.  When m, off and
- * tile_beads equal the previous call's, no host synchronisation happens
- * and the call can be captured into a CUDA graph (device buffers only). */
+ * Only the transform copy of the requested precision is refreshed, so a
+ * later zq_apply_Q / zq_apply_QT must use the same precision (else
+ * ZQ_ESTATE).  Asynchronous; the results are ready after zq_sync.  When m,
+ * off and level_cut equal the previous call's, no host synchronisation
+ * happens and the call can be captured into a CUDA graph (device buffers
+ * only). */
 #define ZQ_HOST_BUFFERS 1
 #define ZQ_KEEP_TREE 2
 zq_status zq_pipeline(zq_ctx *ctx, zq_prec prec, int64_t m, const int64_t *off, const double *x,
                       const double *y, const double *z, const void *v, void *qv, const void *w,
-                      void *qtw, int32_t tile_beads, int32_t flags);
+                      void *qtw, int32_t level_cut, int32_t flags);
 
 /* Measurement hook: while set, every launch of the named kernel is
  * bracketed by cudaEventRecord(start_event) / cudaEventRecord(stop_event)
  * (cudaEvent_t handles owned by the caller) on the context's stream, also
- * inside a CUDA-graph capture.  Names: "aabb", "keys", "sort_small",
- * "sort_radix", "sort_radix_count", "lcp", "bottom_up", "scan", "classify",
- * "build_tiles", "build_top", "up_tiles", "up_top", "down_top",
- * "down_tiles" (a name shared by several launches brackets the last of
- * them).  name = NULL clears it. */
+ * inside a CUDA-graph capture.  Names: "bead_body", "aabb", "keys",
+ * "sort_small", "sort_radix", "sort_radix_count", "lcp", "bottom_up",
+ * "scan", "schedule", "build_level", "build_tail", "up_level", "up_tail",
+ * "down_tail", "down_level".  When one API call launches the named kernel
+ * several times (one launch per height), start is recorded before its
+ * first launch and stop after its last launch in that call. */
 zq_status zq_time_kernel(zq_ctx *ctx, const char *name, void *start_event, void *stop_event);
 
 /* Number of kernels this context has launched since it was created (for

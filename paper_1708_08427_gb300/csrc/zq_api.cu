@@ -26,10 +26,10 @@ zq_status grow(T** p, int64_t count) {
 }
 
 void free_all(Ctx& c) {
-  void* ps[] = {c.off, c.small_d, c.top_d, c.aabb, c.root, c.key, c.skey, c.perm, c.key_tmp,
-                c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height, c.parent,
-                c.flag, c.roff, c.scan_tmp, c.tiles, c.top, c.counters, c.st64, c.rec64, c.rec32,
-                c.x64, c.x32, c.stage};
+  void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.root, c.root_slot, c.key, c.skey, c.perm,
+                c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
+                c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
+                c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.stage};
   for (void* p : ps)
     if (p) cudaFree(p);
   Ctx fresh;
@@ -51,9 +51,10 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     const int64_t nodes = N;  // >= N - m
     ZQ_TRY(grow(&c.off, m + 1));
     ZQ_TRY(grow(&c.small_d, m));
-    ZQ_TRY(grow(&c.top_d, m));
+    ZQ_TRY(grow(&c.bead_body, N));
     ZQ_TRY(grow(&c.aabb, 6 * m));
     ZQ_TRY(grow(&c.root, m));
+    ZQ_TRY(grow(&c.root_slot, m));
     ZQ_TRY(grow(&c.key, N));
     ZQ_TRY(grow(&c.skey, N));
     ZQ_TRY(grow(&c.perm, N));
@@ -65,16 +66,22 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.first, nodes));
     ZQ_TRY(grow(&c.cnt, nodes));
     ZQ_TRY(grow(&c.height, nodes));
-    ZQ_TRY(grow(&c.parent, nodes));
     ZQ_TRY(grow(&c.flag, nodes));
     ZQ_TRY(grow(&c.roff, nodes));
     ZQ_TRY(grow(&c.scan_tmp, zq::scan_tmp_words(nodes)));
-    ZQ_TRY(grow(&c.tiles, nodes));
-    ZQ_TRY(grow(&c.top, nodes));
     ZQ_TRY(grow(&c.counters, 4));
+    ZQ_TRY(grow(&c.sid, nodes));
+    ZQ_TRY(grow(&c.slot_of, nodes));
+    ZQ_TRY(grow(&c.sc, nodes));
+    ZQ_TRY(grow(&c.sroff, nodes));
+    ZQ_TRY(grow(&c.scnt, nodes));
+    ZQ_TRY(grow(&c.sheight, nodes));
+    ZQ_TRY(grow(&c.bstart, zq::kMaxBuckets + 1));
+    ZQ_TRY(grow(&c.brec, zq::kMaxBuckets + 1));
+    ZQ_TRY(grow(&c.bhist, zq::bucket_hist_words(nodes)));
     ZQ_TRY(grow(&c.st64, nodes * zq::kState));
-    ZQ_TRY(grow(&c.rec64, nodes * zq::kRec));
-    ZQ_TRY(grow(&c.rec32, nodes * zq::kRec));
+    ZQ_TRY(grow(&c.rec64, nodes * zq::kRecMax));
+    ZQ_TRY(grow(&c.rec32, nodes * zq::kRecMax));
     ZQ_TRY(grow(&c.x64, nodes * 6));
     ZQ_TRY(grow(&c.x32, nodes * 6));
     ZQ_CUDA_TRY(cudaMemsetAsync(c.counters, 0, 4 * sizeof(int32_t), c.stream));
@@ -133,10 +140,10 @@ zq_status zq_destroy(zq_ctx* ctx) {
 }
 
 zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, const double* x,
-                                const double* y, const double* z, int32_t tile_beads) {
+                                const double* y, const double* z, int32_t level_cut) {
   if (!ctx || !off || !x || !y || !z || m < 1) return ZQ_EINVAL;
-  if (tile_beads == 0) tile_beads = zq::kDefaultTile;
-  if (tile_beads < 64 || tile_beads > zq::kMaxTile) return ZQ_EINVAL;
+  if (level_cut == 0) level_cut = zq::kDefaultCut;
+  if (level_cut < 1 || level_cut > zq::kMaxCut) return ZQ_EINVAL;
   if (off[0] != 0) return ZQ_EINVAL;
   int64_t max_big = 0;
   for (int64_t j = 0; j < m; ++j) {
@@ -147,10 +154,11 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
   const int64_t N = off[m];
   if (N > 700000000LL) return ZQ_EINVAL;
   Ctx& c = ctx->c;
+  c.time_started = false;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
-  // Same bodies and tile as the previous tree: reuse the launch plan (no
+  // Same bodies and level cut as the previous tree: reuse the launch plan (no
   // host synchronisation, so the call can be captured in a CUDA graph).
-  if (c.have_tree && m == c.m && tile_beads == c.tile &&
+  if (c.have_tree && m == c.m && level_cut == c.cut &&
       std::equal(off, off + m + 1, c.off_h.begin())) {
     c.have_xform = false;
     ZQ_TRY(zq::launch_tree(c, x, y, z));
@@ -163,13 +171,12 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
   c.m = m;
   c.nodes = N - m;
   c.R = 3 * N - 6 * m;
-  c.tile = tile_beads;
+  c.cut = level_cut;
   c.have_tree = false;
   c.have_xform = false;
   c.off_h.assign(off, off + m + 1);
   c.small_bodies.clear();
   c.big_bodies.clear();
-  c.top_bodies.clear();
   c.max_small = 0;
   for (int64_t j = 0; j < m; ++j) {
     const int64_t n = off[j + 1] - off[j];
@@ -179,35 +186,34 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
     } else {
       c.big_bodies.push_back((int32_t)j);
     }
-    if (n > c.tile) c.top_bodies.push_back((int32_t)j);
   }
   ZQ_CUDA_TRY(cudaMemcpyAsync(c.off, off, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
   if (!c.small_bodies.empty())
     ZQ_CUDA_TRY(cudaMemcpyAsync(c.small_d, c.small_bodies.data(), c.small_bodies.size() * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, c.stream));
-  if (!c.top_bodies.empty())
-    ZQ_CUDA_TRY(cudaMemcpyAsync(c.top_d, c.top_bodies.data(), c.top_bodies.size() * sizeof(int32_t),
-                                cudaMemcpyHostToDevice, c.stream));
   // the host vectors are read by the copies above: keep them alive until then
   ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  ZQ_TRY(zq::launch_bead_body(c));
   ZQ_TRY(zq::launch_tree(c, x, y, z));
   c.have_tree = true;
   return ZQ_OK;
 }
 
 zq_status zq_build_tree(zq_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
-                        int32_t tile_beads) {
+                        int32_t level_cut) {
   const int64_t off[2] = {0, n};
-  return zq_build_tree_batched(ctx, 1, off, x, y, z, tile_beads);
+  return zq_build_tree_batched(ctx, 1, off, x, y, z, level_cut);
 }
 
 zq_status zq_build_transforms(zq_ctx* ctx, const double* x, const double* y, const double* z) {
   if (!ctx || !x || !y || !z) return ZQ_EINVAL;
   Ctx& c = ctx->c;
+  c.time_started = false;
   if (!c.have_tree) return ZQ_ESTATE;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
-  ZQ_TRY(zq::launch_build(c, x, y, z));
+  ZQ_TRY(zq::launch_build(c, x, y, z, 3));
   c.have_xform = true;
+  c.have64 = c.have32 = true;
   return ZQ_OK;
 }
 
@@ -216,7 +222,8 @@ zq_status zq_apply_Q(zq_ctx* ctx, zq_prec prec, int64_t k, const void* v, int64_
   if (!ctx || !v || !out || k < 1) return ZQ_EINVAL;
   if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
   Ctx& c = ctx->c;
-  if (!c.have_xform) return ZQ_ESTATE;
+  c.time_started = false;
+  if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
   if (ldv < 3 * c.N || ldo < c.R) return ZQ_EINVAL;
   const size_t es = prec == ZQ_FP64 ? sizeof(double) : sizeof(float);
   for (int64_t col = 0; col < k; ++col) {
@@ -232,7 +239,8 @@ zq_status zq_apply_QT(zq_ctx* ctx, zq_prec prec, int64_t k, const void* w, int64
   if (!ctx || !w || !out || k < 1) return ZQ_EINVAL;
   if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
   Ctx& c = ctx->c;
-  if (!c.have_xform) return ZQ_ESTATE;
+  c.time_started = false;
+  if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
   if (ldw < c.R || ldo < 3 * c.N) return ZQ_EINVAL;
   const size_t es = prec == ZQ_FP64 ? sizeof(double) : sizeof(float);
   for (int64_t col = 0; col < k; ++col) {
@@ -245,11 +253,12 @@ zq_status zq_apply_QT(zq_ctx* ctx, zq_prec prec, int64_t k, const void* w, int64
 
 zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
                       const double* y, const double* z, const void* v, void* qv, const void* w,
-                      void* qtw, int32_t tile_beads, int32_t flags) {
+                      void* qtw, int32_t level_cut, int32_t flags) {
   if (!ctx || !off || !x || !y || !z || m < 1) return ZQ_EINVAL;
   if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
   if ((v == nullptr) != (qv == nullptr) || (w == nullptr) != (qtw == nullptr)) return ZQ_EINVAL;
   Ctx& c = ctx->c;
+  c.time_started = false;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
   const bool host = (flags & ZQ_HOST_BUFFERS) != 0;
   const bool keep = (flags & ZQ_KEEP_TREE) != 0;
@@ -289,8 +298,12 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
     dqv = qv ? sqv : nullptr;
     dqtw = qtw ? sqtw : nullptr;
   }
-  if (!keep) ZQ_TRY(zq_build_tree_batched(ctx, m, off, dx, dy, dz, tile_beads));
-  ZQ_TRY(zq_build_transforms(ctx, dx, dy, dz));
+  if (!keep) ZQ_TRY(zq_build_tree_batched(ctx, m, off, dx, dy, dz, level_cut));
+  // only the records of the precision the sweeps use
+  ZQ_TRY(zq::launch_build(c, dx, dy, dz, prec == ZQ_FP64 ? 1 : 2));
+  c.have_xform = true;
+  c.have64 = prec == ZQ_FP64;
+  c.have32 = prec == ZQ_FP32;
   if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
   if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));
   if (host) {
@@ -376,9 +389,11 @@ zq_status zq_get_nodes(zq_ctx* ctx, double* centroid, double* T22) {
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
   ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
   std::vector<double> st((size_t)c.nodes * zq::kState);
+  std::vector<int32_t> slot((size_t)c.nodes);
   ZQ_CUDA_TRY(cudaMemcpy(st.data(), c.st64, st.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemcpy(slot.data(), c.slot_of, slot.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
   for (int64_t q = 0; q < c.nodes; ++q) {
-    const double* s = st.data() + (size_t)q * zq::kState;
+    const double* s = st.data() + (size_t)slot[(size_t)q] * zq::kState;
     if (centroid)
       for (int a = 0; a < 3; ++a) centroid[3 * q + a] = s[a];
     if (T22)
@@ -390,11 +405,50 @@ zq_status zq_get_nodes(zq_ctx* ctx, double* centroid, double* T22) {
 zq_status zq_get_records(zq_ctx* ctx, double* rec) {
   if (!ctx || !rec) return ZQ_EINVAL;
   Ctx& c = ctx->c;
-  if (!c.have_xform) return ZQ_ESTATE;
+  if (!c.have_xform || !c.have64) return ZQ_ESTATE;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
   ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
-  ZQ_CUDA_TRY(cudaMemcpy(rec, c.rec64, (size_t)c.nodes * zq::kRec * sizeof(double),
-                         cudaMemcpyDeviceToHost));
+  const size_t nodes = (size_t)c.nodes;
+  const int nb = 3 * c.cut + 1;
+  std::vector<double> cr(nodes * zq::kRecMax);
+  std::vector<int32_t> sid(nodes), bstart(nb + 1), brec(nb + 1);
+  std::vector<int2> sc(nodes);
+  ZQ_CUDA_TRY(cudaMemcpy(cr.data(), c.rec64, cr.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemcpy(sid.data(), c.sid, nodes * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemcpy(sc.data(), c.sc, nodes * sizeof(int2), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemcpy(bstart.data(), c.bstart, (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemcpy(brec.data(), c.brec, (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  // compact (by slot) -> dense documented layout (by node id)
+  static const int rows6[3][3] = {{4, 5, -1}, {3, 4, 5}, {3, 4, 5}};
+  static const int rows9[3][6] = {{3, 7, 8, -1, -1, -1}, {3, 4, 6, 7, 8, -1}, {3, 4, 5, 6, 7, 8}};
+  static const int off6[3] = {5, 7, 10}, off9[3] = {5, 8, 13};
+  int b = 0;
+  for (size_t s = 0; s < nodes; ++s) {
+    while (b < nb - 1 && (int32_t)s >= bstart[b + 1]) ++b;
+    const int type = (sc[s].x >= 0) + (sc[s].y >= 0);
+    const bool tail = b == nb - 1;
+    const size_t rw = (size_t)brec[b] + (s - (size_t)bstart[b]) * (tail ? zq::kRecMax : zq::rec_words(type));
+    const double* r = cr.data() + rw;
+    double* d = rec + (size_t)sid[s] * zq::kRec;
+    for (int i = 0; i < zq::kRec; ++i) d[i] = 0.0;
+    d[0] = r[0];
+    d[1] = r[1];
+    if (type == 0) {
+      for (int i = 0; i < 9; ++i) d[5 + i] = r[2 + i];
+      continue;
+    }
+    const int k = type == 1 ? 6 : 9;
+    for (int j = 0; j < 3; ++j) d[2 + j] = r[2 + j];
+    int tail_at = 5;
+    for (int j = 0; j < 3; ++j) {
+      const int nv = type == 1 ? (j == 0 ? 2 : 3) : (j == 0 ? 3 : (j == 1 ? 5 : 6));
+      for (int i = 0; i < nv; ++i) {
+        const int row = type == 1 ? rows6[j][i] : rows9[j][i];
+        d[tail_at + row - j - 1] = r[(type == 1 ? off6[j] : off9[j]) + i];
+      }
+      tail_at += k - 1 - j;
+    }
+  }
   return ZQ_OK;
 }
 

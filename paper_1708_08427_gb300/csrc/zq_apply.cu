@@ -13,12 +13,13 @@
 // and a leaf's velocity is the first three entries of its Velocity-set.
 //
 // G is applied as its three Householder reflectors (G u = H3 H2 H1 u,
-// G^T z = H1 H2 H3 z), or as the explicit 3 x 3 matrix for Case I.
+// G^T z = H1 H2 H3 z) restricted to their possibly nonzero rows, or as the
+// explicit 3 x 3 matrix for Case I.
 //
-// Work split: one thread block per tile (a subtree of at most `tile`
-// beads), level by level with the Info-/Velocity-sets in shared memory;
-// nodes above the tiles are handled by one block per body, their sets in
-// global scratch.  Upward: tiles, then tops.  Downward: tops, then tiles.
+// Schedule: heights 1..cut level by level over all bodies (records and
+// Info-/Velocity-sets of a height are contiguous; one launch per height),
+// the nodes above the cut one thread block per body.  Upward: levels then
+// tails; downward: tails then levels.
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -29,126 +30,57 @@ constexpr int kThreads = 256;
 
 template <typename T>
 struct ApplyArgs {
-  const int64_t* off;
-  int64_t m;
   int64_t N;
+  const int64_t* off;
   const int32_t* perm;
-  const int32_t* cl;
-  const int32_t* cr;
-  const int32_t* cnt;
-  const int32_t* first;
-  const int32_t* roff;
-  const uint8_t* height;
-  const int32_t* tiles;
-  const int32_t* top;
-  const int32_t* counters;
-  const int32_t* top_bodies;
-  const int32_t* root;
+  const int2* sc;
+  const int32_t* sroff;
+  const uint8_t* sheight;
+  const int32_t* sid;
+  const int32_t* bstart;
+  const int32_t* brec;
+  const int32_t* root_slot;
+  int cut;
   const T* rec;
-  T* xs;          // Info-/Velocity-sets of tile roots and top nodes [nodes * 6]
-  const T* in;    // up: bead planes; down: residues
-  T* out;         // up: residues; down: bead planes
+  T* xs;        // Info-/Velocity-sets by slot [nodes * 6]
+  const T* in;  // up: bead planes; down: residues
+  T* out;       // up: residues; down: bead planes
 };
 
-// ---------------------------------------------------------- reflectors
-// u <- H_j u for the reflector with tail v (entries j+1..K-1), v_j = 1.
-template <typename T, int K, int J>
-__device__ __forceinline__ void reflect(const T* __restrict__ rec, int tail, T tau, T (&u)[9]) {
-  T w = u[J];
-#pragma unroll
-  for (int i = J + 1; i < K; ++i) w += rec[tail + i - J - 1] * u[i];
-  w *= tau;
-  u[J] -= w;
-#pragma unroll
-  for (int i = J + 1; i < K; ++i) u[i] -= w * rec[tail + i - J - 1];
-}
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double2; };
 
-template <typename T, int K>
-__device__ __forceinline__ void g_apply(const T* __restrict__ rec, T (&u)[9]) {
-  reflect<T, K, 0>(rec, 5, rec[2], u);
-  reflect<T, K, 1>(rec, 5 + K - 1, rec[3], u);
-  reflect<T, K, 2>(rec, 5 + 2 * K - 3, rec[4], u);
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void gt_apply(const T* __restrict__ rec, T (&u)[9]) {
-  reflect<T, K, 2>(rec, 5 + 2 * K - 3, rec[4], u);
-  reflect<T, K, 1>(rec, 5 + K - 1, rec[3], u);
-  reflect<T, K, 0>(rec, 5, rec[2], u);
-}
-
-// ------------------------------------------------------------ node ops
-// in: tx, ty (translational Info-sets), rx / ry (rotational, internal
-// children only).  out: t, r; residues to res[0 .. k-4].
-template <typename T>
-__device__ __forceinline__ void up_node(const T* __restrict__ rec, bool xi, bool yi, const T* tx,
-                                        const T* rx, const T* ty, const T* ry, T* t, T* r,
-                                        T* __restrict__ res) {
-  const T al = rec[0], be = rec[1];
-  T u[9];
-  int k = 0;
-  if (xi) { u[0] = rx[0]; u[1] = rx[1]; u[2] = rx[2]; k = 3; }
-  if (yi) { u[k] = ry[0]; u[k + 1] = ry[1]; u[k + 2] = ry[2]; k += 3; }
+// Load W words of a record (16-byte vector loads, read-only path).
+template <typename T, int W>
+__device__ __forceinline__ void load_rec(const T* __restrict__ g, T (&r)[W]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(g);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    t[a] = al * tx[a] + be * ty[a];
-    u[k + a] = be * tx[a] - al * ty[a];
-  }
-  if (!xi && !yi) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) r[i] = rec[5 + 3 * i] * u[0] + rec[6 + 3 * i] * u[1] + rec[7 + 3 * i] * u[2];
-    return;
-  }
-  if (xi && yi) {
-    g_apply<T, 9>(rec, u);
-#pragma unroll
-    for (int i = 3; i < 9; ++i) res[i - 3] = u[i];
+    for (int i = 0; i < W / 4; ++i) {
+      const float4 q = __ldg(p + i);
+      r[4 * i] = q.x; r[4 * i + 1] = q.y; r[4 * i + 2] = q.z; r[4 * i + 3] = q.w;
+    }
   } else {
-    g_apply<T, 6>(rec, u);
+    const double2* p = reinterpret_cast<const double2*>(g);
 #pragma unroll
-    for (int i = 3; i < 6; ++i) res[i - 3] = u[i];
-  }
-  r[0] = u[0]; r[1] = u[1]; r[2] = u[2];
-}
-
-// in: Velocity-set Lp (6), residue coefficients w (k-3).  out: Lx, Ly (6
-// each; entries 3..5 meaningful only for internal children).
-template <typename T>
-__device__ __forceinline__ void down_node(const T* __restrict__ rec, bool xi, bool yi, const T* Lp,
-                                          const T* __restrict__ w, T* Lx, T* Ly) {
-  const T al = rec[0], be = rec[1];
-  T z[9];
-  z[0] = Lp[3]; z[1] = Lp[4]; z[2] = Lp[5];
-  T sg[3];
-  if (!xi && !yi) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) sg[j] = rec[5 + j] * z[0] + rec[8 + j] * z[1] + rec[11 + j] * z[2];
-  } else if (xi && yi) {
-#pragma unroll
-    for (int i = 3; i < 9; ++i) z[i] = w[i - 3];
-    gt_apply<T, 9>(rec, z);
-    Lx[3] = z[0]; Lx[4] = z[1]; Lx[5] = z[2];
-    Ly[3] = z[3]; Ly[4] = z[4]; Ly[5] = z[5];
-    sg[0] = z[6]; sg[1] = z[7]; sg[2] = z[8];
-  } else {
-#pragma unroll
-    for (int i = 3; i < 6; ++i) z[i] = w[i - 3];
-    gt_apply<T, 6>(rec, z);
-    T* a = xi ? Lx : Ly;
-    a[3] = z[0]; a[4] = z[1]; a[5] = z[2];
-    sg[0] = z[3]; sg[1] = z[4]; sg[2] = z[5];
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    Lx[i] = al * Lp[i] + be * sg[i];
-    Ly[i] = be * Lp[i] - al * sg[i];
+    for (int i = 0; i < W / 2; ++i) {
+      const double2 q = __ldg(p + i);
+      r[2 * i] = q.x; r[2 * i + 1] = q.y;
+    }
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void load_rec(const T* __restrict__ g, T* r) {
+__device__ __forceinline__ void load6(const T* __restrict__ p, T* v) {
 #pragma unroll
-  for (int i = 0; i < kRec; ++i) r[i] = __ldg(g + i);
+  for (int i = 0; i < 6; ++i) v[i] = p[i];
+}
+
+template <typename T>
+__device__ __forceinline__ void store6(T* __restrict__ p, const T* v) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[i] = v[i];
 }
 
 template <typename T>
@@ -167,231 +99,269 @@ __device__ __forceinline__ void store_bead(const ApplyArgs<T>& a, int32_t code, 
   a.out[2 * a.N + i] = L[2];
 }
 
-__device__ int make_levels(const uint8_t* __restrict__ hgt, int nn, uint16_t* list, int* lstart,
-                           int* lcnt, int* hmax) {
-  for (int i = threadIdx.x; i < kMaxHeight + 2; i += blockDim.x) lcnt[i] = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < nn; i += blockDim.x) atomicAdd(&lcnt[hgt[i]], 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int s = 0, H = 0;
-    for (int h = 0; h <= kMaxHeight; ++h) {
-      lstart[h] = s;
-      s += lcnt[h];
-      if (lcnt[h]) H = h;
-      lcnt[h] = 0;
-    }
-    lstart[kMaxHeight + 1] = s;
-    *hmax = H;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-    const int h = hgt[i];
-    list[lstart[h] + atomicAdd(&lcnt[h], 1)] = (uint16_t)i;
-  }
-  __syncthreads();
-  return *hmax;
-}
-
-__device__ inline void top_range(const int32_t* top, int ntop, int64_t a, int64_t b, int* lo,
-                                 int* hi) {
-  int l = 0, r = ntop;
-  while (l < r) { int md = (l + r) >> 1; if (top[md] < a) l = md + 1; else r = md; }
-  *lo = l;
-  r = ntop;
-  while (l < r) { int md = (l + r) >> 1; if (top[md] < b) l = md + 1; else r = md; }
-  *hi = l;
-}
-
-// -------------------------------------------------------------- upward
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_up_tiles(ApplyArgs<T> a, int tile) {
-  extern __shared__ unsigned char smem_raw[];
-  T* info = reinterpret_cast<T*>(smem_raw);
-  uint16_t* list = reinterpret_cast<uint16_t*>(info + (size_t)tile * 6);
-  __shared__ int lstart[kMaxHeight + 2], lcnt[kMaxHeight + 2], hmax;
-  const int ntiles = a.counters[0];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int32_t R = a.tiles[t];
-    const int32_t j = body_of_node(a.off, a.m, R);
-    const int64_t base = (int64_t)a.first[R] - j;
-    const int nn = a.cnt[R] - 1;
-    const int H = make_levels(a.height + base, nn, list, lstart, lcnt, &hmax);
-    for (int h = 1; h <= H; ++h) {
-      for (int p = lstart[h] + threadIdx.x; p < lstart[h + 1]; p += blockDim.x) {
-        const int li = list[p];
-        const int64_t q = base + li;
-        const int32_t lc = a.cl[q], rc = a.cr[q];
-        T rec[kRec];
-        load_rec(a.rec + q * kRec, rec);
-        T bx[3], by[3];
-        const T *tx, *rx = nullptr, *ty, *ry = nullptr;
-        if (is_leaf(lc)) { load_bead(a, lc, bx); tx = bx; }
-        else { tx = info + (lc - base) * 6; rx = tx + 3; }
-        if (is_leaf(rc)) { load_bead(a, rc, by); ty = by; }
-        else { ty = info + (rc - base) * 6; ry = ty + 3; }
-        T tr[6];
-        up_node(rec, !is_leaf(lc), !is_leaf(rc), tx, rx, ty, ry, tr, tr + 3, a.out + a.roff[q]);
-        T* dst = info + (int64_t)li * 6;
+// u <- H u with H = I - tau v v^T, v(j) = 1 and the other nonzeros of v at
+// rows R[0..n-1] with values vv[0..n-1].
+template <typename T, int NV>
+__device__ __forceinline__ void reflect(T* u, int j, const int (&R)[NV], const T* vv, T tau) {
+  T w = u[j];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) dst[i] = tr[i];
-      }
-      __syncthreads();
-    }
-    const int64_t n_body = a.off[j + 1] - a.off[j];
-    if (a.cnt[R] < n_body && threadIdx.x < 6)
-      a.xs[(int64_t)R * 6 + threadIdx.x] = info[(R - base) * 6 + threadIdx.x];
-    __syncthreads();
+  for (int i = 0; i < NV; ++i) w += vv[i] * u[R[i]];
+  w *= tau;
+  u[j] -= w;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) u[R[i]] -= w * vv[i];
+}
+
+// G u and G^T u for the two Householder record types (layout in zq_internal.cuh).
+template <typename T>
+__device__ __forceinline__ void g6(const T* r, T* u, bool transpose) {
+  constexpr int R0[2] = {4, 5}, R1[3] = {3, 4, 5}, R2[3] = {3, 4, 5};
+  if (!transpose) {
+    reflect<T, 2>(u, 0, R0, r + 5, r[2]);
+    reflect<T, 3>(u, 1, R1, r + 7, r[3]);
+    reflect<T, 3>(u, 2, R2, r + 10, r[4]);
+  } else {
+    reflect<T, 3>(u, 2, R2, r + 10, r[4]);
+    reflect<T, 3>(u, 1, R1, r + 7, r[3]);
+    reflect<T, 2>(u, 0, R0, r + 5, r[2]);
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_up_top(ApplyArgs<T> a) {
-  const int32_t j = a.top_bodies[blockIdx.x];
-  const int64_t nb = a.off[j] - j, ne = a.off[j + 1] - (j + 1);
-  int lo, hi;
-  top_range(a.top, a.counters[1], nb, ne, &lo, &hi);
-  const int H = a.height[a.root[j]];
-  for (int h = 1; h <= H; ++h) {
-    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      const int32_t q = a.top[p];
-      if (a.height[q] != h) continue;
-      const int32_t lc = a.cl[q], rc = a.cr[q];
-      T rec[kRec];
-      load_rec(a.rec + (int64_t)q * kRec, rec);
-      T X[6], Y[6];
-      if (is_leaf(lc)) load_bead(a, lc, X);
-      else for (int i = 0; i < 6; ++i) X[i] = a.xs[(int64_t)lc * 6 + i];
-      if (is_leaf(rc)) load_bead(a, rc, Y);
-      else for (int i = 0; i < 6; ++i) Y[i] = a.xs[(int64_t)rc * 6 + i];
-      T tr[6];
-      up_node(rec, !is_leaf(lc), !is_leaf(rc), X, X + 3, Y, Y + 3, tr, tr + 3, a.out + a.roff[q]);
-      for (int i = 0; i < 6; ++i) a.xs[(int64_t)q * 6 + i] = tr[i];
+__device__ __forceinline__ void g9(const T* r, T* u, bool transpose) {
+  constexpr int R0[3] = {3, 7, 8}, R1[5] = {3, 4, 6, 7, 8}, R2[6] = {3, 4, 5, 6, 7, 8};
+  if (!transpose) {
+    reflect<T, 3>(u, 0, R0, r + 5, r[2]);
+    reflect<T, 5>(u, 1, R1, r + 8, r[3]);
+    reflect<T, 6>(u, 2, R2, r + 13, r[4]);
+  } else {
+    reflect<T, 6>(u, 2, R2, r + 13, r[4]);
+    reflect<T, 5>(u, 1, R1, r + 8, r[3]);
+    reflect<T, 3>(u, 0, R0, r + 5, r[2]);
+  }
+}
+
+// --------------------------------------------------------- node: upward
+// X, Y: the children's Info-sets [t; r] (r unused for leaves).  Writes the
+// node's Info-set to P and its residues to res.
+template <typename T, int TYPE>
+__device__ __forceinline__ void up_node(const T* __restrict__ recp, const T* X, const T* Y, bool xi,
+                                        T* P, T* __restrict__ res) {
+  T r[rec_words(TYPE)];
+  load_rec<T, rec_words(TYPE)>(recp, r);
+  const T al = r[0], be = r[1];
+  T u[9];
+  int k = 0;
+  if (TYPE == 2) {
+    u[0] = X[3]; u[1] = X[4]; u[2] = X[5];
+    u[3] = Y[3]; u[4] = Y[4]; u[5] = Y[5];
+    k = 6;
+  } else if (TYPE == 1) {
+    const T* C = xi ? X : Y;
+    u[0] = C[3]; u[1] = C[4]; u[2] = C[5];
+    k = 3;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    P[a] = al * X[a] + be * Y[a];
+    u[k + a] = be * X[a] - al * Y[a];
+  }
+  if (TYPE == 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) P[3 + i] = r[2 + 3 * i] * u[0] + r[3 + 3 * i] * u[1] + r[4 + 3 * i] * u[2];
+    return;
+  }
+  if (TYPE == 1) {
+    g6(r, u, false);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) res[i] = u[3 + i];
+  } else {
+    g9(r, u, false);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) res[i] = u[3 + i];
+  }
+  P[3] = u[0]; P[4] = u[1]; P[5] = u[2];
+}
+
+// ------------------------------------------------------- node: downward
+template <typename T, int TYPE>
+__device__ __forceinline__ void down_node(const T* __restrict__ recp, const T* Lp, const T* __restrict__ w,
+                                          bool xi, T* Lx, T* Ly) {
+  T r[rec_words(TYPE)];
+  load_rec<T, rec_words(TYPE)>(recp, r);
+  const T al = r[0], be = r[1];
+  T z[9];
+  z[0] = Lp[3]; z[1] = Lp[4]; z[2] = Lp[5];
+  T sg[3];
+  if (TYPE == 0) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sg[j] = r[2 + j] * z[0] + r[5 + j] * z[1] + r[8 + j] * z[2];
+  } else if (TYPE == 1) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) z[3 + i] = w[i];
+    g6(r, z, true);
+    T* c = xi ? Lx : Ly;
+    c[3] = z[0]; c[4] = z[1]; c[5] = z[2];
+    sg[0] = z[3]; sg[1] = z[4]; sg[2] = z[5];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) z[3 + i] = w[i];
+    g9(r, z, true);
+    Lx[3] = z[0]; Lx[4] = z[1]; Lx[5] = z[2];
+    Ly[3] = z[3]; Ly[4] = z[4]; Ly[5] = z[5];
+    sg[0] = z[6]; sg[1] = z[7]; sg[2] = z[8];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Lx[i] = al * Lp[i] + be * sg[i];
+    Ly[i] = be * Lp[i] - al * sg[i];
+  }
+}
+
+template <typename T, int TYPE>
+__device__ __forceinline__ void up_slot(const ApplyArgs<T>& a, int64_t s, int64_t rw) {
+  const int2 cc = a.sc[s];
+  T X[6], Y[6], P[6];
+  if (is_leaf(cc.x)) load_bead(a, cc.x, X); else load6(a.xs + (int64_t)cc.x * 6, X);
+  if (is_leaf(cc.y)) load_bead(a, cc.y, Y); else load6(a.xs + (int64_t)cc.y * 6, Y);
+  up_node<T, TYPE>(a.rec + rw, X, Y, cc.x >= 0, P, a.out + a.sroff[s]);
+  store6(a.xs + s * 6, P);
+}
+
+template <typename T, int TYPE>
+__device__ __forceinline__ void down_slot(const ApplyArgs<T>& a, int64_t s, int64_t rw, const T* Lp) {
+  const int2 cc = a.sc[s];
+  T Lx[6], Ly[6];
+  down_node<T, TYPE>(a.rec + rw, Lp, a.in + a.sroff[s], cc.x >= 0, Lx, Ly);
+  if (is_leaf(cc.x)) store_bead(a, cc.x, Lx); else store6(a.xs + (int64_t)cc.x * 6, Lx);
+  if (is_leaf(cc.y)) store_bead(a, cc.y, Ly); else store6(a.xs + (int64_t)cc.y * 6, Ly);
+}
+
+// ------------------------------------------------------------- kernels
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_up_level(ApplyArgs<T> a, int h) {
+  const int b0 = 3 * (h - 1);
+  const int32_t s0 = a.bstart[b0], s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
+  const int32_t r0 = a.brec[b0], r1 = a.brec[b0 + 1], r2 = a.brec[b0 + 2];
+  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    if (s < s1) up_slot<T, 0>(a, s, r0 + (s - s0) * rec_words(0));
+    else if (s < s2) up_slot<T, 1>(a, s, r1 + (s - s1) * rec_words(1));
+    else up_slot<T, 2>(a, s, r2 + (s - s2) * rec_words(2));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_down_level(ApplyArgs<T> a, int h) {
+  const int b0 = 3 * (h - 1);
+  const int32_t s0 = a.bstart[b0], s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
+  const int32_t r0 = a.brec[b0], r1 = a.brec[b0 + 1], r2 = a.brec[b0 + 2];
+  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    T Lp[6];
+    load6(a.xs + s * 6, Lp);
+    if (s < s1) down_slot<T, 0>(a, s, r0 + (s - s0) * rec_words(0), Lp);
+    else if (s < s2) down_slot<T, 1>(a, s, r1 + (s - s1) * rec_words(1), Lp);
+    else down_slot<T, 2>(a, s, r2 + (s - s2) * rec_words(2), Lp);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void tail_range(const ApplyArgs<T>& a, int32_t j, int32_t* lo, int32_t* hi) {
+  const int bt = 3 * a.cut;
+  id_range(a.sid, a.bstart[bt], a.bstart[bt + 1], a.off[j] - j, a.off[j + 1] - (j + 1), lo, hi);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_up_tail(ApplyArgs<T> a) {
+  const int32_t j = blockIdx.x;
+  int32_t lo, hi;
+  tail_range(a, j, &lo, &hi);
+  if (lo == hi) return;
+  const int bt = 3 * a.cut;
+  const int32_t t0 = a.bstart[bt], rt = a.brec[bt];
+  const int H = a.sheight[a.root_slot[j]];
+  for (int h = a.cut + 1; h <= H; ++h) {
+    for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+      if (a.sheight[s] != h) continue;
+      const int2 cc = a.sc[s];
+      const int64_t rw = rt + (int64_t)(s - t0) * kRecMax;
+      const int type = (cc.x >= 0) + (cc.y >= 0);
+      if (type == 0) up_slot<T, 0>(a, s, rw);
+      else if (type == 1) up_slot<T, 1>(a, s, rw);
+      else up_slot<T, 2>(a, s, rw);
     }
     __syncthreads();
   }
 }
 
-// ------------------------------------------------------------ downward
+// Runs before the levels: zero root Velocity-set for every body (Q~^T
+// only), then the nodes above the cut from the root down.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_down_top(ApplyArgs<T> a) {
-  const int32_t j = a.top_bodies[blockIdx.x];
-  const int64_t nb = a.off[j] - j, ne = a.off[j + 1] - (j + 1);
-  int lo, hi;
-  top_range(a.top, a.counters[1], nb, ne, &lo, &hi);
-  const int32_t rt = a.root[j];
-  const int H = a.height[rt];
-  for (int h = H; h >= 1; --h) {
-    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      const int32_t q = a.top[p];
-      if (a.height[q] != h) continue;
-      const int32_t lc = a.cl[q], rc = a.cr[q];
-      T rec[kRec];
-      load_rec(a.rec + (int64_t)q * kRec, rec);
+__global__ void __launch_bounds__(kThreads) k_down_tail(ApplyArgs<T> a) {
+  const int32_t j = blockIdx.x;
+  const int32_t rs = a.root_slot[j];
+  if (threadIdx.x < 6) a.xs[(int64_t)rs * 6 + threadIdx.x] = T(0);
+  __syncthreads();
+  int32_t lo, hi;
+  tail_range(a, j, &lo, &hi);
+  if (lo == hi) return;
+  const int bt = 3 * a.cut;
+  const int32_t t0 = a.bstart[bt], rt = a.brec[bt];
+  const int H = a.sheight[rs];
+  for (int h = H; h > a.cut; --h) {
+    for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+      if (a.sheight[s] != h) continue;
+      const int2 cc = a.sc[s];
+      const int64_t rw = rt + (int64_t)(s - t0) * kRecMax;
       T Lp[6];
-      for (int i = 0; i < 6; ++i) Lp[i] = (q == rt) ? T(0) : a.xs[(int64_t)q * 6 + i];
-      T Lx[6], Ly[6];
-      down_node(rec, !is_leaf(lc), !is_leaf(rc), Lp, a.in + a.roff[q], Lx, Ly);
-      if (is_leaf(lc)) store_bead(a, lc, Lx);
-      else for (int i = 0; i < 6; ++i) a.xs[(int64_t)lc * 6 + i] = Lx[i];
-      if (is_leaf(rc)) store_bead(a, rc, Ly);
-      else for (int i = 0; i < 6; ++i) a.xs[(int64_t)rc * 6 + i] = Ly[i];
+      load6(a.xs + (int64_t)s * 6, Lp);
+      const int type = (cc.x >= 0) + (cc.y >= 0);
+      if (type == 0) down_slot<T, 0>(a, s, rw, Lp);
+      else if (type == 1) down_slot<T, 1>(a, s, rw, Lp);
+      else down_slot<T, 2>(a, s, rw, Lp);
     }
     __syncthreads();
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_down_tiles(ApplyArgs<T> a, int tile) {
-  extern __shared__ unsigned char smem_raw[];
-  T* vel = reinterpret_cast<T*>(smem_raw);
-  uint16_t* list = reinterpret_cast<uint16_t*>(vel + (size_t)tile * 6);
-  __shared__ int lstart[kMaxHeight + 2], lcnt[kMaxHeight + 2], hmax;
-  const int ntiles = a.counters[0];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int32_t R = a.tiles[t];
-    const int32_t j = body_of_node(a.off, a.m, R);
-    const int64_t base = (int64_t)a.first[R] - j;
-    const int nn = a.cnt[R] - 1;
-    const int64_t n_body = a.off[j + 1] - a.off[j];
-    if (threadIdx.x < 6)
-      vel[(R - base) * 6 + threadIdx.x] =
-          (a.cnt[R] < n_body) ? a.xs[(int64_t)R * 6 + threadIdx.x] : T(0);
-    const int H = make_levels(a.height + base, nn, list, lstart, lcnt, &hmax);
-    for (int h = H; h >= 1; --h) {
-      for (int p = lstart[h] + threadIdx.x; p < lstart[h + 1]; p += blockDim.x) {
-        const int li = list[p];
-        const int64_t q = base + li;
-        const int32_t lc = a.cl[q], rc = a.cr[q];
-        T rec[kRec];
-        load_rec(a.rec + q * kRec, rec);
-        T Lp[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) Lp[i] = vel[(int64_t)li * 6 + i];
-        T Lx[6], Ly[6];
-        down_node(rec, !is_leaf(lc), !is_leaf(rc), Lp, a.in + a.roff[q], Lx, Ly);
-        if (is_leaf(lc)) store_bead(a, lc, Lx);
-        else {
-#pragma unroll
-          for (int i = 0; i < 6; ++i) vel[(lc - base) * 6 + i] = Lx[i];
-        }
-        if (is_leaf(rc)) store_bead(a, rc, Ly);
-        else {
-#pragma unroll
-          for (int i = 0; i < 6; ++i) vel[(rc - base) * 6 + i] = Ly[i];
-        }
-      }
-      __syncthreads();
-    }
   }
 }
 
 template <typename T>
 ApplyArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   ApplyArgs<T> a;
-  a.off = c.off; a.m = c.m; a.N = c.N;
-  a.perm = c.perm; a.cl = c.cl; a.cr = c.cr; a.cnt = c.cnt; a.first = c.first; a.roff = c.roff;
-  a.height = c.height; a.tiles = c.tiles; a.top = c.top; a.counters = c.counters;
-  a.top_bodies = c.top_d; a.root = c.root;
+  a.N = c.N; a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.sroff = c.sroff; a.sheight = c.sheight;
+  a.sid = c.sid; a.bstart = c.bstart; a.brec = c.brec; a.root_slot = c.root_slot; a.cut = c.cut;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;
   return a;
 }
 
 template <typename T>
-size_t tile_smem(int tile) { return (size_t)tile * (6 * sizeof(T) + sizeof(uint16_t)); }
-
-template <typename T>
 zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out) {
   ApplyArgs<T> a = make_args<T>(c, rec, xs, v, out);
-  const size_t smem = tile_smem<T>(c.tile);
-  ZQ_CUDA_TRY(cudaFuncSetAttribute(k_up_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  time_begin(c, "up_tiles");
-  k_up_tiles<T><<<c.num_sms * 4, kThreads, smem, c.stream>>>(a, c.tile);
-  time_end(c, "up_tiles");
-  ZQ_CUDA_TRY(cudaGetLastError());
-  if (!c.top_bodies.empty()) {
-    time_begin(c, "up_top");
-    k_up_top<T><<<(unsigned)c.top_bodies.size(), kThreads, 0, c.stream>>>(a);
-    time_end(c, "up_top");
-    ZQ_CUDA_TRY(cudaGetLastError());
+  const int grid = c.num_sms * 8;
+  for (int h = 1; h <= c.cut; ++h) {
+    time_begin(c, "up_level");
+    k_up_level<T><<<grid, kThreads, 0, c.stream>>>(a, h);
+    time_end(c, "up_level");
   }
+  time_begin(c, "up_tail");
+  k_up_tail<T><<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
+  time_end(c, "up_tail");
+  ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }
 
 template <typename T>
 zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out) {
   ApplyArgs<T> a = make_args<T>(c, rec, xs, w, out);
-  if (!c.top_bodies.empty()) {
-    time_begin(c, "down_top");
-    k_down_top<T><<<(unsigned)c.top_bodies.size(), kThreads, 0, c.stream>>>(a);
-    time_end(c, "down_top");
-    ZQ_CUDA_TRY(cudaGetLastError());
+  time_begin(c, "down_tail");
+  k_down_tail<T><<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
+  time_end(c, "down_tail");
+  const int grid = c.num_sms * 8;
+  for (int h = c.cut; h >= 1; --h) {
+    time_begin(c, "down_level");
+    k_down_level<T><<<grid, kThreads, 0, c.stream>>>(a, h);
+    time_end(c, "down_level");
   }
-  const size_t smem = tile_smem<T>(c.tile);
-  ZQ_CUDA_TRY(cudaFuncSetAttribute(k_down_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  time_begin(c, "down_tiles");
-  k_down_tiles<T><<<c.num_sms * 4, kThreads, smem, c.stream>>>(a, c.tile);
-  time_end(c, "down_tiles");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }

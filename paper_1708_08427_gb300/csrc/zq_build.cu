@@ -6,7 +6,7 @@
 //   K = sqrt(n_x n / n_y) R21 with R21 = [c_x - c_p]x, which equals
 //       sqrt(n_x n_y / n) [c_x - c_y]x  (c_x - c_p = (n_y / n)(c_x - c_y)),
 //   M = [T22_x | T22_y | K] (3 x k; a leaf child has no T22 block, Case II),
-//   M = [T22_p 0] G by Householder reflections of M^T (Eq. 3.5; LAPACK
+//   M = [T22_p 0] G by Householder reflections of A = M^T (Eq. 3.5; LAPACK
 //       dgeqrf convention: beta_j = -sign(alpha_j) ||x||, no reflection when
 //       the part below the diagonal is exactly zero; T22_p = R^T, G = Q^T);
 //       before each reflection, column entries <= 2^-44 ||M||_F are set to
@@ -17,10 +17,13 @@
 // T22_p = sqrt(n_x n_y / n) |d| [g2, -g1, 0]; d = 0 gives G = I, T22 = 0
 // and the degenerate warning.
 //
-// Nodes are processed tile by tile (a tile = subtree of at most `tile`
-// beads, one thread block) and inside a tile level by level (heights
-// 1, 2, ...); the nodes above the tiles are then processed per body.
-// The children's state (centroid, T22) is read from global memory.
+// A has structural zeros (T22 blocks are lower triangular, [d]x has a zero
+// diagonal); the reflections below touch only the entries that can be
+// nonzero, which is exact (the skipped products are by exact zeros).
+//
+// Schedule: heights 1..cut level by level over all bodies (one launch per
+// height, nodes sorted by type inside a height), then the remaining nodes
+// one thread block per body.  A node's children are finished before it.
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -34,249 +37,312 @@ struct BuildArgs {
   const double* y;
   const double* z;
   const int64_t* off;
-  int64_t m;
   const int32_t* perm;
-  const int32_t* cl;
-  const int32_t* cr;
-  const int32_t* cnt;
-  const int32_t* first;
-  const uint8_t* height;
-  const int32_t* tiles;
-  const int32_t* top;
-  const int32_t* counters;
-  const int32_t* top_bodies;
-  const int32_t* root;
+  const int2* sc;
+  const int32_t* scnt;
+  const uint8_t* sheight;
+  const int32_t* sid;
+  const int32_t* bstart;
+  const int32_t* brec;
+  const int32_t* root_slot;
+  int cut;
   double* st64;
-  double* rec64;
+  double* rec64;  // compact records (may be null: not wanted)
   float* rec32;
   int32_t* err;
 };
 
 struct Child {
-  int n;
+  double n;
   double c[3];
-  double L[6];  // packed lower triangle, valid for internal children
-  bool internal;
+  double L[6];  // packed lower triangle (L00, L10, L11, L20, L21, L22)
 };
 
-__device__ inline void load_child(const BuildArgs& a, int32_t code, Child& ch) {
-  if (is_leaf(code)) {
-    const int32_t i = a.perm[leaf_pos(code)];
-    ch.n = 1;
-    ch.c[0] = a.x[i];
-    ch.c[1] = a.y[i];
-    ch.c[2] = a.z[i];
-    ch.internal = false;
-  } else {
-    const double* s = a.st64 + (int64_t)code * kState;
-    ch.n = a.cnt[code];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ch.c[i] = s[i];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) ch.L[i] = s[3 + i];
-    ch.internal = true;
-  }
+__device__ __forceinline__ void load_leaf(const BuildArgs& a, int32_t code, Child& ch) {
+  const int32_t i = a.perm[leaf_pos(code)];
+  ch.n = 1.0;
+  ch.c[0] = a.x[i];
+  ch.c[1] = a.y[i];
+  ch.c[2] = a.z[i];
 }
 
-__device__ void build_node(const BuildArgs& a, int64_t q) {
-  const int32_t lc = a.cl[q], rc = a.cr[q];
-  Child X, Y;
-  load_child(a, lc, X);
-  load_child(a, rc, Y);
-  const double nx = (double)X.n, ny = (double)Y.n, n = nx + ny;
-  double cp[3], d[3];
+__device__ __forceinline__ void load_node(const BuildArgs& a, int32_t slot, Child& ch) {
+  const double2* s = reinterpret_cast<const double2*>(a.st64 + (int64_t)slot * kState);
+  const double2 s0 = s[0], s1 = s[1], s2 = s[2], s3 = s[3], s4 = s[4];
+  ch.n = (double)a.scnt[slot];
+  ch.c[0] = s0.x; ch.c[1] = s0.y; ch.c[2] = s1.x;
+  ch.L[0] = s1.y; ch.L[1] = s2.x; ch.L[2] = s2.y; ch.L[3] = s3.x; ch.L[4] = s3.y; ch.L[5] = s4.x;
+}
+
+struct Geo {
+  double cp[3], d[3], al, be, sk;
+};
+
+__device__ __forceinline__ void geometry(const Child& X, const Child& Y, Geo& g) {
+  const double n = X.n + Y.n, rn = 1.0 / n;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    cp[i] = (nx * X.c[i] + ny * Y.c[i]) / n;
-    d[i] = X.c[i] - Y.c[i];
+    g.cp[i] = (X.n * X.c[i] + Y.n * Y.c[i]) * rn;
+    g.d[i] = X.c[i] - Y.c[i];
   }
-  const double sk = sqrt(nx * ny / n);
-  double rec[kRec];
-#pragma unroll
-  for (int i = 0; i < kRec; ++i) rec[i] = 0.0;
-  rec[0] = sqrt(nx / n);
-  rec[1] = sqrt(ny / n);
-  double Lp[6];
+  g.al = sqrt(X.n * rn);
+  g.be = sqrt(Y.n * rn);
+  g.sk = sqrt(X.n * Y.n * rn);
+}
 
-  if (!X.internal && !Y.internal) {
-    // Case I, bead & bead (Eqs. 3.9-3.10)
-    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    if (dn == 0.0) {
-      rec[5] = 1.0; rec[9] = 1.0; rec[13] = 1.0;
+template <int W>
+__device__ __forceinline__ void store(const BuildArgs& a, int64_t slot, int64_t rw, const double (&rec)[W],
+                                      const double* cp, const double* L) {
+  double2* st = reinterpret_cast<double2*>(a.st64 + slot * kState);
+  st[0] = make_double2(cp[0], cp[1]);
+  st[1] = make_double2(cp[2], L[0]);
+  st[2] = make_double2(L[1], L[2]);
+  st[3] = make_double2(L[3], L[4]);
+  st[4] = make_double2(L[5], 0.0);
+  if (a.rec64) {
+    double2* r = reinterpret_cast<double2*>(a.rec64 + rw);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) Lp[i] = 0.0;
-      atomicOr(a.err, kErrDegenerate);
-    } else {
-      const double h[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
-      double g1[3];
-      if (d[1] != 0.0 || d[2] != 0.0) {
-        const double s = sqrt(d[1] * d[1] + d[2] * d[2]);
-        g1[0] = 0.0; g1[1] = -d[2] / s; g1[2] = d[1] / s;
-      } else {
-        g1[0] = 0.0; g1[1] = 0.0; g1[2] = -d[0] / fabs(d[0]);
-      }
-      const double g2[3] = {h[1] * g1[2] - h[2] * g1[1], h[2] * g1[0] - h[0] * g1[2],
-                            h[0] * g1[1] - h[1] * g1[0]};
+    for (int i = 0; i < W / 2; ++i) r[i] = make_double2(rec[2 * i], rec[2 * i + 1]);
+  }
+  if (a.rec32) {
+    float4* r = reinterpret_cast<float4*>(a.rec32 + rw);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        rec[5 + i] = g1[i];
-        rec[8 + i] = g2[i];
-        rec[11 + i] = -h[i];
-      }
-      const double s = sk * dn;
-      Lp[0] = s * g2[0];
-      Lp[1] = s * g2[1];
-      Lp[2] = -s * g1[1];
-      Lp[3] = s * g2[2];
-      Lp[4] = -s * g1[2];
-      Lp[5] = 0.0;
-    }
+    for (int i = 0; i < W / 4; ++i)
+      r[i] = make_float4((float)rec[4 * i], (float)rec[4 * i + 1], (float)rec[4 * i + 2], (float)rec[4 * i + 3]);
+  }
+}
+
+// ------------------------------------------------------------ Case I
+__device__ void node_case1(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
+  Child X, Y;
+  load_leaf(a, cc.x, X);
+  load_leaf(a, cc.y, Y);
+  Geo g;
+  geometry(X, Y, g);
+  double rec[12];
+  rec[0] = g.al;
+  rec[1] = g.be;
+  rec[11] = 0.0;
+  double L[6];
+  const double* d = g.d;
+  const double dn2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  if (dn2 == 0.0) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rec[2 + i] = (i % 4 == 0) ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) L[i] = 0.0;
+    atomicOr(a.err, kErrDegenerate);
   } else {
-    // General node / Case II: Householder QR of A = M^T (k x 3)
-    double A[9][3];
-    int k = 0;
-    if (X.internal) {
-      A[0][0] = X.L[0]; A[0][1] = X.L[1]; A[0][2] = X.L[3];
-      A[1][0] = 0.0;    A[1][1] = X.L[2]; A[1][2] = X.L[4];
-      A[2][0] = 0.0;    A[2][1] = 0.0;    A[2][2] = X.L[5];
-      k = 3;
+    const double dn = sqrt(dn2), rdn = 1.0 / dn;
+    const double h[3] = {d[0] * rdn, d[1] * rdn, d[2] * rdn};
+    double g1[3];
+    if (d[1] != 0.0 || d[2] != 0.0) {  // e_x x d, first row of U in Eq. 3.10
+      const double rs = 1.0 / sqrt(d[1] * d[1] + d[2] * d[2]);
+      g1[0] = 0.0; g1[1] = -d[2] * rs; g1[2] = d[1] * rs;
+    } else {                            // d along x: e_y x d
+      g1[0] = 0.0; g1[1] = 0.0; g1[2] = d[0] > 0.0 ? -1.0 : 1.0;
     }
-    if (Y.internal) {
-      A[k][0] = Y.L[0];   A[k][1] = Y.L[1];   A[k][2] = Y.L[3];
-      A[k + 1][0] = 0.0;  A[k + 1][1] = Y.L[2]; A[k + 1][2] = Y.L[4];
-      A[k + 2][0] = 0.0;  A[k + 2][1] = 0.0;  A[k + 2][2] = Y.L[5];
-      k += 3;
+    const double g2[3] = {h[1] * g1[2] - h[2] * g1[1], h[2] * g1[0] - h[0] * g1[2],
+                          h[0] * g1[1] - h[1] * g1[0]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      rec[2 + i] = g1[i];
+      rec[5 + i] = g2[i];
+      rec[8 + i] = -h[i];
     }
-    A[k][0] = sk * 0.0;        A[k][1] = sk * d[2];       A[k][2] = sk * (-d[1]);
-    A[k + 1][0] = sk * (-d[2]); A[k + 1][1] = sk * 0.0;    A[k + 1][2] = sk * d[0];
-    A[k + 2][0] = sk * d[1];   A[k + 2][1] = sk * (-d[0]); A[k + 2][2] = sk * 0.0;
-    k += 3;
-    // entries <= 2^-44 ||M||_F are rounding noise of an exact zero
-    // (rank-deficient M); they are zeroed before each reflection
-    double mn2 = 0.0;
-    for (int i = 0; i < k; ++i)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) mn2 += A[i][c] * A[i][c];
-    const double tiny = sqrt(mn2) * 0x1p-44;
-    int tail = 5;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      for (int i = j; i < k; ++i)
-        if (fabs(A[i][j]) <= tiny) A[i][j] = 0.0;
-      double xn2 = 0.0;
-      for (int i = j + 1; i < k; ++i) xn2 += A[i][j] * A[i][j];
-      if (xn2 != 0.0) {
-        const double al = A[j][j];
-        const double norm = sqrt(al * al + xn2);
-        const double be = (al >= 0.0) ? -norm : norm;
-        const double tau = (be - al) / be;
-        const double den = al - be;
-        double v[9];
-        for (int i = j + 1; i < k; ++i) v[i] = A[i][j] / den;
-        A[j][j] = be;
-        for (int i = j + 1; i < k; ++i) A[i][j] = 0.0;
-#pragma unroll
-        for (int c = j + 1; c < 3; ++c) {
-          double w = A[j][c];
-          for (int i = j + 1; i < k; ++i) w += v[i] * A[i][c];
-          A[j][c] -= tau * w;
-          for (int i = j + 1; i < k; ++i) A[i][c] -= tau * w * v[i];
-        }
-        rec[2 + j] = tau;
-        for (int i = j + 1; i < k; ++i) rec[tail + (i - j - 1)] = v[i];
-      }
-      tail += k - 1 - j;
-    }
-    Lp[0] = A[0][0];
-    Lp[1] = A[0][1];
-    Lp[2] = A[1][1];
-    Lp[3] = A[0][2];
-    Lp[4] = A[1][2];
-    Lp[5] = A[2][2];
+    const double sl = g.sk * dn;  // T22 = sk |d| [g2, -g1, 0]
+    L[0] = sl * g2[0];
+    L[1] = sl * g2[1];
+    L[2] = -sl * g1[1];
+    L[3] = sl * g2[2];
+    L[4] = -sl * g1[2];
+    L[5] = 0.0;
   }
-  double* st = a.st64 + q * kState;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) st[i] = cp[i];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) st[3 + i] = Lp[i];
-  double2* r64 = reinterpret_cast<double2*>(a.rec64 + q * kRec);
-  float4* r32 = reinterpret_cast<float4*>(a.rec32 + q * kRec);
-#pragma unroll
-  for (int i = 0; i < kRec / 2; ++i) r64[i] = make_double2(rec[2 * i], rec[2 * i + 1]);
-#pragma unroll
-  for (int i = 0; i < kRec / 4; ++i)
-    r32[i] = make_float4((float)rec[4 * i], (float)rec[4 * i + 1], (float)rec[4 * i + 2],
-                         (float)rec[4 * i + 3]);
+  store<12>(a, s, rw, rec, g.cp, L);
 }
 
-// Per-tile level lists in shared memory: list[lstart[h] .. lstart[h+1]) =
-// local indices of the tile's nodes of height h.  Returns the tile height.
-__device__ int make_levels(const uint8_t* __restrict__ hgt, int nn, uint16_t* list, int* lstart,
-                           int* lcnt, int* hmax) {
-  for (int i = threadIdx.x; i < kMaxHeight + 2; i += blockDim.x) lcnt[i] = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < nn; i += blockDim.x) atomicAdd(&lcnt[hgt[i]], 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int s = 0, H = 0;
-    for (int h = 0; h <= kMaxHeight; ++h) {
-      lstart[h] = s;
-      s += lcnt[h];
-      if (lcnt[h]) H = h;
-      lcnt[h] = 0;
-    }
-    lstart[kMaxHeight + 1] = s;
-    *hmax = H;
+// One Householder step (LAPACK dlarfg convention) on a column whose
+// possibly nonzero entries below the diagonal are x[0..M-1]; al is the
+// diagonal entry.  Returns tau (0: no reflection) and scales x into the
+// tail of v (v_j = 1 implicit); al becomes beta.
+template <int M>
+__device__ __forceinline__ double reflector(double& al, double (&x)[M]) {
+  double xn2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < M; ++i) xn2 += x[i] * x[i];
+  if (xn2 == 0.0) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) x[i] = 0.0;
+    return 0.0;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-    const int h = hgt[i];
-    list[lstart[h] + atomicAdd(&lcnt[h], 1)] = (uint16_t)i;
-  }
-  __syncthreads();
-  return *hmax;
+  const double norm = sqrt(al * al + xn2);
+  const double be = (al >= 0.0) ? -norm : norm;
+  const double tau = (be - al) / be;
+  const double rden = 1.0 / (al - be);
+#pragma unroll
+  for (int i = 0; i < M; ++i) x[i] *= rden;
+  al = be;
+  return tau;
 }
 
-__global__ void __launch_bounds__(kThreads) k_build_tiles(BuildArgs a) {
-  extern __shared__ unsigned char smem[];
-  __shared__ int lstart[kMaxHeight + 2], lcnt[kMaxHeight + 2], hmax;
-  uint16_t* list = reinterpret_cast<uint16_t*>(smem);
-  const int ntiles = a.counters[0];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int32_t R = a.tiles[t];
-    const int32_t j = body_of_node(a.off, a.m, R);
-    const int64_t base = (int64_t)a.first[R] - j;
-    const int nn = a.cnt[R] - 1;
-    const int H = make_levels(a.height + base, nn, list, lstart, lcnt, &hmax);
-    for (int h = 1; h <= H; ++h) {
-      for (int p = lstart[h] + threadIdx.x; p < lstart[h + 1]; p += blockDim.x)
-        build_node(a, base + list[p]);
-      __syncthreads();
-    }
+__device__ __forceinline__ void flush(double& v, double tiny) {
+  if (fabs(v) <= tiny) v = 0.0;
+}
+
+// ------------------------------------------------- k = 6 (Case II)
+// A rows: 0-2 = T22_c^T of the internal child, 3-5 = K^T.
+__device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
+  Child X, Y;
+  const bool xi = cc.x >= 0;
+  if (xi) { load_node(a, cc.x, X); load_leaf(a, cc.y, Y); }
+  else { load_leaf(a, cc.x, X); load_node(a, cc.y, Y); }
+  Geo g;
+  geometry(X, Y, g);
+  const double* Lc = xi ? X.L : Y.L;
+  const double kx = g.sk * g.d[0], ky = g.sk * g.d[1], kz = g.sk * g.d[2];
+  // columns of A: a0 (rows 0, 4, 5), a1 (rows 0, 1, 3, 5 + fill 4), a2 (rows 0-4 + fill 5)
+  double A00 = Lc[0], A01 = Lc[1], A02 = Lc[3];
+  double A11 = Lc[2], A12 = Lc[4];
+  double A22 = Lc[5];
+  double A31 = kz, A32 = -ky;
+  double A40 = -kz, A41 = 0.0, A42 = kx;
+  double A50 = ky, A51 = -kx, A52 = 0.0;
+  const double mn2 = A00 * A00 + A01 * A01 + A02 * A02 + A11 * A11 + A12 * A12 + A22 * A22 +
+                     2.0 * (kx * kx + ky * ky + kz * kz);
+  const double tiny = sqrt(mn2) * 0x1p-44;
+  double rec[16];
+  rec[0] = g.al;
+  rec[1] = g.be;
+  rec[13] = rec[14] = rec[15] = 0.0;
+  // H1: column 0, rows 4, 5 below the diagonal
+  flush(A00, tiny); flush(A40, tiny); flush(A50, tiny);
+  {
+    double x[2] = {A40, A50};
+    const double tau = reflector<2>(A00, x);
+    const double v4 = x[0], v5 = x[1];
+    double w = (A01 + v5 * A51) * tau;
+    A01 -= w; A41 -= w * v4; A51 -= w * v5;
+    w = (A02 + v4 * A42) * tau;
+    A02 -= w; A42 -= w * v4; A52 -= w * v5;
+    rec[2] = tau; rec[5] = v4; rec[6] = v5;
+  }
+  // H2: column 1, rows 3, 4, 5
+  flush(A11, tiny); flush(A31, tiny); flush(A41, tiny); flush(A51, tiny);
+  {
+    double x[3] = {A31, A41, A51};
+    const double tau = reflector<3>(A11, x);
+    const double v3 = x[0], v4 = x[1], v5 = x[2];
+    const double w = (A12 + v3 * A32 + v4 * A42 + v5 * A52) * tau;
+    A12 -= w; A32 -= w * v3; A42 -= w * v4; A52 -= w * v5;
+    rec[3] = tau; rec[7] = v3; rec[8] = v4; rec[9] = v5;
+  }
+  // H3: column 2, rows 3, 4, 5
+  flush(A22, tiny); flush(A32, tiny); flush(A42, tiny); flush(A52, tiny);
+  {
+    double x[3] = {A32, A42, A52};
+    const double tau = reflector<3>(A22, x);
+    rec[4] = tau; rec[10] = x[0]; rec[11] = x[1]; rec[12] = x[2];
+  }
+  const double L[6] = {A00, A01, A11, A02, A12, A22};
+  store<16>(a, s, rw, rec, g.cp, L);
+}
+
+// ------------------------------------------------- k = 9 (general)
+// A rows: 0-2 = T22_x^T, 3-5 = T22_y^T, 6-8 = K^T.
+__device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
+  Child X, Y;
+  load_node(a, cc.x, X);
+  load_node(a, cc.y, Y);
+  Geo g;
+  geometry(X, Y, g);
+  const double kx = g.sk * g.d[0], ky = g.sk * g.d[1], kz = g.sk * g.d[2];
+  double A00 = X.L[0], A01 = X.L[1], A02 = X.L[3];
+  double A11 = X.L[2], A12 = X.L[4];
+  double A22 = X.L[5];
+  double A30 = Y.L[0], A31 = Y.L[1], A32 = Y.L[3];
+  double A41 = Y.L[2], A42 = Y.L[4];
+  double A52 = Y.L[5];
+  double A61 = kz, A62 = -ky;
+  double A70 = -kz, A71 = 0.0, A72 = kx;
+  double A80 = ky, A81 = -kx, A82 = 0.0;
+  const double mn2 = A00 * A00 + A01 * A01 + A02 * A02 + A11 * A11 + A12 * A12 + A22 * A22 +
+                     A30 * A30 + A31 * A31 + A32 * A32 + A41 * A41 + A42 * A42 + A52 * A52 +
+                     2.0 * (kx * kx + ky * ky + kz * kz);
+  const double tiny = sqrt(mn2) * 0x1p-44;
+  double rec[20];
+  rec[0] = g.al;
+  rec[1] = g.be;
+  rec[19] = 0.0;
+  // H1: column 0, rows 3, 7, 8
+  flush(A00, tiny); flush(A30, tiny); flush(A70, tiny); flush(A80, tiny);
+  {
+    double x[3] = {A30, A70, A80};
+    const double tau = reflector<3>(A00, x);
+    const double v3 = x[0], v7 = x[1], v8 = x[2];
+    double w = (A01 + v3 * A31 + v8 * A81) * tau;
+    A01 -= w; A31 -= w * v3; A71 -= w * v7; A81 -= w * v8;
+    w = (A02 + v3 * A32 + v7 * A72) * tau;
+    A02 -= w; A32 -= w * v3; A72 -= w * v7; A82 -= w * v8;
+    rec[2] = tau; rec[5] = v3; rec[6] = v7; rec[7] = v8;
+  }
+  // H2: column 1, rows 3, 4, 6, 7, 8
+  flush(A11, tiny); flush(A31, tiny); flush(A41, tiny); flush(A61, tiny); flush(A71, tiny); flush(A81, tiny);
+  {
+    double x[5] = {A31, A41, A61, A71, A81};
+    const double tau = reflector<5>(A11, x);
+    const double v3 = x[0], v4 = x[1], v6 = x[2], v7 = x[3], v8 = x[4];
+    const double w = (A12 + v3 * A32 + v4 * A42 + v6 * A62 + v7 * A72 + v8 * A82) * tau;
+    A12 -= w; A32 -= w * v3; A42 -= w * v4; A62 -= w * v6; A72 -= w * v7; A82 -= w * v8;
+    rec[3] = tau; rec[8] = v3; rec[9] = v4; rec[10] = v6; rec[11] = v7; rec[12] = v8;
+  }
+  // H3: column 2, rows 3..8
+  flush(A22, tiny); flush(A32, tiny); flush(A42, tiny); flush(A52, tiny); flush(A62, tiny);
+  flush(A72, tiny); flush(A82, tiny);
+  {
+    double x[6] = {A32, A42, A52, A62, A72, A82};
+    const double tau = reflector<6>(A22, x);
+    rec[4] = tau;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) rec[13 + i] = x[i];
+  }
+  const double L[6] = {A00, A01, A11, A02, A12, A22};
+  store<20>(a, s, rw, rec, g.cp, L);
+}
+
+__device__ __forceinline__ void build_slot(const BuildArgs& a, int64_t s, int type, int64_t rw) {
+  const int2 cc = a.sc[s];
+  if (type == 0) node_case1(a, s, cc, rw);
+  else if (type == 1) node_hh6(a, s, cc, rw);
+  else node_hh9(a, s, cc, rw);
+}
+
+__global__ void __launch_bounds__(kThreads) k_build_level(BuildArgs a, int h) {
+  const int b0 = 3 * (h - 1);
+  const int32_t s0 = a.bstart[b0], s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
+  const int32_t r0 = a.brec[b0], r1 = a.brec[b0 + 1], r2 = a.brec[b0 + 2];
+  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    if (s < s1) build_slot(a, s, 0, r0 + (s - s0) * rec_words(0));
+    else if (s < s2) build_slot(a, s, 1, r1 + (s - s1) * rec_words(1));
+    else build_slot(a, s, 2, r2 + (s - s2) * rec_words(2));
   }
 }
 
-// Range [lo, hi) of the sorted top-node list holding ids in [a, b).
-__device__ inline void top_range(const int32_t* top, int ntop, int64_t a, int64_t b, int* lo,
-                                 int* hi) {
-  int l = 0, r = ntop;
-  while (l < r) { int md = (l + r) >> 1; if (top[md] < a) l = md + 1; else r = md; }
-  *lo = l;
-  r = ntop;
-  while (l < r) { int md = (l + r) >> 1; if (top[md] < b) l = md + 1; else r = md; }
-  *hi = l;
-}
-
-__global__ void __launch_bounds__(kThreads) k_build_top(BuildArgs a) {
-  const int32_t j = a.top_bodies[blockIdx.x];
-  const int64_t nb = a.off[j] - j, ne = a.off[j + 1] - (j + 1);
-  int lo, hi;
-  top_range(a.top, a.counters[1], nb, ne, &lo, &hi);
-  const int H = a.height[a.root[j]];
-  for (int h = 1; h <= H; ++h) {
-    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      const int32_t q = a.top[p];
-      if (a.height[q] == h) build_node(a, q);
+// Nodes above the cut: one block per body, height by height.
+__global__ void __launch_bounds__(kThreads) k_build_tail(BuildArgs a) {
+  const int32_t j = blockIdx.x;
+  const int bt = 3 * a.cut;
+  const int32_t t0 = a.bstart[bt], t1 = a.bstart[bt + 1];
+  int32_t lo, hi;
+  id_range(a.sid, t0, t1, a.off[j] - j, a.off[j + 1] - (j + 1), &lo, &hi);
+  if (lo == hi) return;
+  const int H = a.sheight[a.root_slot[j]];
+  const int32_t rt = a.brec[bt];
+  for (int h = a.cut + 1; h <= H; ++h) {
+    for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+      if (a.sheight[s] != h) continue;
+      const int2 cc = a.sc[s];
+      build_slot(a, s, (cc.x >= 0) + (cc.y >= 0), rt + (int64_t)(s - t0) * kRecMax);
     }
     __syncthreads();
   }
@@ -284,26 +350,25 @@ __global__ void __launch_bounds__(kThreads) k_build_top(BuildArgs a) {
 
 }  // namespace
 
-zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z) {
+zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which) {
   BuildArgs a;
   a.x = x; a.y = y; a.z = z;
-  a.off = c.off; a.m = c.m;
-  a.perm = c.perm; a.cl = c.cl; a.cr = c.cr; a.cnt = c.cnt; a.first = c.first;
-  a.height = c.height; a.tiles = c.tiles; a.top = c.top; a.counters = c.counters;
-  a.top_bodies = c.top_d; a.root = c.root;
-  a.st64 = c.st64; a.rec64 = c.rec64; a.rec32 = c.rec32; a.err = c.counters + 2;
-  const size_t smem = (size_t)c.tile * sizeof(uint16_t);
-  const int grid = c.num_sms * 8;
-  time_begin(c, "build_tiles");
-  k_build_tiles<<<grid, kThreads, smem, c.stream>>>(a);
-  time_end(c, "build_tiles");
-  ZQ_CUDA_TRY(cudaGetLastError());
-  if (!c.top_bodies.empty()) {
-    time_begin(c, "build_top");
-    k_build_top<<<(unsigned)c.top_bodies.size(), kThreads, 0, c.stream>>>(a);
-    time_end(c, "build_top");
-    ZQ_CUDA_TRY(cudaGetLastError());
+  a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.scnt = c.scnt; a.sheight = c.sheight; a.sid = c.sid;
+  a.bstart = c.bstart; a.brec = c.brec; a.root_slot = c.root_slot; a.cut = c.cut;
+  a.st64 = c.st64;
+  a.rec64 = (which & 1) ? c.rec64 : nullptr;
+  a.rec32 = (which & 2) ? c.rec32 : nullptr;
+  a.err = c.counters + 2;
+  const int grid = c.num_sms * 4;
+  for (int h = 1; h <= c.cut; ++h) {
+    time_begin(c, "build_level");
+    k_build_level<<<grid, kThreads, 0, c.stream>>>(a, h);
+    time_end(c, "build_level");
   }
+  time_begin(c, "build_tail");
+  k_build_tail<<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
+  time_end(c, "build_tail");
+  ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }
 

@@ -15,14 +15,30 @@ namespace zq {
 constexpr int kQBits = 21;            // bits per coordinate (Sec. 2.1 quantisation)
 constexpr int kMaxHeight = 96;        // 63 coordinate + 32 index bisection levels + 1
 constexpr int kSmallSortMax = 8192;   // bodies sorted inside one thread block
-constexpr int kDefaultTile = 2048;    // beads per sweep tile
-constexpr int kMaxTile = 4096;      // FP64 sweep tile: 4096 * 50 B of shared memory
+// Schedule: nodes of height 1..cut are processed level by level over all
+// bodies at once, sorted by (height, type) into 3 * cut buckets (type 0:
+// two leaf children, k = 3; 1: one, k = 6; 2: none, k = 9); the nodes
+// above the cut ("tail") form one more bucket, processed one block per body.
+constexpr int kDefaultCut = 15;
+constexpr int kMaxCut = 21;           // 3 * 21 + 1 = 64 buckets
+constexpr int kMaxBuckets = 3 * kMaxCut + 1;
 
-// Node record: one per internal node, float or double, kRec words.
-//   [0] sqrt(n_x/n)  [1] sqrt(n_y/n)  [2..4] tau_1..tau_3 (Householder)
-//   [5 ...] reflector tails v_1(2..k), v_2(3..k), v_3(4..k)  (k = 6, 9)
-//   [5 .. 13] G row-major (k = 3, Case I)
-// k = 3 + 3 * (number of internal children); the children are in the tree.
+// Node records (float or double words), compact and type-specific.  With
+// A = M^T (k x 3) built from [T22_x | T22_y | K], K = sqrt(n_x n_y/n)[d]x,
+// the Householder vectors of the LQ have structural zeros; only the
+// possibly nonzero entries are stored (0-based row indices of A):
+//   type 0 (k = 3, Case I), 12 words: [0] alpha [1] beta [2..10] G row-major
+//   type 1 (k = 6: rows 0-2 T22 of the internal child, 3-5 K), 16 words:
+//     [0] alpha [1] beta [2..4] tau_1..3 [5,6] v1(4,5) [7..9] v2(3,4,5)
+//     [10..12] v3(3,4,5)
+//   type 2 (k = 9: rows 0-2 T22_x, 3-5 T22_y, 6-8 K), 20 words:
+//     [0] alpha [1] beta [2..4] tau [5..7] v1(3,7,8) [8..12] v2(3,4,6,7,8)
+//     [13..18] v3(3..8)
+// (v_j(j) = 1 implicit.)  Records of a (height, type) bucket are contiguous;
+// tail records use 20-word slots.
+__host__ __device__ constexpr int rec_words(int type) { return type == 0 ? 12 : (type == 1 ? 16 : 20); }
+constexpr int kRecMax = 20;
+// Dense export layout (zq_get_records): 28 doubles per node.
 constexpr int kRec = 28;
 // FP64 build state per node: centroid (3), T22 packed lower (6), pad (1).
 constexpr int kState = 10;
@@ -39,19 +55,19 @@ struct Ctx {
   int64_t cap_N = 0, cap_m = 0;
   // current problem
   int64_t N = 0, m = 0, nodes = 0, R = 0;
-  int tile = kDefaultTile;
-  bool have_tree = false, have_xform = false;
+  int cut = kDefaultCut;
+  bool have_tree = false, have_xform = false, have64 = false, have32 = false;
   std::vector<int64_t> off_h;
   std::vector<int32_t> small_bodies;  // n_j <= kSmallSortMax
   std::vector<int32_t> big_bodies;    // n_j > kSmallSortMax (device radix sort)
-  std::vector<int32_t> top_bodies;    // n_j > tile (have nodes above the tiles)
   int32_t max_small = 0;
   // device buffers (bodies)
   int64_t* off = nullptr;        // [m+1]
   int32_t* small_d = nullptr;    // [m] ids of small bodies
-  int32_t* top_d = nullptr;      // [m] ids of bodies with top nodes
+  int32_t* bead_body = nullptr;  // [N] body of each bead / sorted position
   uint64_t* aabb = nullptr;      // [m * 6] ordered-int encoded lo[3], hi[3]
   int32_t* root = nullptr;       // [m] root node id
+  int32_t* root_slot = nullptr;  // [m] root slot
   // beads
   uint64_t* key = nullptr;       // [N] Morton keys in bead order
   uint64_t* skey = nullptr;      // [N] keys in sorted order
@@ -67,18 +83,26 @@ struct Ctx {
   int32_t* first = nullptr;      // [nodes] first sorted position
   int32_t* cnt = nullptr;        // [nodes] beads below
   uint8_t* height = nullptr;     // [nodes]
-  int32_t* parent = nullptr;     // [nodes] (-1 at a body root)
   int32_t* flag = nullptr;       // [nodes] bottom-up arrival counters
   int32_t* roff = nullptr;       // [nodes] residue offsets
   int32_t* scan_tmp = nullptr;   // [nodes + blocks] scan workspace
-  int32_t* tiles = nullptr;      // [nodes] tile-root ids
-  int32_t* top = nullptr;        // [nodes] ids of nodes above the tiles
-  int32_t* counters = nullptr;   // [4]: ntiles, ntop, err, spare
-  // transforms
+  int32_t* counters = nullptr;   // [4]: spare, spare, err, spare
+  // schedule, indexed by slot (the processing order; see kDefaultCut)
+  int32_t* sid = nullptr;        // [nodes] slot -> node id
+  int32_t* slot_of = nullptr;    // [nodes] node id -> slot
+  int2* sc = nullptr;            // [nodes] child codes: >= 0 child slot, < 0 leaf
+  int32_t* sroff = nullptr;      // [nodes] residue offset
+  int32_t* scnt = nullptr;       // [nodes] beads below
+  uint8_t* sheight = nullptr;    // [nodes] height
+  int32_t* bstart = nullptr;     // [kMaxBuckets + 1] first slot of each bucket
+  int32_t* brec = nullptr;       // [kMaxBuckets + 1] first record word of each bucket
+  int32_t* bhist = nullptr;      // bucket-sort histograms
+  int64_t bhist_cap = 0;
+  // transforms, by slot
   double* st64 = nullptr;        // [nodes * kState]
-  double* rec64 = nullptr;       // [nodes * kRec]
-  float* rec32 = nullptr;        // [nodes * kRec]
-  // sweep scratch: Info-sets / Velocity-sets of nodes outside the tiles
+  double* rec64 = nullptr;       // [nodes * kRecMax] compact records
+  float* rec32 = nullptr;        // [nodes * kRecMax]
+  // sweep scratch: Info-sets / Velocity-sets by slot
   double* x64 = nullptr;         // [nodes * 6]
   float* x32 = nullptr;          // [nodes * 6]
   // staging for host-buffer calls (bytes)
@@ -87,14 +111,18 @@ struct Ctx {
   // kernel timing hook
   char time_name[32] = {0};
   cudaEvent_t time_ev0 = nullptr, time_ev1 = nullptr;
-  int64_t launches = 0;  // kernels launched by this context
+  bool time_started = false;  // start recorded in the current API call
+  int64_t launches = 0;       // kernels launched by this context
 };
 
 // Every kernel launch goes through time_begin / time_end: counts the launch
 // and brackets it with the caller's events when it is the timed kernel.
 inline void time_begin(Ctx& c, const char* name) {
   ++c.launches;
-  if (c.time_ev0 && __builtin_strcmp(c.time_name, name) == 0) cudaEventRecord(c.time_ev0, c.stream);
+  if (c.time_ev0 && !c.time_started && __builtin_strcmp(c.time_name, name) == 0) {
+    cudaEventRecord(c.time_ev0, c.stream);
+    c.time_started = true;
+  }
 }
 inline void time_end(const Ctx& c, const char* name) {
   if (c.time_ev1 && __builtin_strcmp(c.time_name, name) == 0) cudaEventRecord(c.time_ev1, c.stream);
@@ -103,6 +131,23 @@ inline void time_end(const Ctx& c, const char* name) {
 // --------------------------------------------------------------- helpers
 __host__ __device__ inline bool is_leaf(int32_t code) { return code < 0; }
 __host__ __device__ inline int32_t leaf_pos(int32_t code) { return -1 - code; }
+
+// Bucket of a node of height h and type t (see kDefaultCut).
+__host__ __device__ inline int bucket_of(int h, int t, int cut) {
+  return h <= cut ? 3 * (h - 1) + t : 3 * cut;
+}
+
+// Range [lo, hi) of slots in [a, b) whose node id lies in [ida, idb); the
+// node ids of those slots increase with the slot.
+__device__ inline void id_range(const int32_t* __restrict__ sid, int32_t a, int32_t b, int64_t ida,
+                                int64_t idb, int32_t* lo, int32_t* hi) {
+  int32_t l = a, r = b;
+  while (l < r) { int32_t md = (l + r) >> 1; if (sid[md] < ida) l = md + 1; else r = md; }
+  *lo = l;
+  r = b;
+  while (l < r) { int32_t md = (l + r) >> 1; if (sid[md] < idb) l = md + 1; else r = md; }
+  *hi = l;
+}
 
 // Body of a global sorted position / bead index: largest j with off[j] <= i.
 __device__ inline int32_t body_of_bead(const int64_t* __restrict__ off, int64_t m, int64_t i) {
@@ -142,6 +187,8 @@ __device__ inline double ord_decode(unsigned long long u) {
 // ---------------------------------------------------- launchers (per TU)
 // zq_tree.cu
 zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z);
+zq_status launch_bead_body(Ctx& c);
+int64_t bucket_hist_words(int64_t nodes);
 // zq_sort.cu
 zq_status launch_sort(Ctx& c);
 // zq_scan.cu
@@ -149,7 +196,8 @@ zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t
                                 int32_t* total);
 int64_t scan_tmp_words(int64_t n);
 // zq_build.cu
-zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z);
+// which: bit 0 = FP64 records, bit 1 = FP32 records
+zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which);
 // zq_apply.cu
 zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t ldv, void* out);
 zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t ldo);

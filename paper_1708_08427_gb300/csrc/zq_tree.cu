@@ -10,7 +10,10 @@
 //    parent (range, count, height, residue size 0/3/6 of Sec. 3) -- pruning
 //    of empty boxes and collapse of single-child chains are implicit;
 // 6. residue offsets by prefix sum over node ids (split-position order,
-//    bodies concatenated), and the tile / top classification of the sweeps.
+//    bodies concatenated);
+// 7. the processing schedule: a stable bucket sort of the nodes by
+//    (height, type) for heights up to the cut, the rest ("tail") last in
+//    node-id order; node data is then re-laid out by slot.
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -19,14 +22,20 @@ namespace {
 
 constexpr int kThreads = 256;
 
+__global__ void k_bead_body(const int64_t* __restrict__ off, int64_t m, int64_t N,
+                            int32_t* __restrict__ bead_body) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) bead_body[i] = body_of_bead(off, m, i);
+}
+
 __global__ void k_aabb(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, const int64_t* __restrict__ off, int64_t m,
+                       const double* __restrict__ z, const int32_t* __restrict__ bead_body,
                        int64_t N, unsigned long long* __restrict__ lo,
                        unsigned long long* __restrict__ hi, int32_t* __restrict__ err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = i < N;
-  const int32_t j = valid ? body_of_bead(off, m, i) : -1;
+  const int32_t j = valid ? bead_body[i] : -1;
   double p[3] = {valid ? x[i] : 0.0, valid ? y[i] : 0.0, valid ? z[i] : 0.0};
   if (valid && !(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(err, kErrNonFinite);
   const int32_t j0 = __shfl_sync(0xffffffffu, j, 0);
@@ -77,12 +86,12 @@ __device__ inline uint32_t quantise(double p, double lo, double hi) {
 }
 
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, const int64_t* __restrict__ off, int64_t m,
+                       const double* __restrict__ z, const int32_t* __restrict__ bead_body,
                        int64_t N, const unsigned long long* __restrict__ lo,
                        const unsigned long long* __restrict__ hi, uint64_t* __restrict__ key) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int32_t j = body_of_bead(off, m, i);
+  const int32_t j = bead_body[i];
   uint32_t q[3];
   const double p[3] = {x[i], y[i], z[i]};
 #pragma unroll
@@ -92,14 +101,15 @@ __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ 
 
 // Depth of the bisection separating sorted neighbours s and s+1 of a body:
 // 63 coordinate levels (key bit 62 - l) followed by 32 index levels.
-__global__ void k_lcp(const int64_t* __restrict__ off, int64_t m, int64_t nodes,
-                      const uint64_t* __restrict__ skey, const int32_t* __restrict__ perm,
+__global__ void k_lcp(const int64_t* __restrict__ off, const int32_t* __restrict__ bead_body,
+                      int64_t N, const uint64_t* __restrict__ skey, const int32_t* __restrict__ perm,
                       uint8_t* __restrict__ lcp) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nodes) return;
-  const int32_t j = body_of_node(off, m, q);
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // sorted position
+  if (s >= N) return;
+  const int32_t j = bead_body[s];
+  if (s == off[j + 1] - 1) return;  // last bead of a body: no split after it
   const int64_t o = off[j];
-  const int64_t s = q + j;  // = o + (q - (o - j))
+  const int64_t q = s - j;          // node of the split between s and s + 1
   const uint64_t k1 = skey[s], k2 = skey[s + 1];
   int d;
   if (k1 != k2) {
@@ -111,15 +121,15 @@ __global__ void k_lcp(const int64_t* __restrict__ off, int64_t m, int64_t nodes,
   lcp[q] = (uint8_t)d;
 }
 
-__global__ void k_bottom_up(const int64_t* __restrict__ off, int64_t m, int64_t N,
-                            const uint8_t* __restrict__ lcp, int32_t* __restrict__ cl,
+__global__ void k_bottom_up(const int64_t* __restrict__ off, const int32_t* __restrict__ bead_body,
+                            int64_t N, const uint8_t* __restrict__ lcp, int32_t* __restrict__ cl,
                             int32_t* __restrict__ cr, int32_t* __restrict__ first,
                             int32_t* __restrict__ cnt, uint8_t* __restrict__ height,
-                            int32_t* __restrict__ parent, int32_t* __restrict__ flag,
-                            int32_t* __restrict__ res, int32_t* __restrict__ root) {
+                            int32_t* __restrict__ flag, int32_t* __restrict__ res,
+                            int32_t* __restrict__ root) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N) return;
-  const int32_t j = body_of_bead(off, m, s);
+  const int32_t j = bead_body[s];
   const int64_t o = off[j];
   const int32_t n = (int32_t)(off[j + 1] - o);
   const int64_t nb = o - j;
@@ -143,7 +153,6 @@ __global__ void k_bottom_up(const int64_t* __restrict__ off, int64_t m, int64_t 
       cr[q] = code;
       cnt[q] = r;  // the parent's last local position, until completion
     }
-    if (code >= 0) parent[code] = (int32_t)q;
     __threadfence();
     if (atomicAdd(&flag[q], 1) == 0) break;  // the sibling completes q
     __threadfence();
@@ -168,40 +177,143 @@ __global__ void k_bottom_up(const int64_t* __restrict__ off, int64_t m, int64_t 
   }
 }
 
-__global__ void k_flags(const int32_t* __restrict__ cnt, const int32_t* __restrict__ parent,
-                        int64_t nodes, int tile, int want_top, int32_t* __restrict__ f) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nodes) return;
-  const int32_t c = cnt[q];
-  int32_t v;
-  if (want_top) {
-    v = c > tile;
-  } else {
-    const int32_t p = parent[q];
-    v = (c <= tile) && (p < 0 || cnt[p] > tile);
-  }
-  f[q] = v;
+// ------------------------------------------------------- schedule
+constexpr int kBItems = 16;
+constexpr int kBTile = kThreads * kBItems;
+
+__device__ inline int node_bucket(const uint8_t* __restrict__ height, const int32_t* __restrict__ cl,
+                                  const int32_t* __restrict__ cr, int64_t q, int cut) {
+  return bucket_of(height[q], (cl[q] >= 0) + (cr[q] >= 0), cut);
 }
 
-__global__ void k_compact(const int32_t* __restrict__ cnt, const int32_t* __restrict__ parent,
-                          int64_t nodes, int tile, int want_top, const int32_t* __restrict__ pos,
-                          int32_t* __restrict__ list) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nodes) return;
-  const int32_t c = cnt[q];
-  bool v;
-  if (want_top) {
-    v = c > tile;
-  } else {
-    const int32_t p = parent[q];
-    v = (c <= tile) && (p < 0 || cnt[p] > tile);
+__global__ void __launch_bounds__(kThreads)
+k_bucket_count(const uint8_t* __restrict__ height, const int32_t* __restrict__ cl,
+               const int32_t* __restrict__ cr, int64_t nodes, int cut, int nb,
+               int32_t* __restrict__ hist, int64_t nblk) {
+  __shared__ int32_t cnt[kMaxBuckets];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kBTile + (int64_t)threadIdx.x * kBItems;
+  for (int i = 0; i < kBItems; ++i)
+    if (base + i < nodes) atomicAdd(&cnt[node_bucket(height, cl, cr, base + i, cut)], 1);
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(int64_t)b * nblk + blockIdx.x] = cnt[b];
+}
+
+// Stable scatter: nodes keep increasing id order inside each bucket.
+__global__ void __launch_bounds__(kThreads)
+k_bucket_scatter(const uint8_t* __restrict__ height, const int32_t* __restrict__ cl,
+                 const int32_t* __restrict__ cr, int64_t nodes, int cut, int nb,
+                 const int32_t* __restrict__ hist, int64_t nblk, int32_t* __restrict__ sid,
+                 int32_t* __restrict__ slot_of) {
+  extern __shared__ int32_t cur[];  // [nb][kThreads]
+  __shared__ int32_t sh[33], bb[kMaxBuckets];
+  const int t = threadIdx.x;
+  for (int b = 0; b < nb; ++b) cur[b * kThreads + t] = 0;
+  const int64_t base = (int64_t)blockIdx.x * kBTile + (int64_t)t * kBItems;
+  for (int i = 0; i < kBItems; ++i)
+    if (base + i < nodes) ++cur[node_bucket(height, cl, cr, base + i, cut) * kThreads + t];
+  __syncthreads();
+  // exclusive scan of cur in (bucket, thread) order: thread t owns entries
+  // [t * nb, (t + 1) * nb) of the flattened array
+  int32_t s = 0;
+  for (int f = t * nb; f < (t + 1) * nb; ++f) s += cur[f];
+  const int lane = t & 31, warp = t >> 5;
+  int32_t inc = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
   }
-  if (v) list[pos[q]] = (int32_t)q;
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t wv = (lane < kThreads / 32) ? sh[lane] : 0;
+    int32_t wi = wv;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int32_t o = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += o;
+    }
+    sh[lane] = wi - wv;
+  }
+  __syncthreads();
+  int32_t run = inc - s + sh[warp];
+  for (int f = t * nb; f < (t + 1) * nb; ++f) {
+    const int32_t v = cur[f];
+    cur[f] = run;
+    run += v;
+  }
+  __syncthreads();
+  for (int b = t; b < nb; b += kThreads) bb[b] = cur[b * kThreads];
+  __syncthreads();
+  for (int i = 0; i < kBItems; ++i) {
+    const int64_t q = base + i;
+    if (q < nodes) {
+      const int b = node_bucket(height, cl, cr, q, cut);
+      const int32_t pos = hist[(int64_t)b * nblk + blockIdx.x] + (cur[b * kThreads + t]++ - bb[b]);
+      sid[pos] = (int32_t)q;
+      slot_of[q] = pos;
+    }
+  }
+}
+
+__global__ void k_bucket_starts(const int32_t* __restrict__ hist, int64_t nblk, int nb, int64_t nodes,
+                                int32_t* __restrict__ bstart, int32_t* __restrict__ brec) {
+  __shared__ int32_t st[kMaxBuckets + 1];
+  const int b = threadIdx.x;
+  if (b < nb) st[b] = hist[(int64_t)b * nblk];
+  if (b == nb) st[nb] = (int32_t)nodes;
+  __syncthreads();
+  if (b <= nb) bstart[b] = st[b];
+  if (b == 0) {
+    int32_t w = 0;
+    for (int k = 0; k < nb; ++k) {
+      brec[k] = w;
+      w += (st[k + 1] - st[k]) * (k == nb - 1 ? kRecMax : rec_words(k % 3));
+    }
+    brec[nb] = w;
+  }
+}
+
+__global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
+                            const int32_t* __restrict__ slot_of, const int32_t* __restrict__ cl,
+                            const int32_t* __restrict__ cr, const int32_t* __restrict__ roff,
+                            const int32_t* __restrict__ cnt, const uint8_t* __restrict__ height,
+                            int2* __restrict__ sc, int32_t* __restrict__ sroff,
+                            int32_t* __restrict__ scnt, uint8_t* __restrict__ sheight) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nodes) return;
+  const int32_t q = sid[s];
+  const int32_t a = cl[q], b = cr[q];
+  sc[s] = make_int2(a >= 0 ? slot_of[a] : a, b >= 0 ? slot_of[b] : b);
+  sroff[s] = roff[q];
+  scnt[s] = cnt[q];
+  sheight[s] = height[q];
+}
+
+__global__ void k_root_slots(int64_t m, const int32_t* __restrict__ root,
+                             const int32_t* __restrict__ slot_of, int32_t* __restrict__ root_slot) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) root_slot[j] = slot_of[root[j]];
 }
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 }  // namespace
+
+int64_t bucket_hist_words(int64_t nodes) {
+  const int64_t nblk = (nodes + kBTile - 1) / kBTile;
+  return kMaxBuckets * nblk + scan_tmp_words(kMaxBuckets * nblk);
+}
+
+zq_status launch_bead_body(Ctx& c) {
+  time_begin(c, "bead_body");
+  k_bead_body<<<blocks(c.N), kThreads, 0, c.stream>>>(c.off, c.m, c.N, c.bead_body);
+  time_end(c, "bead_body");
+  ZQ_CUDA_TRY(cudaGetLastError());
+  return ZQ_OK;
+}
 
 zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z) {
   cudaStream_t s = c.stream;
@@ -211,38 +323,52 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
   ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
   time_begin(c, "aabb");
-  k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.off, c.m, c.N, lo, hi, err);
+  k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.N, lo, hi, err);
   time_end(c, "aabb");
   time_begin(c, "keys");
-  k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.off, c.m, c.N, lo, hi, c.key);
+  k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.N, lo, hi, c.key);
   time_end(c, "keys");
   ZQ_CUDA_TRY(cudaGetLastError());
   zq_status st = launch_sort(c);
   if (st != ZQ_OK) return st;
   time_begin(c, "lcp");
-  k_lcp<<<blocks(c.nodes), kThreads, 0, s>>>(c.off, c.m, c.nodes, c.skey, c.perm, c.lcp);
+  k_lcp<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.skey, c.perm, c.lcp);
   time_end(c, "lcp");
   ZQ_CUDA_TRY(cudaMemsetAsync(c.flag, 0, c.nodes * sizeof(int32_t), s));
-  ZQ_CUDA_TRY(cudaMemsetAsync(c.parent, 0xff, c.nodes * sizeof(int32_t), s));
   time_begin(c, "bottom_up");
-  k_bottom_up<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.m, c.N, c.lcp, c.cl, c.cr, c.first, c.cnt,
-                                               c.height, c.parent, c.flag, c.roff, c.root);
+  k_bottom_up<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.lcp, c.cl, c.cr, c.first,
+                                               c.cnt, c.height, c.flag, c.roff, c.root);
   time_end(c, "bottom_up");
   ZQ_CUDA_TRY(cudaGetLastError());
   st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
   if (st != ZQ_OK) return st;
-  for (int want_top = 0; want_top < 2; ++want_top) {
-    time_begin(c, "classify");
-    k_flags<<<blocks(c.nodes), kThreads, 0, s>>>(c.cnt, c.parent, c.nodes, c.tile, want_top, c.flag);
-    time_end(c, "classify");
-    st = launch_exclusive_scan(c, c.flag, c.flag, c.nodes, c.scan_tmp, c.counters + want_top);
-    if (st != ZQ_OK) return st;
-    time_begin(c, "classify");
-    k_compact<<<blocks(c.nodes), kThreads, 0, s>>>(c.cnt, c.parent, c.nodes, c.tile, want_top, c.flag,
-                                                   want_top ? c.top : c.tiles);
-    time_end(c, "classify");
-    ZQ_CUDA_TRY(cudaGetLastError());
-  }
+  // schedule
+  const int nb = 3 * c.cut + 1;
+  const int64_t nblk = (c.nodes + kBTile - 1) / kBTile;
+  int32_t* hist = c.bhist;
+  int32_t* tmp = c.bhist + kMaxBuckets * nblk;
+  time_begin(c, "schedule");
+  k_bucket_count<<<(unsigned)nblk, kThreads, 0, s>>>(c.height, c.cl, c.cr, c.nodes, c.cut, nb, hist, nblk);
+  time_end(c, "schedule");
+  st = launch_exclusive_scan(c, hist, hist, nb * nblk, tmp, nullptr);
+  if (st != ZQ_OK) return st;
+  const size_t smem = (size_t)nb * kThreads * sizeof(int32_t);
+  ZQ_CUDA_TRY(cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  time_begin(c, "schedule");
+  k_bucket_scatter<<<(unsigned)nblk, kThreads, smem, s>>>(c.height, c.cl, c.cr, c.nodes, c.cut, nb, hist,
+                                                         nblk, c.sid, c.slot_of);
+  time_end(c, "schedule");
+  time_begin(c, "schedule");
+  k_bucket_starts<<<1, 128, 0, s>>>(hist, nblk, nb, c.nodes, c.bstart, c.brec);
+  time_end(c, "schedule");
+  time_begin(c, "schedule");
+  k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.roff, c.cnt,
+                                                   c.height, c.sc, c.sroff, c.scnt, c.sheight);
+  time_end(c, "schedule");
+  time_begin(c, "schedule");
+  k_root_slots<<<blocks(c.m), kThreads, 0, s>>>(c.m, c.root, c.slot_of, c.root_slot);
+  time_end(c, "schedule");
+  ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }
 

@@ -126,17 +126,17 @@ class Context:
             pass
 
     # ------------------------------------------------------------ builds
-    def build_tree_batched(self, off, x, y, z, tile_beads: int = 0):
+    def build_tree_batched(self, off, x, y, z, level_cut: int = 0):
         off = np.ascontiguousarray(off, dtype=np.int64)
         self._off = off
         m = off.shape[0] - 1
         for t in (x, y, z):
             assert t.is_cuda and t.dtype == self._torch.float64 and t.is_contiguous()
         _check(_lib().zq_build_tree_batched(self._h, m, off.ctypes.data_as(_i64p), _ptr(x), _ptr(y),
-                                            _ptr(z), int(tile_beads)), "zq_build_tree_batched")
+                                            _ptr(z), int(level_cut)), "zq_build_tree_batched")
 
-    def build_tree(self, x, y, z, tile_beads: int = 0):
-        self.build_tree_batched(np.array([0, x.shape[0]], np.int64), x, y, z, tile_beads)
+    def build_tree(self, x, y, z, level_cut: int = 0):
+        self.build_tree_batched(np.array([0, x.shape[0]], np.int64), x, y, z, level_cut)
 
     def build_transforms(self, x, y, z):
         _check(_lib().zq_build_transforms(self._h, _ptr(x), _ptr(y), _ptr(z)), "zq_build_transforms")
@@ -183,7 +183,7 @@ class Context:
         _check(_lib().zq_apply_QT(self._h, self._prec(w), k, _ptr(ww), R, _ptr(out), 3 * N), "zq_apply_QT")
         return out.reshape(3, N) if squeeze else out
 
-    def pipeline(self, off, x, y, z, v=None, qv=None, w=None, qtw=None, tile_beads: int = 0,
+    def pipeline(self, off, x, y, z, v=None, qv=None, w=None, qtw=None, level_cut: int = 0,
                  host: bool = False, keep_tree: bool = False, prec: int | None = None):
         """One step: tree, FP64 transforms, qv = Q~ v, qtw = Q~^T w.  With
         host=True all tensors are (pinned) host tensors staged by the
@@ -197,7 +197,7 @@ class Context:
         flags = (ZQ_HOST_BUFFERS if host else 0) | (ZQ_KEEP_TREE if keep_tree else 0)
         p = lambda t: None if t is None else _ptr(t)
         _check(_lib().zq_pipeline(self._h, prec, m, off.ctypes.data_as(_i64p), _ptr(x), _ptr(y), _ptr(z),
-                                  p(v), p(qv), p(w), p(qtw), int(tile_beads), flags), "zq_pipeline")
+                                  p(v), p(qv), p(w), p(qtw), int(level_cut), flags), "zq_pipeline")
 
     def time_kernel(self, name: str | None, start=None, stop=None):
         """Bracket launches of kernel `name` with torch.cuda.Event start/stop

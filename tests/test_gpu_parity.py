@@ -2,9 +2,11 @@
 
 Tree and index construction: bit-exact.  FP64 transforms and sweeps:
 relative error <= 1e-12; FP32 sweeps: <= 1e-5 (per body, 2-norm relative to
-the oracle's result).  Sizes span several tiles and ragged tails; edge
-cases: 3-bead bodies, flat and far-off bodies, coincident beads, bodies that
-need the device radix sort, the largest tile, and the full-size workloads.
+the oracle's result).  Sizes span many thread blocks, per-height launches
+and per-body launches, with ragged bucket boundaries; edge cases: 3-bead
+bodies, flat and far-off bodies, coincident beads, collinear and lattice
+bodies, bodies that need the device radix sort, the lowest and highest
+level cut, and the full-size workloads.
 """
 import numpy as np
 import pytest
@@ -30,12 +32,12 @@ def _zq():
     return zq
 
 
-def make_ctx(bt, tile=0):
+def make_ctx(bt, cut=0):
     dev = _dev()
     zq = _zq()
     x, y, z = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (bt.x, bt.y, bt.z))
     ctx = zq.Context(0)
-    ctx.build_tree_batched(bt.off, x, y, z, tile)
+    ctx.build_tree_batched(bt.off, x, y, z, cut)
     ctx.build_transforms(x, y, z)
     return ctx, (x, y, z)
 
@@ -137,7 +139,7 @@ def test_single_body_256_sixteen_vectors():
     """n = 256 shell of radius 2 with N(0, 0.05^2) jitter, 16 right-hand
     sides; bisection tree exact, FP64 and FP32 sweeps."""
     bt = W.shell_body(256, radius=2.0, sigma=0.05, seed=0)
-    ctx, _ = make_ctx(bt, tile=64)
+    ctx, _ = make_ctx(bt, cut=3)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_nodes(ctx, bt, bodies)
@@ -145,12 +147,13 @@ def test_single_body_256_sixteen_vectors():
     check_apply(ctx, bt, np.float32, k=16, seed=1)
 
 
-@pytest.mark.parametrize("tile", [64, 512, 4096])
-def test_batch_ragged_tiles(tile):
-    """Bodies from 3 to 700 beads: many tiles per body for small tiles,
-    nodes above the tiles, 3-bead bodies."""
+@pytest.mark.parametrize("cut", [1, 4, 15, 21])
+def test_batch_ragged_levels(cut):
+    """Bodies from 3 to 700 beads; a low level cut sends most nodes through
+    the per-body kernels, a high one through the per-height kernels; bucket
+    boundaries fall inside warps; 3-bead bodies."""
     bt = W.shell_batch(m=60, nmin=3, nmax=700, seed=4)
-    ctx, _ = make_ctx(bt, tile=tile)
+    ctx, _ = make_ctx(bt, cut=cut)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_nodes(ctx, bt, bodies)
@@ -158,15 +161,15 @@ def test_batch_ragged_tiles(tile):
     check_apply(ctx, bt, np.float32, seed=3)
 
 
-def test_results_do_not_depend_on_tile():
+def test_results_do_not_depend_on_level_cut():
     bt = W.shell_batch(m=20, nmin=50, nmax=2000, seed=8)
     dev = _dev()
     rng = np.random.default_rng(5)
     v = torch.from_numpy(rng.standard_normal((3, bt.N))).to(dev)
     w = torch.from_numpy(rng.standard_normal(bt.n_residues)).to(dev)
     outs = []
-    for tile in (64, 300, 2048):
-        ctx, _ = make_ctx(bt, tile=tile)
+    for cut in (1, 6, 15, 21):
+        ctx, _ = make_ctx(bt, cut=cut)
         outs.append((ctx.apply_Q(v).cpu(), ctx.apply_QT(w).cpu(),
                      ctx.apply_Q(v.float()).cpu(), ctx.apply_QT(w.float()).cpu()))
         ctx.sync()
@@ -176,10 +179,10 @@ def test_results_do_not_depend_on_tile():
 
 
 def test_large_body_radix_sort_path():
-    """A body above the per-block sort limit (device radix sort) and above
-    the tile size (nodes above the tiles)."""
+    """A body above the per-block sort limit (device radix sort), with many
+    nodes above the level cut (one block for the whole body's top)."""
     bt = W.ellipsoid_body(n=20000, seed=3)
-    ctx, _ = make_ctx(bt, tile=512)
+    ctx, _ = make_ctx(bt, cut=8)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_nodes(ctx, bt, bodies)
@@ -204,7 +207,7 @@ def test_edge_geometries():
         np.r_[rng.uniform(0, 1, (20, 3)), np.full((4, 3), 0.5)],      # beads sharing one cell
     ]
     bt = _batch_from_points(pts)
-    ctx, _ = make_ctx(bt, tile=64)
+    ctx, _ = make_ctx(bt, cut=3)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_apply(ctx, bt, np.float64)
@@ -216,7 +219,7 @@ def test_coincident_beads_warn():
     p[7] = p[3]
     bt = _batch_from_points([p])
     zq = _zq()
-    ctx, _ = make_ctx(bt, tile=64)
+    ctx, _ = make_ctx(bt, cut=3)
     assert ctx.sync(allow_degenerate=True) == zq.ZQ_WDEGENERATE
     check_tree(ctx, bt, oracle_bodies(bt))
     check_apply(ctx, bt, np.float64)
@@ -227,7 +230,7 @@ def test_non_finite_coordinates_reported():
     bt = W.shell_body(64, seed=2)
     bt.x[5] = np.nan
     with pytest.raises(zq.ZQError) as ei:
-        ctx, _ = make_ctx(bt, tile=64)
+        ctx, _ = make_ctx(bt, cut=3)
         ctx.sync()
     assert ei.value.code == zq.ZQ_ENONFINITE
 
@@ -280,7 +283,7 @@ def test_collinear_and_lattice_bodies_match():
     g = np.arange(64)
     lattice = np.c_[g % 4, (g // 4) % 4, g // 16].astype(float) * 0.3
     bt = _batch_from_points([line, lattice])
-    ctx, _ = make_ctx(bt, tile=64)
+    ctx, _ = make_ctx(bt, cut=3)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_apply(ctx, bt, np.float64)
