@@ -43,9 +43,10 @@
  *     dgeqrf/dorgqr (and hence Matlab qr) computes it: T22 = R(1:3,1:3)^T,
  *     G = Q^T, no sign normalisation; a column whose part below the
  *     diagonal is exactly zero gets no reflection.  Before each reflection,
- *     entries of the column with magnitude <= 2^-44 ||M||_F are set to 0
- *     (rounding noise of an exact zero when M is rank-deficient; LAPACK
- *     would reflect on the noise).
+ *     entries of the column whose binary exponent is more than 40 below
+ *     that of the largest entry of M are set to 0 (rounding noise of an
+ *     exact zero when M is rank-deficient; LAPACK would reflect on the
+ *     noise).
  *   - Case I: G rows are the three rows of U in Eq. 3.10 with the factor
  *     [1, -1]/sqrt(2) removed: g1 = (e_x x d)/|e_x x d|, g2 = dhat x g1,
  *     g3 = -dhat, d = c_x - c_y; T22 = K G^T, which reduces to
@@ -55,6 +56,7 @@
  *     Definition 4.2 / the single-bead remark after Theorem 4.3); the
  *     transform of a node has k = 3 + 3 * (number of internal children).
  */
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -179,20 +181,20 @@ static void lq(const double *M, int k, double *L, double *G) {
   double A[9][3];
   double v[3][9];
   double tau[3];
-  double mn2 = 0.0;
+  int emax = INT_MIN;
   for (int i = 0; i < k; ++i)
     for (int j = 0; j < 3; ++j) {
       A[i][j] = M[j * k + i];
-      mn2 += A[i][j] * A[i][j];
+      if (A[i][j] != 0.0 && ilogb(A[i][j]) > emax) emax = ilogb(A[i][j]);
     }
-  /* Entries of magnitude <= 2^-44 ||M||_F are rounding noise of an exact
-   * zero (rank-deficient M: collinear or coincident beads below the node);
-   * they are set to zero before each reflection, so that the reflection is
-   * a deterministic function of the geometry. */
-  const double tiny = ldexp(sqrt(mn2), -44);
+  /* An entry whose binary exponent is more than 40 below that of the
+   * largest entry of M is rounding noise of an exact zero (rank-deficient
+   * M: collinear or coincident beads below the node); such entries are set
+   * to zero before each reflection, so that the reflection is a
+   * deterministic function of the geometry. */
   for (int j = 0; j < 3; ++j) {
     for (int i = j; i < k; ++i)
-      if (fabs(A[i][j]) <= tiny) A[i][j] = 0.0;
+      if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;
     for (int i = 0; i < k; ++i) v[j][i] = 0.0;
     v[j][j] = 1.0;
     double xn2 = 0.0;

@@ -23,6 +23,7 @@ CHECKS = [
     lambda: P.test_invariants_large(1000),
     lambda: P.test_table1_orthogonality(500),
     lambda: [P.test_node_assembly_eq_3_5(s) for s in range(3)],
+    lambda: P.test_lq_rank_deficient_is_exact_and_valid(),
 ]
 
 failed = 0

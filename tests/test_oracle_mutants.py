@@ -38,6 +38,7 @@ MUTANTS = [
     ("bisect_axis_order_x_first", "int axis = 2 - l % 3; /* z, then y, then x */", "int axis = l % 3;"),
     ("bisect_msb_last", "int bit = QBITS - 1 - l / 3;", "int bit = l / 3;"),
     ("quantise_unnormalised", "double t = (p[a][i] - lo) / (hi - lo);", "double t = (p[a][i] - lo);"),
+    ("no_numerical_zero_rule", "if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;", ";"),
 ]
 
 
