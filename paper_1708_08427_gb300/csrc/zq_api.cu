@@ -26,7 +26,7 @@ zq_status grow(T** p, int64_t count) {
 }
 
 void free_all(Ctx& c) {
-  void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.root, c.root_slot, c.key, c.skey, c.perm,
+  void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.root, c.root_slot, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
                 c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.stage};
@@ -53,6 +53,7 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.small_d, m));
     ZQ_TRY(grow(&c.bead_body, N));
     ZQ_TRY(grow(&c.aabb, 6 * m));
+    ZQ_TRY(grow(&c.body_scale, 3 * m));
     ZQ_TRY(grow(&c.root, m));
     ZQ_TRY(grow(&c.root_slot, m));
     ZQ_TRY(grow(&c.key, N));
@@ -70,6 +71,10 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.roff, nodes));
     ZQ_TRY(grow(&c.scan_tmp, zq::scan_tmp_words(nodes)));
     ZQ_TRY(grow(&c.counters, 4));
+    if (!c.count_tab) {
+      ZQ_TRY(grow(&c.count_tab, 2 * zq::kCountTab));
+      ZQ_TRY(zq::launch_count_table(c));
+    }
     ZQ_TRY(grow(&c.sid, nodes));
     ZQ_TRY(grow(&c.slot_of, nodes));
     ZQ_TRY(grow(&c.sc, nodes));

@@ -9,9 +9,10 @@
 //   M = [T22_p 0] G by Householder reflections of A = M^T (Eq. 3.5; LAPACK
 //       dgeqrf convention: beta_j = -sign(alpha_j) ||x||, no reflection when
 //       the part below the diagonal is exactly zero; T22_p = R^T, G = Q^T);
-//       before each reflection, column entries <= 2^-44 ||M||_F are set to
-//       zero, so rank-deficient M (collinear or coincident beads) give a
-//       transform that does not depend on rounding noise.
+//       before each reflection, column entries whose binary exponent is
+//       more than 40 below that of M's largest entry are set to zero, so
+//       rank-deficient M (collinear or coincident beads) give a transform
+//       that does not depend on rounding noise.
 // Case I (two leaves, Eqs. 3.9-3.10): G rows g1 = (e_x x d)/|e_x x d|
 // (e_y x d when d has no y, z part), g2 = dhat x g1, g3 = -dhat, and
 // T22_p = sqrt(n_x n_y / n) |d| [g2, -g1, 0]; d = 0 gives G = I, T22 = 0
@@ -20,6 +21,12 @@
 // A has structural zeros (T22 blocks are lower triangular, [d]x has a zero
 // diagonal); the reflections below touch only the entries that can be
 // nonzero, which is exact (the skipped products are by exact zeros).
+//
+// FP64 runs at 1/64 of the FP32 rate on this GPU and square roots and
+// divisions expand to long instruction sequences, so: sqrt(n) and
+// 1/sqrt(n) of bead counts come from a table, Case I (n_x = n_y = 1) uses
+// the constants sqrt(1/2) and 1/2, each reflection takes one reciprocal
+// square root and one division, and the zero test works on exponent bits.
 //
 // Schedule: heights 1..cut level by level over all bodies (one launch per
 // height, nodes sorted by type inside a height), then the remaining nodes
@@ -45,6 +52,7 @@ struct BuildArgs {
   const int32_t* bstart;
   const int32_t* brec;
   const int32_t* root_slot;
+  const double* ctab;  // sqrt(n) [0, kCountTab), 1/sqrt(n) [kCountTab, 2 kCountTab)
   int cut;
   double* st64;
   double* rec64;  // compact records (may be null: not wanted)
@@ -53,14 +61,14 @@ struct BuildArgs {
 };
 
 struct Child {
-  double n;
+  int n;
   double c[3];
   double L[6];  // packed lower triangle (L00, L10, L11, L20, L21, L22)
 };
 
 __device__ __forceinline__ void load_leaf(const BuildArgs& a, int32_t code, Child& ch) {
   const int32_t i = a.perm[leaf_pos(code)];
-  ch.n = 1.0;
+  ch.n = 1;
   ch.c[0] = a.x[i];
   ch.c[1] = a.y[i];
   ch.c[2] = a.z[i];
@@ -69,7 +77,7 @@ __device__ __forceinline__ void load_leaf(const BuildArgs& a, int32_t code, Chil
 __device__ __forceinline__ void load_node(const BuildArgs& a, int32_t slot, Child& ch) {
   const double2* s = reinterpret_cast<const double2*>(a.st64 + (int64_t)slot * kState);
   const double2 s0 = s[0], s1 = s[1], s2 = s[2], s3 = s[3], s4 = s[4];
-  ch.n = (double)a.scnt[slot];
+  ch.n = a.scnt[slot];
   ch.c[0] = s0.x; ch.c[1] = s0.y; ch.c[2] = s1.x;
   ch.L[0] = s1.y; ch.L[1] = s2.x; ch.L[2] = s2.y; ch.L[3] = s3.x; ch.L[4] = s3.y; ch.L[5] = s4.x;
 }
@@ -78,17 +86,39 @@ struct Geo {
   double cp[3], d[3], al, be, sk;
 };
 
-__device__ __forceinline__ void geometry(const Child& X, const Child& Y, Geo& g) {
-  const double n = X.n + Y.n, rn = 1.0 / n;
+__device__ __forceinline__ double count_sqrt(const BuildArgs& a, int n) {
+  return n < kCountTab ? __ldg(a.ctab + n) : sqrt((double)n);
+}
+__device__ __forceinline__ double count_rsqrt(const BuildArgs& a, int n) {
+  return n < kCountTab ? __ldg(a.ctab + kCountTab + n) : rsqrt((double)n);
+}
+
+__device__ __forceinline__ void geometry(const BuildArgs& a, const Child& X, const Child& Y, Geo& g) {
+  const double sx = count_sqrt(a, X.n), sy = count_sqrt(a, Y.n), r = count_rsqrt(a, X.n + Y.n);
+  const double rn = r * r, nx = (double)X.n, ny = (double)Y.n;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    g.cp[i] = (X.n * X.c[i] + Y.n * Y.c[i]) * rn;
+    g.cp[i] = (nx * X.c[i] + ny * Y.c[i]) * rn;
     g.d[i] = X.c[i] - Y.c[i];
   }
-  g.al = sqrt(X.n * rn);
-  g.be = sqrt(Y.n * rn);
-  g.sk = sqrt(X.n * Y.n * rn);
+  g.al = sx * r;
+  g.be = sy * r;
+  g.sk = sx * sy * r;
 }
+
+// Case I: n_x = n_y = 1, n = 2.
+__device__ __forceinline__ void geometry_pair(const Child& X, const Child& Y, Geo& g) {
+  constexpr double kRootHalf = 0.70710678118654757;  // sqrt(1/2), correctly rounded
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    g.cp[i] = (X.c[i] + Y.c[i]) * 0.5;
+    g.d[i] = X.c[i] - Y.c[i];
+  }
+  g.al = g.be = g.sk = kRootHalf;
+}
+
+// Biased binary exponent of a double (0 for zero and subnormals).
+__device__ __forceinline__ int bexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
 template <int W>
 __device__ __forceinline__ void store(const BuildArgs& a, int64_t slot, int64_t rw, const double (&rec)[W],
@@ -118,7 +148,7 @@ __device__ void node_case1(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   load_leaf(a, cc.x, X);
   load_leaf(a, cc.y, Y);
   Geo g;
-  geometry(X, Y, g);
+  geometry_pair(X, Y, g);
   double rec[12];
   rec[0] = g.al;
   rec[1] = g.be;
@@ -133,11 +163,11 @@ __device__ void node_case1(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
     for (int i = 0; i < 6; ++i) L[i] = 0.0;
     atomicOr(a.err, kErrDegenerate);
   } else {
-    const double dn = sqrt(dn2), rdn = 1.0 / dn;
+    const double rdn = rsqrt(dn2), dn = dn2 * rdn;
     const double h[3] = {d[0] * rdn, d[1] * rdn, d[2] * rdn};
     double g1[3];
     if (d[1] != 0.0 || d[2] != 0.0) {  // e_x x d, first row of U in Eq. 3.10
-      const double rs = 1.0 / sqrt(d[1] * d[1] + d[2] * d[2]);
+      const double rs = rsqrt(d[1] * d[1] + d[2] * d[2]);
       g1[0] = 0.0; g1[1] = -d[2] * rs; g1[2] = d[1] * rs;
     } else {                            // d along x: e_y x d
       g1[0] = 0.0; g1[1] = 0.0; g1[2] = d[0] > 0.0 ? -1.0 : 1.0;
@@ -175,9 +205,11 @@ __device__ __forceinline__ double reflector(double& al, double (&x)[M]) {
     for (int i = 0; i < M; ++i) x[i] = 0.0;
     return 0.0;
   }
-  const double norm = sqrt(al * al + xn2);
+  const double n2 = al * al + xn2;
+  const double rnorm = rsqrt(n2);
+  const double norm = n2 * rnorm;
   const double be = (al >= 0.0) ? -norm : norm;
-  const double tau = (be - al) / be;
+  const double tau = 1.0 + fabs(al) * rnorm;  // = (be - al) / be
   const double rden = 1.0 / (al - be);
 #pragma unroll
   for (int i = 0; i < M; ++i) x[i] *= rden;
@@ -185,8 +217,9 @@ __device__ __forceinline__ double reflector(double& al, double (&x)[M]) {
   return tau;
 }
 
-__device__ __forceinline__ void flush(double& v, double tiny) {
-  if (fabs(v) <= tiny) v = 0.0;
+// The zero rule: entries whose exponent is more than 40 below the largest.
+__device__ __forceinline__ void flush(double& v, int lim) {
+  if (bexp(v) < lim) v = 0.0;
 }
 
 // ------------------------------------------------- k = 6 (Case II)
@@ -197,7 +230,7 @@ __device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   if (xi) { load_node(a, cc.x, X); load_leaf(a, cc.y, Y); }
   else { load_leaf(a, cc.x, X); load_node(a, cc.y, Y); }
   Geo g;
-  geometry(X, Y, g);
+  geometry(a, X, Y, g);
   const double* Lc = xi ? X.L : Y.L;
   const double kx = g.sk * g.d[0], ky = g.sk * g.d[1], kz = g.sk * g.d[2];
   // columns of A: a0 (rows 0, 4, 5), a1 (rows 0, 1, 3, 5 + fill 4), a2 (rows 0-4 + fill 5)
@@ -207,9 +240,8 @@ __device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   double A31 = kz, A32 = -ky;
   double A40 = -kz, A41 = 0.0, A42 = kx;
   double A50 = ky, A51 = -kx, A52 = 0.0;
-  const double mn2 = A00 * A00 + A01 * A01 + A02 * A02 + A11 * A11 + A12 * A12 + A22 * A22 +
-                     2.0 * (kx * kx + ky * ky + kz * kz);
-  const double tiny = sqrt(mn2) * 0x1p-44;
+  const int tiny = max(max(max(bexp(A00), bexp(A01)), max(bexp(A02), bexp(A11))),
+                       max(max(bexp(A12), bexp(A22)), max(max(bexp(kx), bexp(ky)), bexp(kz)))) - 40;
   double rec[16];
   rec[0] = g.al;
   rec[1] = g.be;
@@ -254,7 +286,7 @@ __device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   load_node(a, cc.x, X);
   load_node(a, cc.y, Y);
   Geo g;
-  geometry(X, Y, g);
+  geometry(a, X, Y, g);
   const double kx = g.sk * g.d[0], ky = g.sk * g.d[1], kz = g.sk * g.d[2];
   double A00 = X.L[0], A01 = X.L[1], A02 = X.L[3];
   double A11 = X.L[2], A12 = X.L[4];
@@ -265,10 +297,10 @@ __device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   double A61 = kz, A62 = -ky;
   double A70 = -kz, A71 = 0.0, A72 = kx;
   double A80 = ky, A81 = -kx, A82 = 0.0;
-  const double mn2 = A00 * A00 + A01 * A01 + A02 * A02 + A11 * A11 + A12 * A12 + A22 * A22 +
-                     A30 * A30 + A31 * A31 + A32 * A32 + A41 * A41 + A42 * A42 + A52 * A52 +
-                     2.0 * (kx * kx + ky * ky + kz * kz);
-  const double tiny = sqrt(mn2) * 0x1p-44;
+  const int tiny = max(max(max(max(bexp(A00), bexp(A01)), max(bexp(A02), bexp(A11))),
+                           max(max(bexp(A12), bexp(A22)), max(bexp(A30), bexp(A31)))),
+                       max(max(max(bexp(A32), bexp(A41)), max(bexp(A42), bexp(A52))),
+                           max(max(bexp(kx), bexp(ky)), bexp(kz)))) - 40;
   double rec[20];
   rec[0] = g.al;
   rec[1] = g.be;
@@ -355,6 +387,7 @@ zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z
   a.x = x; a.y = y; a.z = z;
   a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.scnt = c.scnt; a.sheight = c.sheight; a.sid = c.sid;
   a.bstart = c.bstart; a.brec = c.brec; a.root_slot = c.root_slot; a.cut = c.cut;
+  a.ctab = c.count_tab;
   a.st64 = c.st64;
   a.rec64 = (which & 1) ? c.rec64 : nullptr;
   a.rec32 = (which & 2) ? c.rec32 : nullptr;

@@ -43,6 +43,9 @@ constexpr int kRec = 28;
 // FP64 build state per node: centroid (3), T22 packed lower (6), pad (1).
 constexpr int kState = 10;
 
+// sqrt(n) and 1/sqrt(n) for bead counts n < kCountTab (built once per context).
+constexpr int kCountTab = 1 << 16;
+
 // Device error word bits (reported by zq_sync).
 constexpr int kErrNonFinite = 1;
 constexpr int kErrDegenerate = 2;
@@ -66,6 +69,8 @@ struct Ctx {
   int32_t* small_d = nullptr;    // [m] ids of small bodies
   int32_t* bead_body = nullptr;  // [N] body of each bead / sorted position
   uint64_t* aabb = nullptr;      // [m * 6] ordered-int encoded lo[3], hi[3]
+  double* body_scale = nullptr;  // [m * 3] 1 / (hi - lo) per axis (0 if hi == lo)
+  double* count_tab = nullptr;   // [2 * kCountTab]: sqrt(n), 1/sqrt(n)
   int32_t* root = nullptr;       // [m] root node id
   int32_t* root_slot = nullptr;  // [m] root slot
   // beads
@@ -188,6 +193,7 @@ __device__ inline double ord_decode(unsigned long long u) {
 // zq_tree.cu
 zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z);
 zq_status launch_bead_body(Ctx& c);
+zq_status launch_count_table(Ctx& c);
 int64_t bucket_hist_words(int64_t nodes);
 // zq_sort.cu
 zq_status launch_sort(Ctx& c);

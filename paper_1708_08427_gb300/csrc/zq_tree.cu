@@ -85,17 +85,48 @@ __device__ inline uint32_t quantise(double p, double lo, double hi) {
   return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
 }
 
+// Same result as quantise() with the division replaced, in all but a
+// vanishing fraction of cases, by a product with 1 / (hi - lo): the two
+// quotients differ by a few ulps, so when t * 2^21 lies more than 2^-26
+// from an integer both floors agree; otherwise the exact formula is used.
+__device__ inline uint32_t quantise_fast(double p, double lo, double hi, double inv) {
+  if (!(hi > lo)) return 0u;
+  const double s = __dmul_rn(__dmul_rn(__dsub_rn(p, lo), inv), (double)(1u << kQBits));
+  const double f = floor(s);
+  const double r = s - f;
+  if (r > 0x1p-26 && r < 1.0 - 0x1p-26 && s < (double)((1u << kQBits) - 1)) return (uint32_t)f;
+  return quantise(p, lo, hi);
+}
+
+__global__ void k_body_scale(int64_t m, const unsigned long long* __restrict__ lo,
+                             const unsigned long long* __restrict__ hi, double* __restrict__ scale) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * m) return;
+  const double l = ord_decode(lo[t]), h = ord_decode(hi[t]);
+  scale[t] = h > l ? 1.0 / (h - l) : 0.0;
+}
+
+__global__ void k_count_table(double* __restrict__ tab) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kCountTab) return;
+  const double s = sqrt((double)n);
+  tab[n] = s;
+  tab[kCountTab + n] = n > 0 ? 1.0 / s : 0.0;
+}
+
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, const int32_t* __restrict__ bead_body,
                        int64_t N, const unsigned long long* __restrict__ lo,
-                       const unsigned long long* __restrict__ hi, uint64_t* __restrict__ key) {
+                       const unsigned long long* __restrict__ hi, const double* __restrict__ scale,
+                       uint64_t* __restrict__ key) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int32_t j = bead_body[i];
   uint32_t q[3];
   const double p[3] = {x[i], y[i], z[i]};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) q[a] = quantise(p[a], ord_decode(lo[3 * j + a]), ord_decode(hi[3 * j + a]));
+  for (int a = 0; a < 3; ++a)
+    q[a] = quantise_fast(p[a], ord_decode(lo[3 * j + a]), ord_decode(hi[3 * j + a]), scale[3 * j + a]);
   key[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
 }
 
@@ -307,6 +338,14 @@ int64_t bucket_hist_words(int64_t nodes) {
   return kMaxBuckets * nblk + scan_tmp_words(kMaxBuckets * nblk);
 }
 
+zq_status launch_count_table(Ctx& c) {
+  time_begin(c, "count_table");
+  k_count_table<<<kCountTab / kThreads, kThreads, 0, c.stream>>>(c.count_tab);
+  time_end(c, "count_table");
+  ZQ_CUDA_TRY(cudaGetLastError());
+  return ZQ_OK;
+}
+
 zq_status launch_bead_body(Ctx& c) {
   time_begin(c, "bead_body");
   k_bead_body<<<blocks(c.N), kThreads, 0, c.stream>>>(c.off, c.m, c.N, c.bead_body);
@@ -326,7 +365,10 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.N, lo, hi, err);
   time_end(c, "aabb");
   time_begin(c, "keys");
-  k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.N, lo, hi, c.key);
+  k_body_scale<<<blocks(3 * c.m), kThreads, 0, s>>>(c.m, lo, hi, c.body_scale);
+  time_end(c, "keys");
+  time_begin(c, "keys");
+  k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.N, lo, hi, c.body_scale, c.key);
   time_end(c, "keys");
   ZQ_CUDA_TRY(cudaGetLastError());
   zq_status st = launch_sort(c);
