@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["shells2000", "ellipsoid"], default="shells2000")
     ap.add_argument("--cut", type=int, default=15, help="level cut (performance only)")
+    ap.add_argument("--build", choices=["dd", "fp64"], default="dd",
+                    help="node-transform arithmetic: double-single on FP32 pipes or native FP64")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / apply-only / e2e / CPU legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -277,6 +279,7 @@ def run_ours(args, world, rank, local):
     stream.synchronize()
     _XYZ[id(bt)] = (x, y, z)
     ctx = zq.Context(local, stream=stream)
+    ctx.set_build_arith(args.build)
 
     def step(prec_t=torch.float32, vv=v, ww=w, oq=qv, oqt=qtw):
         ctx.pipeline(bt.off, x, y, z, vv, oq, ww, oqt, level_cut=args.cut)
@@ -380,10 +383,11 @@ def run_ours(args, world, rank, local):
     out = {
         "metric": METRIC, "value": value, "unit": "beads/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweeps, f64 transforms",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 sweeps; transforms " + ("double-single (2 x f32, ~48-bit)" if args.build == "dd" else "f64"),
         "data": "synthetic (seeded numpy generators; no dataset)",
         "config": {"workload": desc, "m": m, "N": N, "residues": R, "level_cut": args.cut,
-                   "graph": False, "prec": "fp32",
+                   "graph": False, "prec": "fp32", "build": args.build,
                    "step": "tree + FP64 transforms + Q~v + Q~^T w (one C-ABI call, zq_pipeline)",
                    "l2": "512 MB buffer written before every step, outside the step events",
                    "wall_s_timed_region": wall},
@@ -394,6 +398,10 @@ def run_ours(args, world, rank, local):
     if not args.no_graph:
         out["graph_replay"] = timed(args, step, stream, flush, world, dev, N, graph=True)
     if not args.no_extras:
+        other = "fp64" if args.build == "dd" else "dd"
+        ctx.set_build_arith(other)
+        out[f"build_{other}_step"] = timed(args, step, stream, flush, world, dev, N, graph=not args.no_graph)
+        ctx.set_build_arith(args.build)
         out["fp64_step"] = fp64_step(args, ctx, bt, stream, flush, rng, world, dev)
         out["apply"] = apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev)
         out["e2e"] = e2e(args, ctx, bt, stream, world, dev)

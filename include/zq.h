@@ -158,6 +158,17 @@ zq_status zq_pipeline(zq_ctx *ctx, zq_prec prec, int64_t m, const int64_t *off, 
  * first launch and stop after its last launch in that call. */
 zq_status zq_time_kernel(zq_ctx *ctx, const char *name, void *start_event, void *stop_event);
 
+/* Arithmetic of the node-transform build.  ZQ_BUILD_FP64: native double
+ * precision.  ZQ_BUILD_DD (default): double-single -- each value an
+ * unevaluated sum of two floats (about 48 significant bits, relative
+ * error ~1e-14), evaluated on the FP32 pipes with error-free
+ * transformations; on this GPU FP64 runs at 1/64 of the FP32 rate.  Both
+ * meet the 1e-12 parity with the FP64 CPU oracle; the FP32 and FP64
+ * records the sweeps use are rounded from either.  Takes effect at the
+ * next build. */
+typedef enum { ZQ_BUILD_DD = 0, ZQ_BUILD_FP64 = 1 } zq_build_arith;
+zq_status zq_set_build_arith(zq_ctx *ctx, zq_build_arith arith);
+
 /* Number of kernels this context has launched since it was created (for
  * launch accounting in measurements). */
 zq_status zq_launch_count(const zq_ctx *ctx, int64_t *launches);

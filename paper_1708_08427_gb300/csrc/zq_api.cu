@@ -26,7 +26,7 @@ zq_status grow(T** p, int64_t count) {
 }
 
 void free_all(Ctx& c) {
-  void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.root, c.root_slot, c.key, c.skey, c.perm,
+  void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
                 c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.stage};
@@ -73,7 +73,9 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.counters, 4));
     if (!c.count_tab) {
       ZQ_TRY(grow(&c.count_tab, 2 * zq::kCountTab));
+      ZQ_TRY(grow(&c.count_tab2, 2 * zq::kCountTab));
       ZQ_TRY(zq::launch_count_table(c));
+      ZQ_TRY(zq::launch_count_table_dd(c));
     }
     ZQ_TRY(grow(&c.sid, nodes));
     ZQ_TRY(grow(&c.slot_of, nodes));
@@ -333,6 +335,12 @@ zq_status zq_time_kernel(zq_ctx* ctx, const char* name, void* start_event, void*
   return ZQ_OK;
 }
 
+zq_status zq_set_build_arith(zq_ctx* ctx, zq_build_arith arith) {
+  if (!ctx || (arith != ZQ_BUILD_DD && arith != ZQ_BUILD_FP64)) return ZQ_EINVAL;
+  ctx->c.build_dd = arith == ZQ_BUILD_DD;
+  return ZQ_OK;
+}
+
 zq_status zq_launch_count(const zq_ctx* ctx, int64_t* launches) {
   if (!ctx || !launches) return ZQ_EINVAL;
   *launches = ctx->c.launches;
@@ -399,10 +407,20 @@ zq_status zq_get_nodes(zq_ctx* ctx, double* centroid, double* T22) {
   ZQ_CUDA_TRY(cudaMemcpy(slot.data(), c.slot_of, slot.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
   for (int64_t q = 0; q < c.nodes; ++q) {
     const double* s = st.data() + (size_t)slot[(size_t)q] * zq::kState;
+    double v[9];
+    for (int a = 0; a < 9; ++a) {
+      if (c.st_is_dd && a >= 3) {  // T22: a double-single pair in the 8-byte word
+        float hl[2];
+        std::memcpy(hl, s + a, sizeof(hl));
+        v[a] = (double)hl[0] + (double)hl[1];
+      } else {
+        v[a] = s[a];
+      }
+    }
     if (centroid)
-      for (int a = 0; a < 3; ++a) centroid[3 * q + a] = s[a];
+      for (int a = 0; a < 3; ++a) centroid[3 * q + a] = v[a];
     if (T22)
-      for (int a = 0; a < 6; ++a) T22[6 * q + a] = s[3 + a];
+      for (int a = 0; a < 6; ++a) T22[6 * q + a] = v[3 + a];
   }
   return ZQ_OK;
 }

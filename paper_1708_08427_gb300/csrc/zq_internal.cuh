@@ -60,6 +60,8 @@ struct Ctx {
   int64_t N = 0, m = 0, nodes = 0, R = 0;
   int cut = kDefaultCut;
   bool have_tree = false, have_xform = false, have64 = false, have32 = false;
+  bool build_dd = true;    // build the transforms in double-single (else native FP64)
+  bool st_is_dd = false;   // representation of st64 written by the last build
   std::vector<int64_t> off_h;
   std::vector<int32_t> small_bodies;  // n_j <= kSmallSortMax
   std::vector<int32_t> big_bodies;    // n_j > kSmallSortMax (device radix sort)
@@ -71,6 +73,7 @@ struct Ctx {
   uint64_t* aabb = nullptr;      // [m * 6] ordered-int encoded lo[3], hi[3]
   double* body_scale = nullptr;  // [m * 3] 1 / (hi - lo) per axis (0 if hi == lo)
   double* count_tab = nullptr;   // [2 * kCountTab]: sqrt(n), 1/sqrt(n)
+  float2* count_tab2 = nullptr;  // the same as double-single pairs
   int32_t* root = nullptr;       // [m] root node id
   int32_t* root_slot = nullptr;  // [m] root slot
   // beads
@@ -194,6 +197,7 @@ __device__ inline double ord_decode(unsigned long long u) {
 zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z);
 zq_status launch_bead_body(Ctx& c);
 zq_status launch_count_table(Ctx& c);
+zq_status launch_count_table_dd(Ctx& c);
 int64_t bucket_hist_words(int64_t nodes);
 // zq_sort.cu
 zq_status launch_sort(Ctx& c);

@@ -21,6 +21,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "_build" / "libzq.so"
 ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE = range(7)
 ZQ_FP64, ZQ_FP32 = 0, 1
 ZQ_HOST_BUFFERS, ZQ_KEEP_TREE = 1, 2
+ZQ_BUILD_DD, ZQ_BUILD_FP64 = 0, 1
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -75,6 +76,8 @@ def _lib() -> ctypes.CDLL:
                                   ctypes.c_int32, ctypes.c_int32]
         L.zq_time_kernel.restype = ctypes.c_int
         L.zq_time_kernel.argtypes = [_vp, ctypes.c_char_p, _vp, _vp]
+        L.zq_set_build_arith.restype = ctypes.c_int
+        L.zq_set_build_arith.argtypes = [_vp, ctypes.c_int]
         L.zq_launch_count.restype = ctypes.c_int
         L.zq_launch_count.argtypes = [_vp, _i64p]
         _L = L
@@ -207,6 +210,11 @@ class Context:
             return
         _check(_lib().zq_time_kernel(self._h, name.encode(), _vp(start.cuda_event), _vp(stop.cuda_event)),
                "zq_time_kernel")
+
+    def set_build_arith(self, arith: str):
+        """'dd' (double-single on the FP32 pipes, default) or 'fp64'."""
+        code = {"dd": ZQ_BUILD_DD, "fp64": ZQ_BUILD_FP64}[arith]
+        _check(_lib().zq_set_build_arith(self._h, code), "zq_set_build_arith")
 
     def launch_count(self) -> int:
         n = _i64()

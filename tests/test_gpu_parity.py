@@ -32,11 +32,12 @@ def _zq():
     return zq
 
 
-def make_ctx(bt, cut=0):
+def make_ctx(bt, cut=0, arith="dd"):
     dev = _dev()
     zq = _zq()
     x, y, z = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (bt.x, bt.y, bt.z))
     ctx = zq.Context(0)
+    ctx.set_build_arith(arith)
     ctx.build_tree_batched(bt.off, x, y, z, cut)
     ctx.build_transforms(x, y, z)
     return ctx, (x, y, z)
@@ -135,11 +136,13 @@ def check_apply(ctx, bt, dtype, k=1, seed=0):
 # --------------------------------------------------------------- cases
 
 
-def test_single_body_256_sixteen_vectors():
+@pytest.mark.parametrize("arith", ["dd", "fp64"])
+def test_single_body_256_sixteen_vectors(arith):
     """n = 256 shell of radius 2 with N(0, 0.05^2) jitter, 16 right-hand
-    sides; bisection tree exact, FP64 and FP32 sweeps."""
+    sides; bisection tree exact, FP64 and FP32 sweeps, transforms built in
+    double-single and in native FP64."""
     bt = W.shell_body(256, radius=2.0, sigma=0.05, seed=0)
-    ctx, _ = make_ctx(bt, cut=3)
+    ctx, _ = make_ctx(bt, cut=3, arith=arith)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_nodes(ctx, bt, bodies)
@@ -147,13 +150,13 @@ def test_single_body_256_sixteen_vectors():
     check_apply(ctx, bt, np.float32, k=16, seed=1)
 
 
-@pytest.mark.parametrize("cut", [1, 4, 15, 21])
-def test_batch_ragged_levels(cut):
+@pytest.mark.parametrize("cut,arith", [(1, "dd"), (4, "fp64"), (15, "dd"), (21, "fp64")])
+def test_batch_ragged_levels(cut, arith):
     """Bodies from 3 to 700 beads; a low level cut sends most nodes through
     the per-body kernels, a high one through the per-height kernels; bucket
     boundaries fall inside warps; 3-bead bodies."""
     bt = W.shell_batch(m=60, nmin=3, nmax=700, seed=4)
-    ctx, _ = make_ctx(bt, cut=cut)
+    ctx, _ = make_ctx(bt, cut=cut, arith=arith)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_nodes(ctx, bt, bodies)
@@ -197,7 +200,8 @@ def _batch_from_points(bodies_pts):
     return W.Batch(off, P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy())
 
 
-def test_edge_geometries():
+@pytest.mark.parametrize("arith", ["dd", "fp64"])
+def test_edge_geometries(arith):
     rng = np.random.default_rng(12)
     pts = [
         rng.uniform(-1, 1, (3, 3)),                                   # smallest body
@@ -207,7 +211,7 @@ def test_edge_geometries():
         np.r_[rng.uniform(0, 1, (20, 3)), np.full((4, 3), 0.5)],      # beads sharing one cell
     ]
     bt = _batch_from_points(pts)
-    ctx, _ = make_ctx(bt, cut=3)
+    ctx, _ = make_ctx(bt, cut=3, arith=arith)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_apply(ctx, bt, np.float64)
@@ -252,11 +256,13 @@ def test_argument_errors():
 # --------------------------------------------------------- full sizes
 
 
-def test_full_size_batched_shells():
+@pytest.mark.parametrize("arith", ["dd", "fp64"])
+def test_full_size_batched_shells(arith):
     """2000 bodies, log-uniform 50..5000 beads: every output against the
-    oracle (FP32 sweeps, FP64 transforms), tree bit-exact."""
+    oracle (FP32 and FP64 sweeps; transforms in double-single or FP64),
+    tree bit-exact."""
     bt = W.shell_batch(m=2000, seed=0)
-    ctx, _ = make_ctx(bt)
+    ctx, _ = make_ctx(bt, arith=arith)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     del bodies
@@ -267,7 +273,7 @@ def test_full_size_batched_shells():
 def test_full_size_ellipsoid():
     """One body of 2^20 beads: tree bit-exact, sweeps against the oracle."""
     bt = W.ellipsoid_body(n=1 << 20, seed=0)
-    ctx, _ = make_ctx(bt)
+    ctx, _ = make_ctx(bt)  # double-single build
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     del bodies
@@ -275,7 +281,8 @@ def test_full_size_ellipsoid():
     check_apply(ctx, bt, np.float64, seed=9)
 
 
-def test_collinear_and_lattice_bodies_match():
+@pytest.mark.parametrize("arith", ["dd", "fp64"])
+def test_collinear_and_lattice_bodies_match(arith):
     """Exactly collinear beads and lattice bodies (rank-deficient node
     matrices everywhere): the FP64 sweeps still match the oracle."""
     n = 30
@@ -283,7 +290,7 @@ def test_collinear_and_lattice_bodies_match():
     g = np.arange(64)
     lattice = np.c_[g % 4, (g // 4) % 4, g // 16].astype(float) * 0.3
     bt = _batch_from_points([line, lattice])
-    ctx, _ = make_ctx(bt, cut=3)
+    ctx, _ = make_ctx(bt, cut=3, arith=arith)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_apply(ctx, bt, np.float64)
