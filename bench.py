@@ -290,7 +290,7 @@ def run_ours(args, world, rank, local):
     census = node_census(ctx)
 
     # --- per-kernel time of one step (measurement hook), picks the dominant kernel
-    names = ["aabb", "keys", "sort_small", "sort_radix", "lcp", "bottom_up", "scan", "schedule",
+    names = ["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "schedule",
              "build_level", "build_tail", "up_level", "up_tail", "down_tail", "down_level"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -311,7 +311,7 @@ def run_ours(args, world, rank, local):
             tot += e0.elapsed_time(e1)
         ctx.time_kernel(None)
         phases[nm] = tot / reps
-    dominant = max(("build_level", "up_level", "down_level", "sort_small", "bottom_up", "keys"),
+    dominant = max(("build_level", "up_level", "down_level", "small_tree", "schedule"),
                    key=lambda k: phases.get(k, 0.0)) if phases else "build_level"
 
     # --- the dominant kernel is bracketed by events in every timed step

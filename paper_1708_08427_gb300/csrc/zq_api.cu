@@ -185,14 +185,22 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
   c.small_bodies.clear();
   c.big_bodies.clear();
   c.max_small = 0;
-  for (int64_t j = 0; j < m; ++j) {
-    const int64_t n = off[j + 1] - off[j];
-    if (n <= zq::kSmallSortMax) {
-      c.small_bodies.push_back((int32_t)j);
-      if (n > c.max_small) c.max_small = (int32_t)n;
-    } else {
-      c.big_bodies.push_back((int32_t)j);
+  {
+    std::vector<int32_t> cls[4];
+    for (int64_t j = 0; j < m; ++j) {
+      const int64_t n = off[j + 1] - off[j];
+      if (n <= zq::kSmallSortMax) {
+        cls[zq::small_tree_class(n)].push_back((int32_t)j);
+        if (n > c.max_small) c.max_small = (int32_t)n;
+      } else {
+        c.big_bodies.push_back((int32_t)j);
+      }
     }
+    for (int k = 0; k < 4; ++k) {
+      c.small_class_start[k] = (int)c.small_bodies.size();
+      c.small_bodies.insert(c.small_bodies.end(), cls[k].begin(), cls[k].end());
+    }
+    c.small_class_start[4] = (int)c.small_bodies.size();
   }
   ZQ_CUDA_TRY(cudaMemcpyAsync(c.off, off, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
   if (!c.small_bodies.empty())

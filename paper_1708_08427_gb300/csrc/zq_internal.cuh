@@ -63,8 +63,9 @@ struct Ctx {
   bool build_dd = true;    // build the transforms in double-single (else native FP64)
   bool st_is_dd = false;   // representation of st64 written by the last build
   std::vector<int64_t> off_h;
-  std::vector<int32_t> small_bodies;  // n_j <= kSmallSortMax
-  std::vector<int32_t> big_bodies;    // n_j > kSmallSortMax (device radix sort)
+  std::vector<int32_t> small_bodies;  // n_j <= kSmallSortMax, grouped by size class
+  std::vector<int32_t> big_bodies;    // n_j > kSmallSortMax (device-wide tree kernels)
+  int small_class_start[5] = {0, 0, 0, 0, 0};
   int32_t max_small = 0;
   // device buffers (bodies)
   int64_t* off = nullptr;        // [m+1]
@@ -196,6 +197,9 @@ __device__ inline double ord_decode(unsigned long long u) {
 // zq_tree.cu
 zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z);
 zq_status launch_bead_body(Ctx& c);
+// zq_smalltree.cu
+int small_tree_class(int64_t n);
+zq_status launch_small_trees(Ctx& c, const double* x, const double* y, const double* z);
 zq_status launch_count_table(Ctx& c);
 zq_status launch_count_table_dd(Ctx& c);
 int64_t bucket_hist_words(int64_t nodes);

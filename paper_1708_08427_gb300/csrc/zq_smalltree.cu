@@ -1,0 +1,378 @@
+// zq_smalltree.cu -- the whole bisection tree of a body of at most 8192
+// beads in one thread block (Sec. 2.1, same readings as zq_tree.cu):
+//   1. bounding box (block min/max on order-preserving integer encodings);
+//   2. 21-bit quantisation and bisection keys (z, then y, then x per octree
+//      level, most significant first);
+//   3. stable LSD radix sort of (key, body-local index) in shared memory,
+//      eight passes of 8-bit digits: equal keys keep index order;
+//   4. LCP of sorted neighbours (63 coordinate levels, then 32 index levels);
+//   5. bottom-up construction: a node's parent is the neighbouring split
+//      with the larger LCP; each child deposits (code, range end, height) in
+//      the parent's 64-bit shared-memory slot with one atomic exchange, and
+//      the child that finds the sibling's deposit completes the parent.
+// Output: the same global node arrays as the device-wide path (perm, child
+// codes, first, count, height, residue size, root).
+#include "zq_internal.cuh"
+
+namespace zq {
+
+namespace {
+
+struct SmallTreeArgs {
+  const double* x;
+  const double* y;
+  const double* z;
+  const int64_t* off;
+  const int32_t* bodies;  // body ids of this size class
+  int32_t* perm;
+  int32_t* cl;
+  int32_t* cr;
+  int32_t* first;
+  int32_t* cnt;
+  uint8_t* height;
+  int32_t* res;
+  int32_t* root;
+  int32_t* err;
+};
+
+__device__ __forceinline__ uint32_t quantise_exact(double p, double lo, double hi) {
+  if (!(hi > lo)) return 0u;
+  const double t = __ddiv_rn(__dsub_rn(p, lo), __dsub_rn(hi, lo));
+  const double s = floor(__dmul_rn(t, (double)(1u << kQBits)));
+  const double top = (double)((1u << kQBits) - 1);
+  return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
+}
+
+// floor((p - lo) / (hi - lo) * 2^21) clamped, equal to quantise_exact: the
+// product with inv21 = 2^21 / (hi - lo) differs from the correctly rounded
+// quotient by a few ulps, so its floor is taken from the bits of s when s
+// is more than 2^-26 from an integer (integer instructions only), and the
+// exact formula is used otherwise.
+__device__ __forceinline__ uint32_t quantise_bits(double p, double lo, double hi, double inv21) {
+  if (!(hi > lo)) return 0u;
+  const double s = __dmul_rn(__dsub_rn(p, lo), inv21);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if ((b >> 63) == 0 && e >= 0 && e <= 20) {
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int fbits = 52 - e;
+    const unsigned long long ip = M >> fbits;
+    const unsigned long long fr = M & ((1ull << fbits) - 1);
+    const unsigned long long margin = 1ull << (fbits - 26);
+    if (fr > margin && fr < (1ull << fbits) - margin && ip < (1ull << kQBits) - 1) return (uint32_t)ip;
+  } else if ((b >> 63) == 0 && e < 0 && e >= -26) {
+    // 2^-26 <= s < 1: floor 0 unless s is within 2^-26 of 1
+    if (s < 1.0 - 0x1p-26) return 0u;
+  }
+  return quantise_exact(p, lo, hi);
+}
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t s = v & 0x1fffffull;
+  s = (s | (s << 32)) & 0x1f00000000ffffull;
+  s = (s | (s << 16)) & 0x1f0000ff0000ffull;
+  s = (s | (s << 8)) & 0x100f00f00f00f00full;
+  s = (s | (s << 4)) & 0x10c30c30c30c30c3ull;
+  s = (s | (s << 2)) & 0x1249249249249249ull;
+  return s;
+}
+
+// Block-wide exclusive scan of one int per thread (THREADS a multiple of 32).
+template <int THREADS>
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += t;
+  }
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int32_t w = (lane < THREADS / 32) ? sh[lane] : 0;
+    int32_t wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += t;
+    }
+    sh[lane] = wi - w;
+    if (lane == 31) sh[32] = wi;
+  }
+  __syncthreads();
+  const int32_t r = inc - v + sh[warp];
+  if (total) *total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+template <int MAXN, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
+  constexpr int NW = THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* keyA = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* keyB = keyA + MAXN;
+  uint16_t* idxA = reinterpret_cast<uint16_t*>(keyB + MAXN);
+  uint16_t* idxB = idxA + MAXN;
+  int32_t* whist = reinterpret_cast<int32_t*>(idxB + MAXN);  // [NW][256]
+  __shared__ int32_t sh[33];
+  __shared__ unsigned long long bb[6];
+  __shared__ double lim[9];  // lo[3], hi[3], 2^21 / (hi - lo)[3]
+
+  const int32_t j = a.bodies[blockIdx.x];
+  const int64_t o = a.off[j];
+  const int n = (int)(a.off[j + 1] - o);
+  const int tid = threadIdx.x;
+
+  // ---- 1. bounding box (order-preserving integer encodings of doubles)
+  if (tid < 3) bb[tid] = ~0ull;
+  if (tid >= 3 && tid < 6) bb[tid] = 0ull;
+  __syncthreads();
+  {
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
+    bool bad = false;
+    for (int i = tid; i < n; i += THREADS) {
+      const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        bad |= !isfinite(p[c]);
+        const unsigned long long e = ord_encode(p[c]);
+        mn[c] = e < mn[c] ? e : mn[c];
+        mx[c] = e > mx[c] ? e : mx[c];
+      }
+    }
+    if (bad) atomicOr(a.err, kErrNonFinite);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn[c], d);
+        const unsigned long long omx = __shfl_xor_sync(0xffffffffu, mx[c], d);
+        mn[c] = omn < mn[c] ? omn : mn[c];
+        mx[c] = omx > mx[c] ? omx : mx[c];
+      }
+      if ((tid & 31) == 0) {
+        atomicMin(&bb[c], mn[c]);
+        atomicMax(&bb[3 + c], mx[c]);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < 3) {
+    const double l = ord_decode(bb[tid]), h = ord_decode(bb[3 + tid]);
+    lim[tid] = l;
+    lim[3 + tid] = h;
+    lim[6 + tid] = h > l ? (double)(1u << kQBits) / (h - l) : 0.0;
+  }
+  __syncthreads();
+
+  // ---- 2. keys
+  {
+    const double inv[3] = {lim[6], lim[7], lim[8]};
+    for (int i = tid; i < n; i += THREADS) {
+      const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
+      uint32_t q[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[c] = quantise_bits(p[c], lim[c], lim[3 + c], inv[c]);
+      keyA[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+      idxA[i] = (uint16_t)i;
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. stable LSD radix sort, 8-bit digits; warp w owns the chunk
+  // [w * PER_WARP, (w + 1) * PER_WARP) of the current order
+  const int lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int per_warp = (n + NW - 1) / NW;
+  uint64_t* kin = keyA;
+  uint64_t* kout = keyB;
+  uint16_t* iin = idxA;
+  uint16_t* iout = idxB;
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 8 * pass;
+    for (int d = lane; d < 256; d += 32) whist[warp * 256 + d] = 0;
+    __syncwarp();
+    const int c0 = min(n, warp * per_warp);
+    const int c1 = min(n, c0 + per_warp);
+    // counts per digit of this warp's chunk
+    for (int base = c0; base < c1; base += 32) {
+      const int i = base + lane;
+      const bool v = i < c1;
+      const int dg = v ? (int)((kin[i] >> shift) & 0xff) : 256 + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      if (v && (peers & lt) == 0) whist[warp * 256 + dg] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // exclusive scan over (digit, warp): thread t owns digit-major entries
+    // [t * (256 * NW / THREADS), ...)
+    constexpr int E = 256 * NW / THREADS;
+    int32_t loc[E];
+    int32_t s = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int f = tid * E + e;        // flattened (digit, warp) index
+      const int dg = f / NW, w = f % NW;
+      loc[e] = whist[w * 256 + dg];
+      s += loc[e];
+    }
+    int32_t run = block_excl_scan<THREADS>(s, sh, nullptr);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int f = tid * E + e;
+      const int dg = f / NW, w = f % NW;
+      whist[w * 256 + dg] = run;  // first output position of (digit, warp)
+      run += loc[e];
+    }
+    __syncthreads();
+    // scatter in chunk order (stable)
+    for (int base = c0; base < c1; base += 32) {
+      const int i = base + lane;
+      const bool v = i < c1;
+      uint64_t k = 0;
+      uint16_t ix = 0;
+      int dg = 256 + lane;
+      if (v) {
+        k = kin[i];
+        ix = iin[i];
+        dg = (int)((k >> shift) & 0xff);
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      if (v) {
+        const int pos = whist[warp * 256 + dg] + __popc(peers & lt);
+        kout[pos] = k;
+        iout[pos] = ix;
+      }
+      __syncwarp();
+      if (v && (peers & lt) == 0) whist[warp * 256 + dg] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint64_t* tk = kin; kin = kout; kout = tk;
+    uint16_t* ti = iin; iin = iout; iout = ti;
+  }
+  // after 8 passes the sorted data is back in keyA / idxA
+
+  // ---- 4. permutation and LCP of neighbours
+  uint8_t* lcp = reinterpret_cast<uint8_t*>(keyB);   // keyB is free now
+  for (int p = tid; p < n; p += THREADS) {
+    a.perm[o + p] = (int32_t)(o + idxA[p]);
+    if (p < n - 1) {
+      const uint64_t k1 = keyA[p], k2 = keyA[p + 1];
+      int d;
+      if (k1 != k2) d = __clzll((long long)(k1 ^ k2)) - 1;
+      else d = 63 + __clz((int)((uint32_t)idxA[p] ^ (uint32_t)idxA[p + 1]));
+      lcp[p] = (uint8_t)d;
+    }
+  }
+  __syncthreads();
+
+  // ---- 5. bottom-up construction (node id of split g: o - j + g).
+  // slot[g] = 0 until a child arrives; a deposit is
+  //   bit 63 valid | bits 24..55 child code | bits 8..23 range end | bits 0..7 height
+  // A lane takes one step of its walk per iteration; a lane whose walk has
+  // ended (it arrived first at a node, or completed the root) takes the
+  // next unprocessed leaf, so warps stay full while a few walks are long.
+  __shared__ int next_leaf;
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(keyA);  // keyA is free now
+  for (int p = tid; p < n; p += THREADS) slot[p] = 0ull;
+  if (tid == 0) next_leaf = THREADS;
+  __syncthreads();
+  const int64_t nb = o - j;
+  int l = tid, r = tid, h = 0;
+  int32_t code = -1 - (int32_t)(o + tid);
+  bool busy = tid < n, more = true;
+  while (__any_sync(0xffffffffu, busy || more)) {
+    if (!busy && more) {
+      const int leaf = atomicAdd(&next_leaf, 1);
+      if (leaf < n) {
+        l = r = leaf;
+        h = 0;
+        code = -1 - (int32_t)(o + leaf);
+        busy = true;
+      } else {
+        more = false;
+      }
+    }
+    if (!busy) continue;
+    if (l == 0 && r == n - 1) {
+      a.root[j] = code;
+      busy = false;
+      continue;
+    }
+    bool is_left;
+    if (l == 0) is_left = true;
+    else if (r == n - 1) is_left = false;
+    else is_left = lcp[r] > lcp[l - 1];
+    const int g = is_left ? r : l - 1;
+    const unsigned long long mine = (1ull << 63) | ((unsigned long long)(uint32_t)code << 24) |
+                                    ((unsigned long long)(is_left ? l : r) << 8) | (unsigned)h;
+    const unsigned long long other = atomicExch(&slot[g], mine);
+    if (other == 0ull) {  // the sibling completes g
+      busy = false;
+      continue;
+    }
+    const int32_t sib = (int32_t)(uint32_t)(other >> 24);
+    const int end = (int)((other >> 8) & 0xffff);
+    const int hs = (int)(other & 0xff);
+    const int lo_ = is_left ? l : end;
+    const int hi_ = is_left ? end : r;
+    const int64_t q = nb + g;
+    const int32_t lc = is_left ? code : sib;
+    const int32_t rc = is_left ? sib : code;
+    h = 1 + (h > hs ? h : hs);
+    a.cl[q] = lc;
+    a.cr[q] = rc;
+    a.first[q] = (int32_t)(o + lo_);
+    a.cnt[q] = hi_ - lo_ + 1;
+    a.height[q] = (uint8_t)h;
+    a.res[q] = 3 * ((lc >= 0) + (rc >= 0));
+    code = (int32_t)q;
+    l = lo_;
+    r = hi_;
+  }
+}
+
+template <int MAXN, int THREADS>
+constexpr size_t small_tree_smem() {
+  return (size_t)MAXN * (8 + 8 + 2 + 2) + (size_t)(THREADS / 32) * 256 * 4;
+}
+
+template <int MAXN, int THREADS>
+zq_status launch_class(Ctx& c, const SmallTreeArgs& a, const int32_t* bodies, int count) {
+  if (count <= 0) return ZQ_OK;
+  constexpr size_t smem = small_tree_smem<MAXN, THREADS>();
+  ZQ_CUDA_TRY(cudaFuncSetAttribute(k_small_tree<MAXN, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  SmallTreeArgs b = a;
+  b.bodies = bodies;
+  time_begin(c, "small_tree");
+  k_small_tree<MAXN, THREADS><<<(unsigned)count, THREADS, smem, c.stream>>>(b);
+  time_end(c, "small_tree");
+  ZQ_CUDA_TRY(cudaGetLastError());
+  return ZQ_OK;
+}
+
+}  // namespace
+
+int small_tree_class(int64_t n) { return n <= 1024 ? 0 : (n <= 2048 ? 1 : (n <= 4096 ? 2 : 3)); }
+
+// Bodies of at most kSmallSortMax beads: c.small_d lists them grouped by
+// size class (c.small_class_start, host).
+zq_status launch_small_trees(Ctx& c, const double* x, const double* y, const double* z) {
+  SmallTreeArgs a;
+  a.x = x; a.y = y; a.z = z;
+  a.off = c.off; a.bodies = nullptr; a.perm = c.perm; a.cl = c.cl; a.cr = c.cr; a.first = c.first;
+  a.cnt = c.cnt; a.height = c.height; a.res = c.roff; a.root = c.root; a.err = c.counters + 2;
+  const int* cs = c.small_class_start;
+  zq_status st;
+  if ((st = launch_class<8192, 1024>(c, a, c.small_d + cs[3], cs[4] - cs[3])) != ZQ_OK) return st;
+  if ((st = launch_class<4096, 512>(c, a, c.small_d + cs[2], cs[3] - cs[2])) != ZQ_OK) return st;
+  if ((st = launch_class<2048, 256>(c, a, c.small_d + cs[1], cs[2] - cs[1])) != ZQ_OK) return st;
+  if ((st = launch_class<1024, 256>(c, a, c.small_d + cs[0], cs[1] - cs[0])) != ZQ_OK) return st;
+  return ZQ_OK;
+}
+
+}  // namespace zq

@@ -2,62 +2,15 @@
 // body-local bead index (Sec. 2.1 readings: beads sharing a 21-bit cell are
 // separated by their index bits).
 //
-// Bodies of at most kSmallSortMax beads: one thread block per body, bitonic
-// sort of (key, local index) pairs in shared memory.
-// Larger bodies: stable LSD radix sort, 16 passes of 4 bits over the 64-bit
-// key; stability keeps equal keys in bead (= index) order.
+// Bodies above kSmallSortMax beads (smaller ones are sorted inside the
+// per-body tree kernel, zq_smalltree.cu): stable LSD radix sort, 16 passes
+// of 4 bits over the 64-bit key; stability keeps equal keys in bead (=
+// index) order.
 #include "zq_internal.cuh"
 
 namespace zq {
 
 namespace {
-
-constexpr int kSortThreads = 1024;
-
-__global__ void __launch_bounds__(kSortThreads)
-k_sort_small(const int64_t* __restrict__ off, const int32_t* __restrict__ bodies,
-             const uint64_t* __restrict__ key, uint64_t* __restrict__ skey,
-             int32_t* __restrict__ perm) {
-  extern __shared__ unsigned char smem[];
-  const int32_t j = bodies[blockIdx.x];
-  const int64_t o = off[j];
-  const int n = (int)(off[j + 1] - o);
-  int P = 1;
-  while (P < n) P <<= 1;
-  uint64_t* k = reinterpret_cast<uint64_t*>(smem);
-  uint16_t* ix = reinterpret_cast<uint16_t*>(k + P);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    if (i < n) {
-      k[i] = key[o + i];
-      ix[i] = (uint16_t)i;
-    } else {
-      k[i] = ~0ull;
-      ix[i] = 0xffffu;
-    }
-  }
-  __syncthreads();
-  for (int size = 2; size <= P; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
-        int a = 2 * t - (t & (stride - 1));
-        int b = a + stride;
-        bool ascending = (a & size) == 0;
-        uint64_t ka = k[a], kb = k[b];
-        uint16_t ia = ix[a], ib = ix[b];
-        bool greater = (ka > kb) || (ka == kb && ia > ib);
-        if (greater == ascending) {
-          k[a] = kb; k[b] = ka;
-          ix[a] = ib; ix[b] = ia;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    skey[o + i] = k[i];
-    perm[o + i] = (int32_t)(o + ix[i]);
-  }
-}
 
 // ------------------------------------------------------------ radix (big)
 constexpr int kRadixThreads = 256;
@@ -146,19 +99,6 @@ k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vi
 
 zq_status launch_sort(Ctx& c) {
   cudaStream_t s = c.stream;
-  if (!c.small_bodies.empty()) {
-    size_t smem = (size_t)c.max_small * (sizeof(uint64_t) + sizeof(uint16_t));
-    int P = 1;
-    while (P < c.max_small) P <<= 1;
-    smem = (size_t)P * (sizeof(uint64_t) + sizeof(uint16_t));
-    ZQ_CUDA_TRY(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    time_begin(c, "sort_small");
-    k_sort_small<<<(unsigned)c.small_bodies.size(), kSortThreads, smem, s>>>(c.off, c.small_d, c.key,
-                                                                          c.skey, c.perm);
-    time_end(c, "sort_small");
-    ZQ_CUDA_TRY(cudaGetLastError());
-  }
   for (int32_t j : c.big_bodies) {
     int64_t o = c.off_h[j], n = c.off_h[j + 1] - o;
     int64_t nblk = (n + kRadixTile - 1) / kRadixTile;

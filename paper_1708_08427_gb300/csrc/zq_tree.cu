@@ -30,19 +30,21 @@ __global__ void k_bead_body(const int64_t* __restrict__ off, int64_t m, int64_t 
 
 __global__ void k_aabb(const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, const int32_t* __restrict__ bead_body,
-                       int64_t N, unsigned long long* __restrict__ lo,
+                       const int64_t* __restrict__ off, int64_t N, unsigned long long* __restrict__ lo,
                        unsigned long long* __restrict__ hi, int32_t* __restrict__ err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = i < N;
-  const int32_t j = valid ? bead_body[i] : -1;
-  double p[3] = {valid ? x[i] : 0.0, valid ? y[i] : 0.0, valid ? z[i] : 0.0};
-  if (valid && !(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(err, kErrNonFinite);
+  int32_t j = valid ? bead_body[i] : -1;
+  if (j >= 0 && off[j + 1] - off[j] <= kSmallSortMax) j = -1;  // done by the per-body kernel
+  const bool mine = j >= 0;
+  double p[3] = {mine ? x[i] : 0.0, mine ? y[i] : 0.0, mine ? z[i] : 0.0};
+  if (mine && !(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(err, kErrNonFinite);
   const int32_t j0 = __shfl_sync(0xffffffffu, j, 0);
   const bool uniform = __all_sync(0xffffffffu, j == j0) && j0 >= 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    unsigned long long e = valid ? ord_encode(p[a]) : 0ull;
+    unsigned long long e = mine ? ord_encode(p[a]) : 0ull;
     if (uniform) {
       unsigned long long mn = e, mx = e;
 #pragma unroll
@@ -56,7 +58,7 @@ __global__ void k_aabb(const double* __restrict__ x, const double* __restrict__ 
         atomicMin(&lo[3 * j0 + a], mn);
         atomicMax(&hi[3 * j0 + a], mx);
       }
-    } else if (valid) {
+    } else if (mine) {
       atomicMin(&lo[3 * j + a], e);
       atomicMax(&hi[3 * j + a], e);
     }
@@ -116,12 +118,14 @@ __global__ void k_count_table(double* __restrict__ tab) {
 
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, const int32_t* __restrict__ bead_body,
-                       int64_t N, const unsigned long long* __restrict__ lo,
+                       const int64_t* __restrict__ off, int64_t N,
+                       const unsigned long long* __restrict__ lo,
                        const unsigned long long* __restrict__ hi, const double* __restrict__ scale,
                        uint64_t* __restrict__ key) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int32_t j = bead_body[i];
+  if (off[j + 1] - off[j] <= kSmallSortMax) return;
   uint32_t q[3];
   const double p[3] = {x[i], y[i], z[i]};
 #pragma unroll
@@ -139,6 +143,7 @@ __global__ void k_lcp(const int64_t* __restrict__ off, const int32_t* __restrict
   if (s >= N) return;
   const int32_t j = bead_body[s];
   if (s == off[j + 1] - 1) return;  // last bead of a body: no split after it
+  if (off[j + 1] - off[j] <= kSmallSortMax) return;
   const int64_t o = off[j];
   const int64_t q = s - j;          // node of the split between s and s + 1
   const uint64_t k1 = skey[s], k2 = skey[s + 1];
@@ -163,6 +168,7 @@ __global__ void k_bottom_up(const int64_t* __restrict__ off, const int32_t* __re
   const int32_t j = bead_body[s];
   const int64_t o = off[j];
   const int32_t n = (int32_t)(off[j + 1] - o);
+  if (n <= kSmallSortMax) return;
   const int64_t nb = o - j;
   int32_t l = (int32_t)(s - o), r = l;
   int32_t code = -1 - (int32_t)s;
@@ -359,29 +365,35 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   unsigned long long* lo = reinterpret_cast<unsigned long long*>(c.aabb);
   unsigned long long* hi = lo + 3 * c.m;
   int32_t* err = c.counters + 2;
-  ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
-  ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
-  time_begin(c, "aabb");
-  k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.N, lo, hi, err);
-  time_end(c, "aabb");
-  time_begin(c, "keys");
-  k_body_scale<<<blocks(3 * c.m), kThreads, 0, s>>>(c.m, lo, hi, c.body_scale);
-  time_end(c, "keys");
-  time_begin(c, "keys");
-  k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.N, lo, hi, c.body_scale, c.key);
-  time_end(c, "keys");
-  ZQ_CUDA_TRY(cudaGetLastError());
-  zq_status st = launch_sort(c);
+  // bodies of at most kSmallSortMax beads: one thread block each
+  zq_status st = launch_small_trees(c, x, y, z);
   if (st != ZQ_OK) return st;
-  time_begin(c, "lcp");
-  k_lcp<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.skey, c.perm, c.lcp);
-  time_end(c, "lcp");
-  ZQ_CUDA_TRY(cudaMemsetAsync(c.flag, 0, c.nodes * sizeof(int32_t), s));
-  time_begin(c, "bottom_up");
-  k_bottom_up<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.lcp, c.cl, c.cr, c.first,
-                                               c.cnt, c.height, c.flag, c.roff, c.root);
-  time_end(c, "bottom_up");
-  ZQ_CUDA_TRY(cudaGetLastError());
+  // larger bodies: device-wide kernels (they skip the beads of small bodies)
+  if (!c.big_bodies.empty()) {
+    ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
+    ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
+    time_begin(c, "aabb");
+    k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.off, c.N, lo, hi, err);
+    time_end(c, "aabb");
+    time_begin(c, "keys");
+    k_body_scale<<<blocks(3 * c.m), kThreads, 0, s>>>(c.m, lo, hi, c.body_scale);
+    time_end(c, "keys");
+    time_begin(c, "keys");
+    k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.off, c.N, lo, hi, c.body_scale, c.key);
+    time_end(c, "keys");
+    ZQ_CUDA_TRY(cudaGetLastError());
+    st = launch_sort(c);
+    if (st != ZQ_OK) return st;
+    time_begin(c, "lcp");
+    k_lcp<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.skey, c.perm, c.lcp);
+    time_end(c, "lcp");
+    ZQ_CUDA_TRY(cudaMemsetAsync(c.flag, 0, c.nodes * sizeof(int32_t), s));
+    time_begin(c, "bottom_up");
+    k_bottom_up<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.lcp, c.cl, c.cr, c.first,
+                                                 c.cnt, c.height, c.flag, c.roff, c.root);
+    time_end(c, "bottom_up");
+    ZQ_CUDA_TRY(cudaGetLastError());
+  }
   st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
   if (st != ZQ_OK) return st;
   // schedule
