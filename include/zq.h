@@ -209,6 +209,49 @@ zq_status zq_get_nodes(zq_ctx *ctx, double *centroid, double *T22);
  * for k = 6, 9; for Case I (k = 3) entries 5..13 hold G row-major. */
 zq_status zq_get_records(zq_ctx *ctx, double *rec);
 
+/* ------------------------------------------------------------------------
+ * Q~ v for one small body without allocating device memory.
+ *
+ * The paper has no counterpart to this entry point: it computes the same
+ * product as zq_build_tree + zq_build_transforms + zq_apply_Q (Algorithm 2,
+ * Eqs. 4.2-4.3, FP64) for ONE body, for callers that cannot allocate device
+ * memory where they call it -- code inside a host framework that owns all
+ * device memory through its own allocator, or a loop that runs on a fixed
+ * memory budget -- and so cannot hold a zq_ctx, whose workspace grows with
+ * the batch.  It needs no context: the intermediate data (tree and node
+ * transforms, about 300 KB) lives in one fixed array in device memory that
+ * the library declares statically, so it exists on every device the library
+ * is loaded on, and the call never allocates.
+ *
+ *   device   CUDA device ordinal the pointers live on (0..63).
+ *   stream   cudaStream_t (NULL = legacy default stream); the call is
+ *            asynchronous on it.
+ *   n        beads, 3 <= n <= ZQ_NOALLOC_MAX_BEADS; any other n returns
+ *            ZQ_EINVAL before touching the GPU.
+ *   x, y, z  DEVICE doubles [n]: bead coordinates (finite; not checked).
+ *   v        DEVICE doubles [3 * n], three planes: v[a * n + i] is axis a
+ *            of bead i.
+ *   out      DEVICE doubles [3n - 6]: the Residues, in the order zq_apply_Q
+ *            writes them for a batch holding only this body.
+ * Nothing has to be zeroed by the caller: every value the kernel reads from
+ * the static array is written earlier in the same call.  Coincident beads
+ * are not reported (zq_sync's ZQ_WDEGENERATE has no equivalent here).
+ *
+ * The first call on each device looks up the address of the static array
+ * (cudaGetSymbolAddress, with that device made current for the lookup, then
+ * the caller's current device restored); make that first call before any
+ * stream capture starts on the device.  Later calls only launch one kernel.
+ *
+ * All calls on a device share the one array: two calls whose kernels can
+ * run at the same time (different streams, or different host threads,
+ * without an event or a synchronisation between them) race on it and both
+ * results are undefined.  Issue the calls on one stream, or order them.
+ * Returns ZQ_OK, ZQ_EINVAL (NULL pointer, n or device out of range) or
+ * ZQ_ECUDA (lookup or launch failed). */
+#define ZQ_NOALLOC_MAX_BEADS 2048
+zq_status zq_apply_Q_noalloc(int device, void *stream, int64_t n, const double *x, const double *y,
+                             const double *z, const double *v, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,395 @@
+// zq_noalloc.cu -- zq_apply_Q_noalloc: Q~v for one small body without any
+// device allocation.
+//
+// For callers that cannot allocate device memory at the point of the call
+// (code that runs where cudaMalloc is unavailable or not allowed: inside a
+// host framework that owns all device memory through its own allocator, a
+// real-time loop with a fixed memory budget, or a plugin that receives only
+// device pointers).  Everything the computation needs besides the caller's
+// inputs and outputs lives in one file-scope device array of fixed size
+// (kScratchBytes below), which every GPU that loads the library holds until
+// the process exits.
+//
+// One thread block computes, for one body of 3 <= n <= ZQ_NOALLOC_MAX_BEADS
+// beads: the bisection tree (same readings as the rest of the library:
+// 21-bit keys, z/y/x bisection, ties by index), then, height by height, each
+// node's FP64 transform (Case I closed form, or the Householder LQ of
+// [T22_x | T22_y | K] with the LAPACK sign convention and the numerical-zero
+// rule) immediately applied to the node's Info-set, writing the Residues to
+// the output in the same order as zq_apply_Q.
+#include <mutex>
+
+#include "zq_internal.cuh"
+
+namespace zq {
+namespace {
+
+constexpr int kNA = ZQ_NOALLOC_MAX_BEADS;  // beads
+constexpr int kNAThreads = 512;
+
+// Scratch layout (per body of at most kNA beads; node arrays indexed by
+// split position g in [0, n - 2]):
+struct NAScratch {
+  int32_t perm[kNA];
+  int32_t cl[kNA], cr[kNA], first[kNA], cnt[kNA], height[kNA], roff[kNA];
+  double st[kNA][9];    // centroid (3), T22 packed lower triangle (6)
+  double info[kNA][6];  // Info-set [t; r]
+};
+constexpr size_t kScratchBytes = sizeof(NAScratch);
+
+// The scratch every call shares.  Host code must not use this name as a
+// device address: kernels receive the address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+__device__ __forceinline__ uint64_t na_spread3(uint32_t v) {
+  uint64_t s = v & 0x1fffffull;
+  s = (s | (s << 32)) & 0x1f00000000ffffull;
+  s = (s | (s << 16)) & 0x1f0000ff0000ffull;
+  s = (s | (s << 8)) & 0x100f00f00f00f00full;
+  s = (s | (s << 4)) & 0x10c30c30c30c30c3ull;
+  s = (s | (s << 2)) & 0x1249249249249249ull;
+  return s;
+}
+
+__device__ __forceinline__ uint32_t na_quantise(double p, double lo, double hi) {
+  if (!(hi > lo)) return 0u;
+  const double t = __ddiv_rn(__dsub_rn(p, lo), __dsub_rn(hi, lo));
+  const double s = floor(__dmul_rn(t, (double)(1u << kQBits)));
+  const double top = (double)((1u << kQBits) - 1);
+  return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
+}
+
+// Householder LQ of the 3 x k matrix M = A^T (A given as k x 3): fills L
+// (3 x 3 lower, packed) and the dense k x k G = H3 H2 H1.
+__device__ void na_lq(double (&A)[9][3], int k, double* L, double (&G)[9][9]) {
+  double v[3][9], tau[3];
+  int emax = -100000;
+  for (int i = 0; i < k; ++i)
+    for (int c = 0; c < 3; ++c)
+      if (A[i][c] != 0.0 && ilogb(A[i][c]) > emax) emax = ilogb(A[i][c]);
+  for (int j = 0; j < 3; ++j) {
+    for (int i = j; i < k; ++i)
+      if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;
+    for (int i = 0; i < k; ++i) v[j][i] = 0.0;
+    v[j][j] = 1.0;
+    double xn2 = 0.0;
+    for (int i = j + 1; i < k; ++i) xn2 += A[i][j] * A[i][j];
+    if (xn2 == 0.0) {
+      tau[j] = 0.0;
+      continue;
+    }
+    const double al = A[j][j];
+    const double norm = sqrt(al * al + xn2);
+    const double be = (al >= 0.0) ? -norm : norm;
+    tau[j] = (be - al) / be;
+    for (int i = j + 1; i < k; ++i) v[j][i] = A[i][j] / (al - be);
+    A[j][j] = be;
+    for (int i = j + 1; i < k; ++i) A[i][j] = 0.0;
+    for (int c = j + 1; c < 3; ++c) {
+      double w = 0.0;
+      for (int i = j; i < k; ++i) w += v[j][i] * A[i][c];
+      for (int i = j; i < k; ++i) A[i][c] -= tau[j] * w * v[j][i];
+    }
+  }
+  L[0] = A[0][0]; L[1] = A[0][1]; L[2] = A[1][1]; L[3] = A[0][2]; L[4] = A[1][2]; L[5] = A[2][2];
+  for (int r = 0; r < k; ++r)
+    for (int c = 0; c < k; ++c) G[r][c] = (r == c) ? 1.0 : 0.0;
+  for (int j = 0; j < 3; ++j)
+    for (int c = 0; c < k; ++c) {
+      double w = 0.0;
+      for (int i = 0; i < k; ++i) w += v[j][i] * G[i][c];
+      for (int i = 0; i < k; ++i) G[i][c] -= tau[j] * w * v[j][i];
+    }
+}
+
+__global__ void __launch_bounds__(kNAThreads)
+k_noalloc_apply_q(NAScratch* __restrict__ S, int n, const double* __restrict__ x,
+                  const double* __restrict__ y, const double* __restrict__ z,
+                  const double* __restrict__ vin, double* __restrict__ out) {
+  __shared__ uint64_t key[kNA];
+  __shared__ uint16_t idx[kNA];
+  __shared__ uint8_t lcp[kNA];
+  __shared__ unsigned long long slot[kNA];
+  __shared__ double red[kNAThreads / 32][6];
+  __shared__ double lim[6];
+  __shared__ int32_t part[kNAThreads / 32 + 1];
+  __shared__ int hroot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // ---- bounding box
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = tid; i < n; i += kNAThreads) {
+    const double p[3] = {x[i], y[i], z[i]};
+    for (int c = 0; c < 3; ++c) {
+      mn[c] = fmin(mn[c], p[c]);
+      mx[c] = fmax(mx[c], p[c]);
+    }
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int d = 16; d > 0; d >>= 1) {
+      mn[c] = fmin(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], d));
+      mx[c] = fmax(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], d));
+    }
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) {
+      red[warp][c] = mn[c];
+      red[warp][3 + c] = mx[c];
+    }
+  __syncthreads();
+  if (tid < 6) {
+    double r = red[0][tid];
+    for (int w = 1; w < kNAThreads / 32; ++w) r = tid < 3 ? fmin(r, red[w][tid]) : fmax(r, red[w][tid]);
+    lim[tid] = r;
+  }
+  __syncthreads();
+
+  // ---- keys and sort by (key, index): bitonic network in shared memory
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = tid; i < P; i += kNAThreads) {
+    if (i < n) {
+      uint32_t q[3] = {na_quantise(x[i], lim[0], lim[3]), na_quantise(y[i], lim[1], lim[4]),
+                       na_quantise(z[i], lim[2], lim[5])};
+      key[i] = na_spread3(q[0]) | (na_spread3(q[1]) << 1) | (na_spread3(q[2]) << 2);
+      idx[i] = (uint16_t)i;
+    } else {
+      key[i] = ~0ull;
+      idx[i] = 0xffffu;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = tid; t < (P >> 1); t += kNAThreads) {
+        const int a = 2 * t - (t & (stride - 1)), b = a + stride;
+        const bool asc = (a & size) == 0;
+        const uint64_t ka = key[a], kb = key[b];
+        const uint16_t ia = idx[a], ib = idx[b];
+        if (((ka > kb) || (ka == kb && ia > ib)) == asc) {
+          key[a] = kb; key[b] = ka;
+          idx[a] = ib; idx[b] = ia;
+        }
+      }
+      __syncthreads();
+    }
+  for (int p = tid; p < n; p += kNAThreads) {
+    S->perm[p] = idx[p];
+    slot[p] = 0ull;  // arrival slots must start empty in every call
+    if (p < n - 1) {
+      const uint64_t k1 = key[p], k2 = key[p + 1];
+      lcp[p] = (uint8_t)(k1 != k2 ? __clzll((long long)(k1 ^ k2)) - 1
+                                  : 63 + __clz((int)((uint32_t)idx[p] ^ (uint32_t)idx[p + 1])));
+    }
+  }
+  __syncthreads();
+
+  // ---- bottom-up construction (as zq_smalltree.cu)
+  for (int leaf = tid; leaf < n; leaf += kNAThreads) {
+    int l = leaf, r = leaf, h = 0;
+    int32_t code = -1 - leaf;
+    for (;;) {
+      if (l == 0 && r == n - 1) {
+        hroot = h;
+        break;
+      }
+      const bool is_left = (l == 0) || (r != n - 1 && lcp[r] > lcp[l - 1]);
+      const int g = is_left ? r : l - 1;
+      const unsigned long long mine = (1ull << 63) | ((unsigned long long)(uint32_t)code << 24) |
+                                      ((unsigned long long)(is_left ? l : r) << 8) | (unsigned)h;
+      const unsigned long long other = atomicExch(&slot[g], mine);
+      if (other == 0ull) break;
+      const int32_t sib = (int32_t)(uint32_t)(other >> 24);
+      const int end = (int)((other >> 8) & 0xffff), hs = (int)(other & 0xff);
+      const int lo_ = is_left ? l : end, hi_ = is_left ? end : r;
+      const int32_t lc = is_left ? code : sib, rc = is_left ? sib : code;
+      h = 1 + (h > hs ? h : hs);
+      S->cl[g] = lc;
+      S->cr[g] = rc;
+      S->first[g] = lo_;
+      S->cnt[g] = hi_ - lo_ + 1;
+      S->height[g] = h;
+      S->roff[g] = 3 * ((lc >= 0) + (rc >= 0));
+      code = g;
+      l = lo_;
+      r = hi_;
+    }
+  }
+  __syncthreads();
+
+  // ---- residue offsets: exclusive prefix over split positions
+  {
+    const int per = (n - 1 + kNAThreads - 1) / kNAThreads;
+    const int g0 = tid * per, g1 = min(n - 1, g0 + per);
+    int32_t s = 0;
+    for (int g = g0; g < g1; ++g) s += S->roff[g];
+    int32_t inc = s;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += t;
+    }
+    if (lane == 31) part[warp] = inc;
+    __syncthreads();
+    if (tid == 0) {
+      int32_t acc = 0;
+      for (int w = 0; w < kNAThreads / 32; ++w) {
+        const int32_t t = part[w];
+        part[w] = acc;
+        acc += t;
+      }
+    }
+    __syncthreads();
+    int32_t run = part[warp] + inc - s;
+    for (int g = g0; g < g1; ++g) {
+      const int32_t v = S->roff[g];
+      S->roff[g] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+
+  // ---- height by height: node transform (FP64) and upward step
+  for (int hh = 1; hh <= hroot; ++hh) {
+    for (int g = tid; g < n - 1; g += kNAThreads) {
+      if (S->height[g] != hh) continue;
+      const int32_t cx = S->cl[g], cy = S->cr[g];
+      double cX[3], cY[3], LX[6], LY[6], tX[3], tY[3], rX[3], rY[3];
+      int nx, ny;
+      if (cx < 0) {
+        const int b = S->perm[-1 - cx];
+        cX[0] = x[b]; cX[1] = y[b]; cX[2] = z[b];
+        tX[0] = vin[b]; tX[1] = vin[n + b]; tX[2] = vin[2 * n + b];
+        nx = 1;
+      } else {
+        for (int i = 0; i < 3; ++i) cX[i] = S->st[cx][i];
+        for (int i = 0; i < 6; ++i) LX[i] = S->st[cx][3 + i];
+        for (int i = 0; i < 3; ++i) { tX[i] = S->info[cx][i]; rX[i] = S->info[cx][3 + i]; }
+        nx = S->cnt[cx];
+      }
+      if (cy < 0) {
+        const int b = S->perm[-1 - cy];
+        cY[0] = x[b]; cY[1] = y[b]; cY[2] = z[b];
+        tY[0] = vin[b]; tY[1] = vin[n + b]; tY[2] = vin[2 * n + b];
+        ny = 1;
+      } else {
+        for (int i = 0; i < 3; ++i) cY[i] = S->st[cy][i];
+        for (int i = 0; i < 6; ++i) LY[i] = S->st[cy][3 + i];
+        for (int i = 0; i < 3; ++i) { tY[i] = S->info[cy][i]; rY[i] = S->info[cy][3 + i]; }
+        ny = S->cnt[cy];
+      }
+      const double dn = (double)(nx + ny);
+      const double al = sqrt((double)nx / dn), be = sqrt((double)ny / dn);
+      const double sk = sqrt((double)nx * (double)ny / dn);
+      double d[3], cp[3], L[6], G[9][9];
+      for (int i = 0; i < 3; ++i) {
+        d[i] = cX[i] - cY[i];
+        cp[i] = ((double)nx * cX[i] + (double)ny * cY[i]) / dn;
+      }
+      int k;
+      if (cx < 0 && cy < 0) {  // Case I, Eqs. 3.9-3.10
+        k = 3;
+        const double dd2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        for (int i = 0; i < 6; ++i) L[i] = 0.0;
+        if (dd2 == 0.0) {
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) G[r][c] = (r == c) ? 1.0 : 0.0;
+        } else {
+          const double dnorm = sqrt(dd2);
+          const double hd[3] = {d[0] / dnorm, d[1] / dnorm, d[2] / dnorm};
+          double g1[3];
+          if (d[1] != 0.0 || d[2] != 0.0) {
+            const double s = sqrt(d[1] * d[1] + d[2] * d[2]);
+            g1[0] = 0.0; g1[1] = -d[2] / s; g1[2] = d[1] / s;
+          } else {
+            g1[0] = 0.0; g1[1] = 0.0; g1[2] = d[0] > 0.0 ? -1.0 : 1.0;
+          }
+          const double g2[3] = {hd[1] * g1[2] - hd[2] * g1[1], hd[2] * g1[0] - hd[0] * g1[2],
+                                hd[0] * g1[1] - hd[1] * g1[0]};
+          for (int c = 0; c < 3; ++c) {
+            G[0][c] = g1[c];
+            G[1][c] = g2[c];
+            G[2][c] = -hd[c];
+          }
+          const double sl = sk * dnorm;
+          L[0] = sl * g2[0]; L[1] = sl * g2[1]; L[2] = -sl * g1[1];
+          L[3] = sl * g2[2]; L[4] = -sl * g1[2]; L[5] = 0.0;
+        }
+      } else {                 // Eq. 3.5 / Case II
+        double A[9][3];
+        k = 0;
+        const double* Ls[2] = {cx >= 0 ? LX : nullptr, cy >= 0 ? LY : nullptr};
+        for (int c = 0; c < 2; ++c) {
+          const double* Lc = Ls[c];
+          if (!Lc) continue;
+          A[k][0] = Lc[0]; A[k][1] = Lc[1]; A[k][2] = Lc[3];
+          A[k + 1][0] = 0.0; A[k + 1][1] = Lc[2]; A[k + 1][2] = Lc[4];
+          A[k + 2][0] = 0.0; A[k + 2][1] = 0.0; A[k + 2][2] = Lc[5];
+          k += 3;
+        }
+        A[k][0] = sk * 0.0; A[k][1] = sk * d[2]; A[k][2] = sk * (-d[1]);
+        A[k + 1][0] = sk * (-d[2]); A[k + 1][1] = sk * 0.0; A[k + 1][2] = sk * d[0];
+        A[k + 2][0] = sk * d[1]; A[k + 2][1] = sk * (-d[0]); A[k + 2][2] = sk * 0.0;
+        k += 3;
+        na_lq(A, k, L, G);
+      }
+      // upward step: [r; eps] = G [r_x?; r_y?; s], t = alpha t_x + beta t_y
+      double u[9], t[3];
+      int m = 0;
+      if (cx >= 0) for (int i = 0; i < 3; ++i) u[m++] = rX[i];
+      if (cy >= 0) for (int i = 0; i < 3; ++i) u[m++] = rY[i];
+      for (int i = 0; i < 3; ++i) {
+        t[i] = al * tX[i] + be * tY[i];
+        u[m++] = be * tX[i] - al * tY[i];
+      }
+      double yv[9];
+      for (int i = 0; i < k; ++i) {
+        yv[i] = 0.0;
+        for (int c = 0; c < k; ++c) yv[i] += G[i][c] * u[c];
+      }
+      for (int i = 3; i < k; ++i) out[S->roff[g] + i - 3] = yv[i];
+      for (int i = 0; i < 3; ++i) {
+        S->st[g][i] = cp[i];
+        S->info[g][i] = t[i];
+        S->info[g][3 + i] = yv[i];
+      }
+      for (int i = 0; i < 6; ++i) S->st[g][3 + i] = L[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Device address of the scratch array, looked up once per device.
+std::mutex g_noalloc_mu;
+NAScratch* g_noalloc_ptr[64] = {nullptr};
+
+}  // namespace
+}  // namespace zq
+
+extern "C" zq_status zq_apply_Q_noalloc(int device, void* cuda_stream, int64_t n, const double* x,
+                                        const double* y, const double* z, const double* v, double* out) {
+  using namespace zq;
+  if (n < 3 || n > ZQ_NOALLOC_MAX_BEADS || !x || !y || !z || !v || !out || device < 0 || device >= 64)
+    return ZQ_EINVAL;
+  NAScratch* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+      int prev = 0;
+      if (cudaGetDevice(&prev) != cudaSuccess) return ZQ_ECUDA;
+      if (cudaSetDevice(device) != cudaSuccess) return ZQ_ECUDA;
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      cudaSetDevice(prev);
+      if (e != cudaSuccess || !p) return ZQ_ECUDA;
+      g_noalloc_ptr[device] = static_cast<NAScratch*>(p);
+    }
+    scratch = g_noalloc_ptr[device];
+  }
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return ZQ_ECUDA;
+  if (prev != device && cudaSetDevice(device) != cudaSuccess) return ZQ_ECUDA;
+  k_noalloc_apply_q<<<1, kNAThreads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+      scratch, (int)n, x, y, z, v, out);
+  const cudaError_t e = cudaGetLastError();
+  if (prev != device) cudaSetDevice(prev);
+  return e == cudaSuccess ? ZQ_OK : ZQ_ECUDA;
+}

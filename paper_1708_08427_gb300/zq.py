@@ -80,6 +80,8 @@ def _lib() -> ctypes.CDLL:
         L.zq_set_build_arith.argtypes = [_vp, ctypes.c_int]
         L.zq_launch_count.restype = ctypes.c_int
         L.zq_launch_count.argtypes = [_vp, _i64p]
+        L.zq_apply_Q_noalloc.restype = ctypes.c_int
+        L.zq_apply_Q_noalloc.argtypes = [ctypes.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
         _L = L
     return _L
 
@@ -265,6 +267,29 @@ class Context:
             tail += k - 1 - j
             G = G - rec[2 + j] * np.outer(v, v @ G)
         return G
+
+
+ZQ_NOALLOC_MAX_BEADS = 2048
+
+
+def apply_Q_noalloc(x, y, z, v, out, stream=None):
+    """Q~v for one body of 3..ZQ_NOALLOC_MAX_BEADS beads through
+    zq_apply_Q_noalloc (no device allocation in the library; the caller
+    provides every buffer).  x, y, z: (n,) float64 device tensors; v: (3, n)
+    float64 device planes; out: (3n - 6,) float64 device tensor."""
+    import torch
+
+    n = int(x.numel())
+    if not 3 <= n <= ZQ_NOALLOC_MAX_BEADS:
+        raise ValueError(f"zq_apply_Q_noalloc takes 3..{ZQ_NOALLOC_MAX_BEADS} beads, got {n}")
+    for t in (x, y, z, v, out):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    assert v.numel() == 3 * n and out.numel() == 3 * n - 6
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    _check(_lib().zq_apply_Q_noalloc(x.device.index, _vp(stream.cuda_stream), n, _ptr(x), _ptr(y),
+                                      _ptr(z), _ptr(v), _ptr(out)), "zq_apply_Q_noalloc")
+    return out
 
 
 # raw C entry points, same names as include/zq.h
