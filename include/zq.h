@@ -203,8 +203,10 @@ zq_status zq_get_nodes(zq_ctx *ctx, double *centroid, double *T22);
 
 /* Node-transform export (synchronous; HOST array of (N - m) * 28 doubles):
  * per node q, rec[28*q + i]: [0] sqrt(n_x/n), [1] sqrt(n_y/n), [2..4] the
- * Householder factors tau_1..3 of Eq. 3.5's LQ (G = H_3 H_2 H_1,
- * H_j = I - tau_j v_j v_j^T, v_j(j) = 1, v_j zero above j), then the
+ * Householder factors tau_1..3 of Eq. 3.5's LQ (G = D H_3 H_2 H_1,
+ * H_j = I - |tau_j| v_j v_j^T, v_j(j) = 1, v_j zero above j; D diagonal,
+ * D_jj = -1 where the sign bit of tau_j is set (T22's diagonal made
+ * nonnegative; tau_j may be -0.0), else 1), then the
  * reflector entries below the unit entry: v_1(2..k), v_2(3..k), v_3(4..k)
  * for k = 6, 9; for Case I (k = 3) entries 5..13 hold G row-major. */
 zq_status zq_get_records(zq_ctx *ctx, double *rec);

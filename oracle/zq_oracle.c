@@ -40,13 +40,19 @@
  *     left subtree ends at in-order leaf g.  Residues are stored in order of
  *     g; within a node, in the order of the rows 4..k of G.
  *   - The LQ factorisation is the Householder QR of M^T exactly as LAPACK
- *     dgeqrf/dorgqr (and hence Matlab qr) computes it: T22 = R(1:3,1:3)^T,
- *     G = Q^T, no sign normalisation; a column whose part below the
- *     diagonal is exactly zero gets no reflection.  Before each reflection,
+ *     dgeqrf/dorgqr (and hence Matlab qr) computes it, then the diagonal of R
+ *     made nonnegative by flipping the signs of rows of R and of Q^T
+ *     together: T22 = R(1:3,1:3)^T lower triangular with a nonnegative
+ *     diagonal (the layout of Eq. 3.6), G = Q^T; a column whose part below
+ *     the diagonal is exactly zero gets no reflection.  Before each reflection,
  *     entries of the column whose binary exponent is more than 40 below
  *     that of the largest entry of M are set to 0 (rounding noise of an
  *     exact zero when M is rank-deficient; LAPACK would reflect on the
  *     noise).
+ *   - A node whose T22 comes out (numerically) singular is flagged
+ *     degenerate: a diagonal entry of T22 zero or more than 33 binary
+ *     orders below M's largest entry; coincident beads in Case I (d = 0)
+ *     are flagged too.
  *   - Case I: G rows are the three rows of U in Eq. 3.10 with the factor
  *     [1, -1]/sqrt(2) removed: g1 = (e_x x d)/|e_x x d|, g2 = dhat x g1,
  *     g3 = -dhat, d = c_x - c_y; T22 = K G^T, which reduces to
@@ -73,7 +79,7 @@
 typedef struct {
   int k;          /* size of G: 3 (two leaves), 6 (one leaf), 9 (none) */
   int cnt;        /* beads below the node */
-  int degenerate; /* Case I with coincident beads */
+  int degenerate; /* coincident beads (Case I) or singular T22 */
   double alpha;   /* sqrt(n_x / n) */
   double beta;    /* sqrt(n_y / n) */
   double c[3];    /* centroid */
@@ -216,6 +222,14 @@ static void lq(const double *M, int k, double *L, double *G) {
       for (int i = j; i < k; ++i) A[i][c] -= tau[j] * w * v[j][i];
     }
   }
+  /* Nonnegative diagonal of R: row j of R and column j of Q (row j of G)
+   * change sign together, which leaves M = [T22 0] G unchanged. */
+  int flip[3];
+  for (int j = 0; j < 3; ++j) {
+    flip[j] = A[j][j] < 0.0;
+    if (flip[j])
+      for (int c = j; c < 3; ++c) A[j][c] = -A[j][c];
+  }
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) L[3 * r + c] = (c <= r) ? A[c][r] : 0.0;
   /* G = Q^T = H_3 H_2 H_1 (each H_j symmetric): apply H_1, H_2, H_3 to I. */
@@ -228,6 +242,23 @@ static void lq(const double *M, int k, double *L, double *G) {
       for (int i = 0; i < k; ++i) G[i * k + c] -= tau[j] * w * v[j][i];
     }
   }
+  for (int j = 0; j < 3; ++j)
+    if (flip[j])
+      for (int c = 0; c < k; ++c) G[j * k + c] = -G[j * k + c];
+}
+
+/* Rank test of Eq. 3.5's M after its factorisation (no pivoting, so a
+ * rank loss can show at any pivot): the node is flagged when a diagonal
+ * entry of T22 is zero or its binary exponent is more than 33 below that of
+ * M's largest entry (below about 1e-10 of max |M|): collinear or coincident
+ * beads below the node. */
+static int rank_deficient(const double *M, int k, const double *L) {
+  int emax = INT_MIN;
+  for (int i = 0; i < 3 * k; ++i)
+    if (M[i] != 0.0 && ilogb(M[i]) > emax) emax = ilogb(M[i]);
+  for (int j = 0; j < 3; ++j)
+    if (L[4 * j] == 0.0 || ilogb(L[4 * j]) < emax - 33) return 1;
+  return 0;
 }
 
 /* Case I, bead & bead (Eqs. 3.9-3.10).  d = c_x - c_y, sk = sqrt(n_x n_y/n). */
@@ -331,6 +362,7 @@ static void transform(orc_body *b, int32_t code) {
     for (int r = 0; r < 3; ++r) M[r * k + col] = sk * K[3 * r + c];
   p->k = k;
   lq(M, k, p->L, p->G);
+  p->degenerate = rank_deficient(M, k, p->L);
 }
 
 /* ------------------------------------------------------------------ */

@@ -12,8 +12,9 @@
 //   L_x = [alpha T + beta sigma; a_x],  L_y = [beta T - alpha sigma; a_y],
 // and a leaf's velocity is the first three entries of its Velocity-set.
 //
-// G is applied as its three Householder reflectors (G u = H3 H2 H1 u,
-// G^T z = H1 H2 H3 z) restricted to their possibly nonzero rows, or as the
+// G is applied as its three Householder reflectors with the diagonal sign
+// normalisation D = diag(+-1, +-1, +-1, 1, ...) (G u = D H3 H2 H1 u,
+// G^T z = H1 H2 H3 D z) restricted to their possibly nonzero rows, or as the
 // explicit 3 x 3 matrix for Case I.
 //
 // Schedule: heights 1..cut level by level over all bodies (records and
@@ -99,10 +100,19 @@ __device__ __forceinline__ void store_bead(const ApplyArgs<T>& a, int32_t code, 
   a.out[2 * a.N + i] = L[2];
 }
 
-// u <- H u with H = I - tau v v^T, v(j) = 1 and the other nonzeros of v at
-// rows R[0..n-1] with values vv[0..n-1].
-template <typename T, int NV>
-__device__ __forceinline__ void reflect(T* u, int j, const int (&R)[NV], const T* vv, T tau) {
+__device__ __forceinline__ bool sign_set(float x) { return __float_as_int(x) < 0; }
+__device__ __forceinline__ bool sign_set(double x) { return __double2hiint(x) < 0; }
+
+// One factor D_j H_j of G = (D_3 H_3)(D_2 H_2)(D_1 H_1): H_j = I - |tau| v v^T
+// with v(j) = 1 and the other nonzeros of v at rows R[0..n-1] with values
+// vv[0..n-1]; D_j negates entry j when tau's sign bit is set (the diagonal
+// sign normalisation of T22).  TR = false: u <- D_j H_j u (forward);
+// TR = true: u <- H_j D_j u (the transpose, G^T = H_1 D_1 H_2 D_2 H_3 D_3).
+template <typename T, int NV, bool TR>
+__device__ __forceinline__ void reflect(T* u, int j, const int (&R)[NV], const T* vv, T tau_s) {
+  const bool neg = sign_set(tau_s);
+  const T tau = neg ? -tau_s : tau_s;
+  if (TR && neg) u[j] = -u[j];
   T w = u[j];
 #pragma unroll
   for (int i = 0; i < NV; ++i) w += vv[i] * u[R[i]];
@@ -110,6 +120,7 @@ __device__ __forceinline__ void reflect(T* u, int j, const int (&R)[NV], const T
   u[j] -= w;
 #pragma unroll
   for (int i = 0; i < NV; ++i) u[R[i]] -= w * vv[i];
+  if (!TR && neg) u[j] = -u[j];
 }
 
 // G u and G^T u for the two Householder record types (layout in zq_internal.cuh).
@@ -117,13 +128,13 @@ template <typename T>
 __device__ __forceinline__ void g6(const T* r, T* u, bool transpose) {
   constexpr int R0[2] = {4, 5}, R1[3] = {3, 4, 5}, R2[3] = {3, 4, 5};
   if (!transpose) {
-    reflect<T, 2>(u, 0, R0, r + 5, r[2]);
-    reflect<T, 3>(u, 1, R1, r + 7, r[3]);
-    reflect<T, 3>(u, 2, R2, r + 10, r[4]);
+    reflect<T, 2, false>(u, 0, R0, r + 5, r[2]);
+    reflect<T, 3, false>(u, 1, R1, r + 7, r[3]);
+    reflect<T, 3, false>(u, 2, R2, r + 10, r[4]);
   } else {
-    reflect<T, 3>(u, 2, R2, r + 10, r[4]);
-    reflect<T, 3>(u, 1, R1, r + 7, r[3]);
-    reflect<T, 2>(u, 0, R0, r + 5, r[2]);
+    reflect<T, 3, true>(u, 2, R2, r + 10, r[4]);
+    reflect<T, 3, true>(u, 1, R1, r + 7, r[3]);
+    reflect<T, 2, true>(u, 0, R0, r + 5, r[2]);
   }
 }
 
@@ -131,13 +142,13 @@ template <typename T>
 __device__ __forceinline__ void g9(const T* r, T* u, bool transpose) {
   constexpr int R0[3] = {3, 7, 8}, R1[5] = {3, 4, 6, 7, 8}, R2[6] = {3, 4, 5, 6, 7, 8};
   if (!transpose) {
-    reflect<T, 3>(u, 0, R0, r + 5, r[2]);
-    reflect<T, 5>(u, 1, R1, r + 8, r[3]);
-    reflect<T, 6>(u, 2, R2, r + 13, r[4]);
+    reflect<T, 3, false>(u, 0, R0, r + 5, r[2]);
+    reflect<T, 5, false>(u, 1, R1, r + 8, r[3]);
+    reflect<T, 6, false>(u, 2, R2, r + 13, r[4]);
   } else {
-    reflect<T, 6>(u, 2, R2, r + 13, r[4]);
-    reflect<T, 5>(u, 1, R1, r + 8, r[3]);
-    reflect<T, 3>(u, 0, R0, r + 5, r[2]);
+    reflect<T, 6, true>(u, 2, R2, r + 13, r[4]);
+    reflect<T, 5, true>(u, 1, R1, r + 8, r[3]);
+    reflect<T, 3, true>(u, 0, R0, r + 5, r[2]);
   }
 }
 

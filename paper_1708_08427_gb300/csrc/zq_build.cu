@@ -8,7 +8,8 @@
 //   M = [T22_x | T22_y | K] (3 x k; a leaf child has no T22 block, Case II),
 //   M = [T22_p 0] G by Householder reflections of A = M^T (Eq. 3.5; LAPACK
 //       dgeqrf convention: beta_j = -sign(alpha_j) ||x||, no reflection when
-//       the part below the diagonal is exactly zero; T22_p = R^T, G = Q^T);
+//       the part below the diagonal is exactly zero; then R's diagonal made
+//       nonnegative; T22_p = R^T, G = Q^T);
 //       before each reflection, column entries whose binary exponent is
 //       more than 40 below that of M's largest entry are set to zero, so
 //       rank-deficient M (collinear or coincident beads) give a transform
@@ -257,6 +258,25 @@ __device__ __forceinline__ void flush(R& v, int lim) {
   if (Real<R>::bexp(v) < lim) v = Real<R>::from_float(0.0f);
 }
 
+// After the three reflections: the rank test, then T22's diagonal made
+// nonnegative.  Row j of R (column j of T22) and row j of G change sign
+// together; the flip of G's row j is recorded in the sign bit of tau_j
+// (tau_j >= 0 otherwise; -0.0 when H_j = I).  A node is flagged degenerate
+// when a pivot is zero or more than 33 binary orders below M's largest
+// entry (lim + 40): collinear or coincident beads below it.
+template <class R>
+__device__ __forceinline__ void finish_lq(const BuildArgs& a, int lim, R& A00, R& A01, R& A02, R& A11,
+                                          R& A12, R& A22, R* rec) {
+  using RT = Real<R>;
+  const int lo = lim + 7;
+  if (RT::is_zero(A00) || RT::is_zero(A11) || RT::is_zero(A22) || RT::bexp(A00) < lo ||
+      RT::bexp(A11) < lo || RT::bexp(A22) < lo)
+    atomicOr(a.err, kErrDegenerate);
+  if (!RT::ge_zero(A00)) { A00 = -A00; A01 = -A01; A02 = -A02; rec[2] = -rec[2]; }
+  if (!RT::ge_zero(A11)) { A11 = -A11; A12 = -A12; rec[3] = -rec[3]; }
+  if (!RT::ge_zero(A22)) { A22 = -A22; rec[4] = -rec[4]; }
+}
+
 // ------------------------------------------------- k = 6 (Case II)
 // A rows: 0-2 = T22_c^T of the internal child, 3-5 = K^T.
 template <class R>
@@ -313,6 +333,7 @@ __device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
     const R tau = reflector<R, 3>(A22, x);
     rec[4] = tau; rec[10] = x[0]; rec[11] = x[1]; rec[12] = x[2];
   }
+  finish_lq(a, lim, A00, A01, A02, A11, A12, A22, rec);
   const R L[6] = {A00, A01, A11, A02, A12, A22};
   store<R, 16>(a, s, rw, rec, g.cp, L);
 }
@@ -378,6 +399,7 @@ __device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) rec[13 + i] = x[i];
   }
+  finish_lq(a, lim, A00, A01, A02, A11, A12, A22, rec);
   const R L[6] = {A00, A01, A11, A02, A12, A22};
   store<R, 20>(a, s, rw, rec, g.cp, L);
 }

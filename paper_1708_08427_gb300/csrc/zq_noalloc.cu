@@ -14,8 +14,8 @@
 // beads: the bisection tree (same readings as the rest of the library:
 // 21-bit keys, z/y/x bisection, ties by index), then, height by height, each
 // node's FP64 transform (Case I closed form, or the Householder LQ of
-// [T22_x | T22_y | K] with the LAPACK sign convention and the numerical-zero
-// rule) immediately applied to the node's Info-set, writing the Residues to
+// [T22_x | T22_y | K] with the LAPACK reflector convention, T22's diagonal
+// made nonnegative and the numerical-zero rule) immediately applied to the node's Info-set, writing the Residues to
 // the output in the same order as zq_apply_Q.
 #include <mutex>
 
@@ -59,8 +59,9 @@ __device__ __forceinline__ uint32_t na_quantise(double p, double lo, double hi) 
   return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
 }
 
-// Householder LQ of the 3 x k matrix M = A^T (A given as k x 3): fills L
-// (3 x 3 lower, packed) and the dense k x k G = H3 H2 H1.
+// Householder LQ of the 3 x k matrix M = A^T (A given as k x 3), T22's
+// diagonal made nonnegative: fills L (3 x 3 lower, packed) and the dense
+// k x k G = D H3 H2 H1.
 __device__ void na_lq(double (&A)[9][3], int k, double* L, double (&G)[9][9]) {
   double v[3][9], tau[3];
   int emax = -100000;
@@ -91,6 +92,13 @@ __device__ void na_lq(double (&A)[9][3], int k, double* L, double (&G)[9][9]) {
       for (int i = j; i < k; ++i) A[i][c] -= tau[j] * w * v[j][i];
     }
   }
+  // nonnegative diagonal of R: rows of R and of G flip together
+  bool flip[3];
+  for (int j = 0; j < 3; ++j) {
+    flip[j] = A[j][j] < 0.0;
+    if (flip[j])
+      for (int c = j; c < 3; ++c) A[j][c] = -A[j][c];
+  }
   L[0] = A[0][0]; L[1] = A[0][1]; L[2] = A[1][1]; L[3] = A[0][2]; L[4] = A[1][2]; L[5] = A[2][2];
   for (int r = 0; r < k; ++r)
     for (int c = 0; c < k; ++c) G[r][c] = (r == c) ? 1.0 : 0.0;
@@ -100,6 +108,9 @@ __device__ void na_lq(double (&A)[9][3], int k, double* L, double (&G)[9][9]) {
       for (int i = 0; i < k; ++i) w += v[j][i] * G[i][c];
       for (int i = 0; i < k; ++i) G[i][c] -= tau[j] * w * v[j][i];
     }
+  for (int j = 0; j < 3; ++j)
+    if (flip[j])
+      for (int c = 0; c < k; ++c) G[j][c] = -G[j][c];
 }
 
 __global__ void __launch_bounds__(kNAThreads)

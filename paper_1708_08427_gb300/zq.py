@@ -265,7 +265,10 @@ class Context:
             v[j] = 1.0
             v[j + 1:] = rec[tail:tail + k - 1 - j]
             tail += k - 1 - j
-            G = G - rec[2 + j] * np.outer(v, v @ G)
+            G = G - abs(rec[2 + j]) * np.outer(v, v @ G)
+        for j in range(3):
+            if np.signbit(rec[2 + j]):
+                G[j] = -G[j]
         return G
 
 

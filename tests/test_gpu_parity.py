@@ -99,6 +99,43 @@ def check_nodes(ctx, bt, bodies):
     return worst
 
 
+def check_records(ctx, bt, bodies, arith, skip=()):
+    """The exported FP64 transforms (Householder records with the sign bits
+    of tau carrying T22's diagonal normalisation, or Case I's explicit G)
+    expand to the oracle's G node by node.  G's sensitivity to a
+    perturbation of M grows with the condition number of T22 (QR
+    perturbation bound |dG| <~ cond(T22) * |dM| / |M|), so each node is held
+    to max(1e-12, 8 * cond(T22) * u), u the relative perturbation: 2^-53 for
+    the FP64 build; for the double-single build 2^-48 plus 2^-40, because
+    its rounded entries can fall on the other side of a binade boundary
+    than the oracle's, so that the numerical-zero rule (entries more than 40
+    binary orders below max |M| set to zero) drops an entry of size about
+    2^-40 |M| on one side only.  Flagged (singular) nodes go through exact
+    zeros and are held to 1e-12.  Bodies listed in `skip` sit far from the
+    origin: there G depends on differences of FP64 centroids of size |c|,
+    whose last-bit rounding (|c| 2^-53 each, different in the oracle's and
+    the kernel's order of operations) is not a property of the method;
+    their products are checked by the sweeps."""
+    zq = _zq()
+    u = 2.0 ** -48 + 2.0 ** -40 if arith == "dd" else 2.0 ** -53
+    rec = ctx.get_records()
+    worst = 0.0
+    for j, B in enumerate(bodies):
+        if j in skip:
+            continue
+        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
+        nb = o - j
+        for gsp in range(n - 1):
+            nd = B.node(gsp)
+            G = zq.Context.record_to_G(rec[nb + gsp], nd["k"])
+            cond = np.linalg.cond(nd["L"]) if nd["k"] > 3 and not nd["degenerate"] else 0.0
+            tol = max(1e-12, 8.0 * cond * u)
+            r = np.abs(G - nd["G"]).max() / tol
+            assert r <= 1.0, (j, gsp, nd["k"], cond, r * tol)
+            worst = max(worst, r)
+    return worst
+
+
 def rel_err_per_body(got, ref, bt, kind):
     errs = []
     ro = 0
@@ -146,6 +183,7 @@ def test_single_body_256_sixteen_vectors(arith):
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
     check_nodes(ctx, bt, bodies)
+    check_records(ctx, bt, bodies, arith)
     check_apply(ctx, bt, np.float64, k=16, seed=1)
     check_apply(ctx, bt, np.float32, k=16, seed=1)
 
@@ -214,6 +252,7 @@ def test_edge_geometries(arith):
     ctx, _ = make_ctx(bt, cut=3, arith=arith)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
+    check_records(ctx, bt, bodies, arith, skip=(2,))
     check_apply(ctx, bt, np.float64)
 
 
@@ -293,5 +332,29 @@ def test_collinear_and_lattice_bodies_match(arith):
     ctx, _ = make_ctx(bt, cut=3, arith=arith)
     bodies = oracle_bodies(bt)
     check_tree(ctx, bt, bodies)
+    check_records(ctx, bt, bodies, arith)
     check_apply(ctx, bt, np.float64)
     check_apply(ctx, bt, np.float32)
+
+
+@pytest.mark.parametrize("arith", ["dd", "fp64"])
+def test_degenerate_warning_matches_oracle_flags(arith):
+    """ZQ_WDEGENERATE is raised exactly for the batches in which the oracle
+    flags a node (singular T22: collinear or coincident beads)."""
+    zq = _zq()
+    rng = np.random.default_rng(21)
+    n = 24
+    g = np.arange(n)
+    cases = [
+        [rng.uniform(0, 1, (50, 3)), rng.uniform(0, 1, (7, 3))],            # generic: no flag
+        [np.c_[g * 0.5, g * 0.25, np.full(n, 2.0)]],                          # collinear
+        [np.c_[g % 3, (g // 3) % 3, g // 9].astype(float)],                   # lattice
+        [np.c_[np.linspace(0, 1, 30), rng.normal(0, 1e-6, 30), rng.normal(0, 1e-6, 30)]],
+    ]
+    for pts in cases:
+        bt = _batch_from_points(pts)
+        ctx, _ = make_ctx(bt, cut=2, arith=arith)
+        want = any(B.node(q)["degenerate"] for B in oracle_bodies(bt) for q in range(B.n - 1))
+        got = ctx.sync(allow_degenerate=True)
+        assert got == (zq.ZQ_WDEGENERATE if want else zq.ZQ_OK), (pts[0][:2], want, got)
+        ctx.close()

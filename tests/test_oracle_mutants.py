@@ -38,6 +38,10 @@ MUTANTS = [
     ("bisect_axis_order_x_first", "int axis = 2 - l % 3; /* z, then y, then x */", "int axis = l % 3;"),
     ("bisect_msb_last", "int bit = QBITS - 1 - l / 3;", "int bit = l / 3;"),
     ("quantise_unnormalised", "double t = (p[a][i] - lo) / (hi - lo);", "double t = (p[a][i] - lo);"),
+    ("no_sign_normalisation", "flip[j] = A[j][j] < 0.0;", "flip[j] = 0;"),
+    ("sign_flip_R_only", "for (int c = 0; c < k; ++c) G[j * k + c] = -G[j * k + c];", ";"),
+    ("rank_flag_last_pivot_only", "for (int j = 0; j < 3; ++j)\n    if (L[4 * j] == 0.0", "for (int j = 2; j < 3; ++j)\n    if (L[4 * j] == 0.0"),
+    ("rank_flag_never", "p->degenerate = rank_deficient(M, k, p->L);", "p->degenerate = 0;"),
     ("no_numerical_zero_rule", "if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;", ";"),
 ]
 

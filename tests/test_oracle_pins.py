@@ -51,11 +51,23 @@ def geometry(kind, n, seed):
 # ---------------------------------------------------------------- Eq. 3.5
 
 
+def qr_nonneg(A):
+    """LAPACK's complete QR of A (k x 3) with the signs of R's diagonal made
+    nonnegative (rows of R and columns of Q flipped together)."""
+    Q, R = np.linalg.qr(A, mode="complete")
+    sgn = np.ones(A.shape[0])
+    sgn[:3] = np.where(np.diag(R[:3, :3]) < 0, -1.0, 1.0)
+    return Q * sgn, sgn[:, None] * R
+
+
 @pytest.mark.parametrize("k", [6, 9])
 @pytest.mark.parametrize("seed", range(5))
 def test_lq_matches_lapack_householder(k, seed):
-    """Eq. 3.5 is computed with 'Matlab qr' = LAPACK dgeqrf/dorgqr; numpy's qr
-    calls the same routines, so T22 = R^T and G = Q^T must agree."""
+    """Eq. 3.5 is computed with a Householder QR ('Matlab qr' = LAPACK
+    dgeqrf/dorgqr; numpy's qr calls the same routines) whose R diagonal is
+    then made nonnegative (T22 lower triangular with a nonnegative diagonal,
+    the layout of Eq. 3.6).  For full-rank M that fixes T22 and G's first
+    three rows uniquely; the completion rows are LAPACK's."""
     rng = np.random.default_rng(100 + seed)
     M = rng.standard_normal((3, k))
     if seed % 2:  # the structure of [R22 S22 K]: lower-triangular blocks and a skew block
@@ -64,9 +76,10 @@ def test_lq_matches_lapack_householder(k, seed):
         d = rng.standard_normal(3)
         M[:, k - 3:] = [[0, -d[2], d[1]], [d[2], 0, -d[0]], [-d[1], d[0], 0]]
     L, G = oracle.lq(M)
-    Q, R = np.linalg.qr(M.T, mode="complete")
+    Q, R = qr_nonneg(M.T)
     np.testing.assert_allclose(L, R[:3, :3].T, atol=1e-14, rtol=0)
     np.testing.assert_allclose(G, Q.T, atol=1e-14, rtol=0)
+    assert np.all(np.diag(L) >= 0.0)
     # and the defining properties
     np.testing.assert_allclose(G @ G.T, np.eye(k), atol=1e-14)
     np.testing.assert_allclose(np.hstack([L, np.zeros((3, k - 3))]) @ G, M, atol=1e-14)
@@ -421,7 +434,7 @@ def test_node_assembly_eq_3_5(seed):
     S22, cy = _pair_T22(*pair(ly))
     cp = 0.25 * p.sum(0)
     M = np.hstack([R22, S22, np.sqrt(2 * 4 / 2) * _cross(cx - cp)])
-    Q, R = np.linalg.qr(M.T, mode="complete")
+    Q, R = qr_nonneg(M.T)
     nd = B.node(root)
     np.testing.assert_allclose(nd["L"], R[:3, :3].T, atol=1e-13)
     np.testing.assert_allclose(nd["G"], Q.T, atol=1e-13)
@@ -440,7 +453,7 @@ def test_node_assembly_eq_3_5(seed):
         S22, _ = _pair_T22(*pair_of(t3, p3, ly))
         cx = p3[t3["perm"][t3["first"][r3]]]
         M = np.hstack([S22, np.sqrt(1 * 3 / 2) * _cross(cx - cp)])
-    Q, R = np.linalg.qr(M.T, mode="complete")
+    Q, R = qr_nonneg(M.T)
     nd = B3.node(r3)
     np.testing.assert_allclose(nd["L"], R[:3, :3].T, atol=1e-13)
     np.testing.assert_allclose(nd["G"], Q.T, atol=1e-13)
@@ -483,3 +496,36 @@ def test_collinear_and_lattice_bodies(n):
         Z = z_matrix(p[:, 0], p[:, 1], p[:, 2])
         np.testing.assert_allclose(Qt @ Qt.T, np.eye(3 * n - 6), atol=1e-13)
         assert np.abs(Qt @ Z.T).max() <= 1e-12 * np.abs(Z).max()
+
+
+def _collinear_int(P):
+    """Exact collinearity of integer points (all cross products zero)."""
+    d = P[1:] - P[0]
+    nz = d[np.any(d != 0, axis=1)]
+    if len(nz) == 0:
+        return True
+    return bool(np.all(np.cross(nz[0], nz) == 0))
+
+
+@pytest.mark.parametrize("n", [12, 27, 40])
+def test_singular_T22_flag_marks_exactly_the_collinear_nodes(n):
+    """A node's T22 is singular exactly when its beads are collinear (the
+    centred rotational rows of Z_p then have rank two, Eq. 3.3); on integer
+    lattices collinearity is decided exactly, so the flag must match it on
+    every node, and no node of a jittered shell is flagged."""
+    g = np.arange(n)
+    for P in (np.c_[g % 3, (g // 3) % 3, g // 9], np.c_[g, 2 * g, np.full(n, 5)],
+              np.c_[g % 4, g // 4, (g * 7) % 5]):
+        P = P.astype(np.int64)
+        B = oracle.Body(*(P[:, a].astype(float) for a in range(3)))
+        t = B.tree()
+        for q in range(n - 1):
+            nd = B.node(q)
+            beads = t["perm"][t["first"][q]:t["last"][q] + 1]
+            if nd["k"] == 3:
+                assert not nd["degenerate"]  # distinct beads
+            else:
+                assert nd["degenerate"] == _collinear_int(P[beads]), (q, P[beads])
+    bt = W.shell_body(n=300, seed=5)
+    B = oracle.Body(bt.x, bt.y, bt.z)
+    assert not any(B.node(q)["degenerate"] for q in range(299))
