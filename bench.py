@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["shells2000", "ellipsoid"], default="shells2000")
+    ap.add_argument("--bodies", type=int, default=2000,
+                    help="bodies of the shell workload (smaller values: profiling captures)")
     ap.add_argument("--cut", type=int, default=15, help="level cut (performance only)")
     ap.add_argument("--build", choices=["dd", "fp64"], default="dd",
                     help="node-transform arithmetic: double-single on FP32 pipes or native FP64")
@@ -105,12 +107,12 @@ def sum_over_ranks(world, x: float, device=None) -> float:
     return float(t.item())
 
 
-def make_workload(name: str, seed: int):
+def make_workload(name: str, seed: int, bodies: int = 2000):
     from paper_1708_08427_gb300 import workloads as W
 
     if name == "shells2000":
-        bt = W.shell_batch(m=2000, nmin=50, nmax=5000, seed=seed)
-        desc = ("batched jittered sphere shells: m=2000, n_j log-uniform [50,5000], radius "
+        bt = W.shell_batch(m=bodies, nmin=50, nmax=5000, seed=seed)
+        desc = (f"batched jittered sphere shells: m={bodies}, n_j log-uniform [50,5000], radius "
                 "0.1*sqrt(n_j), jitter 0.025*radius, centres U[0,100]^3")
     else:
         bt = W.ellipsoid_body(n=1 << 20, seed=seed)
@@ -265,7 +267,7 @@ def run_ours(args, world, rank, local):
 
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    bt, desc = make_workload(args.workload, seed=rank)
+    bt, desc = make_workload(args.workload, seed=rank, bodies=args.bodies)
     N, m, R = bt.N, bt.m, bt.n_residues
     stream = torch.cuda.Stream(device=dev)
     rng = np.random.default_rng(1000 + rank)
@@ -590,7 +592,7 @@ def run_reference(args, world, rank):
     step a bounded sample of the workload."""
     if rank != 0:
         return None
-    bt, desc = make_workload(args.workload, seed=0)
+    bt, desc = make_workload(args.workload, seed=0, bodies=args.bodies)
     per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     nb, _ = oracle_sample(bt, per_step)
     rng = np.random.default_rng(3)
