@@ -12,7 +12,10 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   tree            pinned: brute-force bisection on tiny inputs, an
                   independent sort-and-prefix construction, invariants.
   lq              pinned: LAPACK dgeqrf/dorgqr via numpy.linalg.qr (the
-                  paper computes Eq. 3.5 with Matlab qr, which is LAPACK).
+                  paper computes Eq. 3.5 with Matlab qr, which is LAPACK),
+                  with R's diagonal made nonnegative (unique for full rank).
+  degenerate      pinned: the singular-T22 flag equals exact collinearity
+                  of the node's beads on integer lattices.
   case_one        pinned: the printed closed form, Eqs. 3.9-3.10.
   apply_Q/_QT     pinned: dense projector I - Z^T (Z Z^T)^{-1} Z, SVD
                   complement, rigid-field annihilation, Parseval,
