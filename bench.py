@@ -227,7 +227,7 @@ def kernel_work(name, census, N, R, m, es):
     """(bound, algorithmic amount per launch, unit)."""
     if name in ("build_level", "build_tail"):
         return "alu", sum(census[k] * build_flops(k) for k in census), "flop"
-    if name in ("up_level", "down_level"):
+    if name in ("up_seg", "down_seg"):
         return "hbm", sweep_bytes(census, N, R, es), "B"
     if name == "sort_small":
         return "hbm", 8 * N + 8 * N + 4 * N, "B"
@@ -292,8 +292,8 @@ def run_ours(args, world, rank, local):
     census = node_census(ctx)
 
     # --- per-kernel time of one step (measurement hook), picks the dominant kernel
-    names = ["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "schedule",
-             "build_level", "build_tail", "up_level", "up_tail", "down_tail", "down_level"]
+    names = ["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "segments",
+             "schedule", "build_level", "build_tail", "up_seg", "up_top", "down_top", "down_seg"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e1.record(stream)
@@ -313,7 +313,7 @@ def run_ours(args, world, rank, local):
             tot += e0.elapsed_time(e1)
         ctx.time_kernel(None)
         phases[nm] = tot / reps
-    dominant = max(("build_level", "up_level", "down_level", "small_tree", "schedule"),
+    dominant = max(("build_level", "up_seg", "down_seg", "small_tree", "schedule", "segments"),
                    key=lambda k: phases.get(k, 0.0)) if phases else "build_level"
 
     # --- the dominant kernel is bracketed by events in every timed step

@@ -47,7 +47,7 @@
  *   the context owns the tree, the transforms and its scratch.  Apply calls
  *   never allocate.
  * Errors.  No exceptions cross the ABI.  Argument errors return at once;
- *   errors found on the device (non-finite coordinates, coincident beads)
+ *   errors found on the device (non-finite coordinates, singular node transforms)
  *   are recorded and returned by zq_sync.
  */
 #ifndef ZQ_H
@@ -69,8 +69,9 @@ typedef enum {
   ZQ_ECUDA = 3,         /* a CUDA call failed; the context is unusable */
   ZQ_ESTATE = 4,        /* called out of order (apply before build) */
   ZQ_ENONFINITE = 5,    /* a coordinate is NaN or infinite (from zq_sync) */
-  ZQ_WDEGENERATE = 6    /* warning: two beads of a body coincide; the result
-                           is orthonormal but Q~ misses a direction */
+  ZQ_WDEGENERATE = 6    /* warning: a node's T22 is singular (coincident beads,
+                           or collinear beads below a node); the result is
+                           orthonormal but Q~ may miss a direction */
 } zq_status;
 
 typedef enum { ZQ_FP64 = 0, ZQ_FP32 = 1 } zq_prec;
@@ -106,7 +107,8 @@ zq_status zq_build_tree(zq_ctx *ctx, int64_t n, const double *x, const double *y
  * Eq. 3.5, Case I closed form Eqs. 3.9-3.10, Case II Eqs. 3.11-3.13).
  * x, y, z: DEVICE, the same bodies and bead order as the tree (the beads
  * may have moved: the tree is kept).  Writes both the FP64 and the FP32
- * copy.  Asynchronous; coincident beads are reported by zq_sync. */
+ * copy.  Asynchronous; singular node transforms (coincident or collinear
+ * beads) are reported by zq_sync. */
 zq_status zq_build_transforms(zq_ctx *ctx, const double *x, const double *y, const double *z);
 
 /* out = Q~ v for k columns (upward pass, Algorithm 2, Eqs. 4.2-4.3).

@@ -29,7 +29,9 @@ void free_all(Ctx& c) {
   void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
-                c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.stage};
+                c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.stage,
+                c.par, c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.topv,
+                c.top_off, c.nseg, c.srw};
   for (void* p : ps)
     if (p) cudaFree(p);
   Ctx fresh;
@@ -91,6 +93,19 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.rec32, nodes * zq::kRecMax));
     ZQ_TRY(grow(&c.x64, nodes * 6));
     ZQ_TRY(grow(&c.x32, nodes * 6));
+    ZQ_TRY(grow(&c.par, nodes));
+    ZQ_TRY(grow(&c.pos_of, nodes));
+    ZQ_TRY(grow(&c.pnode, nodes));
+    ZQ_TRY(grow(&c.pc, nodes));
+    ZQ_TRY(grow(&c.proff, nodes));
+    ZQ_TRY(grow(&c.ph, nodes));
+    ZQ_TRY(grow(&c.prw, nodes + 1));
+    ZQ_TRY(grow(&c.seg_flag, nodes));
+    ZQ_TRY(grow(&c.seg, nodes));
+    ZQ_TRY(grow(&c.topv, nodes));
+    ZQ_TRY(grow(&c.top_off, m + 1));
+    ZQ_TRY(grow(&c.nseg, 2));
+    ZQ_TRY(grow(&c.srw, nodes));
     ZQ_CUDA_TRY(cudaMemsetAsync(c.counters, 0, 4 * sizeof(int32_t), c.stream));
     c.cap_N = N;
     c.cap_m = m;
@@ -114,7 +129,7 @@ const char* zq_status_string(zq_status s) {
     case ZQ_ECUDA: return "CUDA error";
     case ZQ_ESTATE: return "call out of order";
     case ZQ_ENONFINITE: return "non-finite coordinate";
-    case ZQ_WDEGENERATE: return "coincident beads (degenerate node)";
+    case ZQ_WDEGENERATE: return "degenerate node (coincident or collinear beads)";
   }
   return "unknown status";
 }
@@ -440,27 +455,22 @@ zq_status zq_get_records(zq_ctx* ctx, double* rec) {
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
   ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
   const size_t nodes = (size_t)c.nodes;
-  const int nb = 3 * c.cut + 1;
-  std::vector<double> cr(nodes * zq::kRecMax);
-  std::vector<int32_t> sid(nodes), bstart(nb + 1), brec(nb + 1);
-  std::vector<int2> sc(nodes);
+  std::vector<uint32_t> prw(nodes + 1);
+  std::vector<int32_t> pnode(nodes);
+  std::vector<int2> pc(nodes);
+  ZQ_CUDA_TRY(cudaMemcpy(prw.data(), c.prw, (nodes + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemcpy(pnode.data(), c.pnode, nodes * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  ZQ_CUDA_TRY(cudaMemcpy(pc.data(), c.pc, nodes * sizeof(int2), cudaMemcpyDeviceToHost));
+  std::vector<double> cr((size_t)prw[nodes] * 4);
   ZQ_CUDA_TRY(cudaMemcpy(cr.data(), c.rec64, cr.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  ZQ_CUDA_TRY(cudaMemcpy(sid.data(), c.sid, nodes * sizeof(int32_t), cudaMemcpyDeviceToHost));
-  ZQ_CUDA_TRY(cudaMemcpy(sc.data(), c.sc, nodes * sizeof(int2), cudaMemcpyDeviceToHost));
-  ZQ_CUDA_TRY(cudaMemcpy(bstart.data(), c.bstart, (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-  ZQ_CUDA_TRY(cudaMemcpy(brec.data(), c.brec, (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-  // compact (by slot) -> dense documented layout (by node id)
+  // compact (by position) -> dense documented layout (by node id)
   static const int rows6[3][3] = {{4, 5, -1}, {3, 4, 5}, {3, 4, 5}};
   static const int rows9[3][6] = {{3, 7, 8, -1, -1, -1}, {3, 4, 6, 7, 8, -1}, {3, 4, 5, 6, 7, 8}};
   static const int off6[3] = {5, 7, 10}, off9[3] = {5, 8, 13};
-  int b = 0;
-  for (size_t s = 0; s < nodes; ++s) {
-    while (b < nb - 1 && (int32_t)s >= bstart[b + 1]) ++b;
-    const int type = (sc[s].x >= 0) + (sc[s].y >= 0);
-    const bool tail = b == nb - 1;
-    const size_t rw = (size_t)brec[b] + (s - (size_t)bstart[b]) * (tail ? zq::kRecMax : zq::rec_words(type));
-    const double* r = cr.data() + rw;
-    double* d = rec + (size_t)sid[s] * zq::kRec;
+  for (size_t p = 0; p < nodes; ++p) {
+    const int type = (pc[p].x >= 0) + (pc[p].y >= 0);
+    const double* r = cr.data() + (size_t)prw[p] * 4;
+    double* d = rec + (size_t)pnode[p] * zq::kRec;
     for (int i = 0; i < zq::kRec; ++i) d[i] = 0.0;
     d[0] = r[0];
     d[1] = r[1];

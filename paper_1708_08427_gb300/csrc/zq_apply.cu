@@ -17,35 +17,38 @@
 // G^T z = H1 H2 H3 D z) restricted to their possibly nonzero rows, or as the
 // explicit 3 x 3 matrix for Case I.
 //
-// Schedule: heights 1..cut level by level over all bodies (records and
-// Info-/Velocity-sets of a height are contiguous; one launch per height),
-// the nodes above the cut one thread block per body.  Upward: levels then
-// tails; downward: tails then levels.
+// Schedule (zq_seg.cu): segments of at most kSegMax beads, one thread block
+// per segment, height by height with the Info-/Velocity-sets in shared
+// memory and the segment's bead values staged in shared memory; the nodes
+// above the segments one thread block per body, through global memory.
+// Upward: segments, then top nodes; downward: top nodes, then segments.
+// The segment's records are prefetched into L2 in bulk when its block
+// starts.
 #include "zq_internal.cuh"
 
 namespace zq {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kSegThreads = 128;
+constexpr int kTopThreads = 256;
 
 template <typename T>
-struct ApplyArgs {
+struct SweepArgs {
   int64_t N;
-  const int64_t* off;
-  const int32_t* perm;
-  const int2* sc;
-  const int32_t* sroff;
-  const uint8_t* sheight;
-  const int32_t* sid;
-  const int32_t* bstart;
-  const int32_t* brec;
-  const int32_t* root_slot;
-  int cut;
+  const int32_t* perm;     // sorted position -> bead
+  const int2* pc;          // by position: children (positions or leaves)
+  const int32_t* proff;    // residue offsets
+  const uint8_t* ph;       // heights
+  const uint32_t* prw;     // record offsets, 4-word units
+  const int4* seg;         // segments
+  const int32_t* nseg;     // device count of segments
+  const int32_t* topv;     // top nodes by body
+  const int32_t* top_off;  // [m + 1]
   const T* rec;
-  T* xs;        // Info-/Velocity-sets by slot [nodes * 6]
-  const T* in;  // up: bead planes; down: residues
-  T* out;       // up: residues; down: bead planes
+  T* xs;                   // Info-/Velocity-sets of segment roots and top nodes, by position
+  const T* in;             // up: bead planes; down: residues
+  T* out;                  // up: residues; down: bead planes
 };
 
 template <typename T> struct V4;
@@ -82,22 +85,6 @@ template <typename T>
 __device__ __forceinline__ void store6(T* __restrict__ p, const T* v) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) p[i] = v[i];
-}
-
-template <typename T>
-__device__ __forceinline__ void load_bead(const ApplyArgs<T>& a, int32_t code, T* t) {
-  const int32_t i = a.perm[leaf_pos(code)];
-  t[0] = a.in[i];
-  t[1] = a.in[a.N + i];
-  t[2] = a.in[2 * a.N + i];
-}
-
-template <typename T>
-__device__ __forceinline__ void store_bead(const ApplyArgs<T>& a, int32_t code, const T* L) {
-  const int32_t i = a.perm[leaf_pos(code)];
-  a.out[i] = L[0];
-  a.out[a.N + i] = L[1];
-  a.out[2 * a.N + i] = L[2];
 }
 
 __device__ __forceinline__ bool sign_set(float x) { return __float_as_int(x) < 0; }
@@ -229,150 +216,255 @@ __device__ __forceinline__ void down_node(const T* __restrict__ recp, const T* L
   }
 }
 
-template <typename T, int TYPE>
-__device__ __forceinline__ void up_slot(const ApplyArgs<T>& a, int64_t s, int64_t rw) {
-  const int2 cc = a.sc[s];
-  T X[6], Y[6], P[6];
-  if (is_leaf(cc.x)) load_bead(a, cc.x, X); else load6(a.xs + (int64_t)cc.x * 6, X);
-  if (is_leaf(cc.y)) load_bead(a, cc.y, Y); else load6(a.xs + (int64_t)cc.y * 6, Y);
-  up_node<T, TYPE>(a.rec + rw, X, Y, cc.x >= 0, P, a.out + a.sroff[s]);
-  store6(a.xs + s * 6, P);
-}
 
-template <typename T, int TYPE>
-__device__ __forceinline__ void down_slot(const ApplyArgs<T>& a, int64_t s, int64_t rw, const T* Lp) {
-  const int2 cc = a.sc[s];
-  T Lx[6], Ly[6];
-  down_node<T, TYPE>(a.rec + rw, Lp, a.in + a.sroff[s], cc.x >= 0, Lx, Ly);
-  if (is_leaf(cc.x)) store_bead(a, cc.x, Lx); else store6(a.xs + (int64_t)cc.x * 6, Lx);
-  if (is_leaf(cc.y)) store_bead(a, cc.y, Ly); else store6(a.xs + (int64_t)cc.y * 6, Ly);
-}
-
-// ------------------------------------------------------------- kernels
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_up_level(ApplyArgs<T> a, int h) {
-  const int b0 = 3 * (h - 1);
-  const int32_t s0 = a.bstart[b0], s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
-  const int32_t r0 = a.brec[b0], r1 = a.brec[b0 + 1], r2 = a.brec[b0 + 2];
-  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    if (s < s1) up_slot<T, 0>(a, s, r0 + (s - s0) * rec_words(0));
-    else if (s < s2) up_slot<T, 1>(a, s, r1 + (s - s1) * rec_words(1));
-    else up_slot<T, 2>(a, s, r2 + (s - s2) * rec_words(2));
+// ------------------------------------------------------------ helpers
+// Bring [p, p + bytes) into L2 (bulk prefetch, 16-byte granules; chunks of
+// at most 4 KB, one per thread of the first warp).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  const uint32_t chunks = (bytes + 4095u) / 4096u;
+  for (uint32_t c = threadIdx.x; c < chunks; c += 32) {
+    const uint32_t off = c * 4096u;
+    const uint32_t len = min(4096u, bytes - off);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char*>(p) + off),
+                 "r"(len)
+                 : "memory");
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_down_level(ApplyArgs<T> a, int h) {
-  const int b0 = 3 * (h - 1);
-  const int32_t s0 = a.bstart[b0], s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
-  const int32_t r0 = a.brec[b0], r1 = a.brec[b0 + 1], r2 = a.brec[b0 + 2];
-  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    T Lp[6];
-    load6(a.xs + s * 6, Lp);
-    if (s < s1) down_slot<T, 0>(a, s, r0 + (s - s0) * rec_words(0), Lp);
-    else if (s < s2) down_slot<T, 1>(a, s, r1 + (s - s1) * rec_words(1), Lp);
-    else down_slot<T, 2>(a, s, r2 + (s - s2) * rec_words(2), Lp);
+// Height boundaries of a segment: hb[h] = first local index of height h,
+// hb[H + 1] = nn (the heights 1..H of a subtree are all present).  Returns H.
+__device__ __forceinline__ int seg_heights(const uint8_t* __restrict__ ph, int32_t p0, int32_t nn, int32_t* hb) {
+  for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int h = ph[p0 + t];
+    const int hp = t > 0 ? ph[p0 + t - 1] : 0;
+    for (int x = hp + 1; x <= h; ++x) hb[x] = t;
+    if (t == nn - 1) hb[h + 1] = nn;
   }
-}
-
-template <typename T>
-__device__ __forceinline__ void tail_range(const ApplyArgs<T>& a, int32_t j, int32_t* lo, int32_t* hi) {
-  const int bt = 3 * a.cut;
-  id_range(a.sid, a.bstart[bt], a.bstart[bt + 1], a.off[j] - j, a.off[j + 1] - (j + 1), lo, hi);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_up_tail(ApplyArgs<T> a) {
-  const int32_t j = blockIdx.x;
-  int32_t lo, hi;
-  tail_range(a, j, &lo, &hi);
-  if (lo == hi) return;
-  const int bt = 3 * a.cut;
-  const int32_t t0 = a.bstart[bt], rt = a.brec[bt];
-  const int H = a.sheight[a.root_slot[j]];
-  for (int h = a.cut + 1; h <= H; ++h) {
-    for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
-      if (a.sheight[s] != h) continue;
-      const int2 cc = a.sc[s];
-      const int64_t rw = rt + (int64_t)(s - t0) * kRecMax;
-      const int type = (cc.x >= 0) + (cc.y >= 0);
-      if (type == 0) up_slot<T, 0>(a, s, rw);
-      else if (type == 1) up_slot<T, 1>(a, s, rw);
-      else up_slot<T, 2>(a, s, rw);
-    }
-    __syncthreads();
-  }
-}
-
-// Runs before the levels: zero root Velocity-set for every body (Q~^T
-// only), then the nodes above the cut from the root down.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_down_tail(ApplyArgs<T> a) {
-  const int32_t j = blockIdx.x;
-  const int32_t rs = a.root_slot[j];
-  if (threadIdx.x < 6) a.xs[(int64_t)rs * 6 + threadIdx.x] = T(0);
   __syncthreads();
-  int32_t lo, hi;
-  tail_range(a, j, &lo, &hi);
-  if (lo == hi) return;
-  const int bt = 3 * a.cut;
-  const int32_t t0 = a.bstart[bt], rt = a.brec[bt];
-  const int H = a.sheight[rs];
-  for (int h = H; h > a.cut; --h) {
-    for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
-      if (a.sheight[s] != h) continue;
-      const int2 cc = a.sc[s];
-      const int64_t rw = rt + (int64_t)(s - t0) * kRecMax;
-      T Lp[6];
-      load6(a.xs + (int64_t)s * 6, Lp);
-      const int type = (cc.x >= 0) + (cc.y >= 0);
-      if (type == 0) down_slot<T, 0>(a, s, rw, Lp);
-      else if (type == 1) down_slot<T, 1>(a, s, rw, Lp);
-      else down_slot<T, 2>(a, s, rw, Lp);
+  return ph[p0 + nn - 1];
+}
+
+template <typename T>
+__device__ __forceinline__ int rec_type(int2 cc) { return (cc.x >= 0) + (cc.y >= 0); }
+
+// ------------------------------------------------------------ upward
+template <typename T>
+__device__ __forceinline__ void up_dispatch(const SweepArgs<T>& a, int64_t p, int2 cc, const T* X, const T* Y,
+                                            T* P) {
+  const T* r = a.rec + 4 * (int64_t)a.prw[p];
+  T* res = a.out + a.proff[p];
+  const int type = rec_type<T>(cc);
+  if (type == 0) up_node<T, 0>(r, X, Y, false, P, res);
+  else if (type == 1) up_node<T, 1>(r, X, Y, cc.x >= 0, P, res);
+  else up_node<T, 2>(r, X, Y, true, P, res);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
+  __shared__ T info[(kSegMax - 1) * 6];
+  __shared__ T bead[kSegMax * 3];
+  __shared__ int32_t hb[kMaxHeight + 2];
+  const int ns = *a.nseg;
+  for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+    const int4 sg = a.seg[i];
+    const int32_t p0 = sg.x, nn = sg.y, f = sg.z;
+    if (threadIdx.x < 32) {
+      const uint32_t w0 = a.prw[p0], w1 = a.prw[p0 + nn];
+      prefetch_l2(a.rec + 4 * (int64_t)w0, (w1 - w0) * 4u * (uint32_t)sizeof(T));
+    }
+    for (int32_t t = threadIdx.x; t <= nn; t += blockDim.x) {
+      const int32_t b = a.perm[f + t];
+      bead[3 * t] = a.in[b];
+      bead[3 * t + 1] = a.in[a.N + b];
+      bead[3 * t + 2] = a.in[2 * a.N + b];
+    }
+    const int H = seg_heights(a.ph, p0, nn, hb);
+    for (int h = 1; h <= H; ++h) {
+      for (int32_t t = hb[h] + threadIdx.x; t < hb[h + 1]; t += blockDim.x) {
+        const int64_t p = p0 + t;
+        const int2 cc = a.pc[p];
+        const T* X = cc.x >= 0 ? info + 6 * (cc.x - p0) : bead + 3 * (leaf_pos(cc.x) - f);
+        const T* Y = cc.y >= 0 ? info + 6 * (cc.y - p0) : bead + 3 * (leaf_pos(cc.y) - f);
+        T P[6];
+        up_dispatch(a, p, cc, X, Y, P);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) info[6 * t + k] = P[k];
+      }
+      __syncthreads();
+    }
+    if (!sg.w && threadIdx.x < 6) a.xs[6 * (int64_t)(p0 + nn - 1) + threadIdx.x] = info[6 * (nn - 1) + threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// Height range of body j's top nodes into lim[0..1]; returns false if none.
+__device__ __forceinline__ bool top_range(const int32_t* __restrict__ topv, const uint8_t* __restrict__ ph,
+                                          int32_t t0, int32_t t1, int* lim) {
+  if (t0 == t1) return false;
+  if (threadIdx.x == 0) {
+    lim[0] = kMaxHeight;
+    lim[1] = 0;
+  }
+  __syncthreads();
+  for (int32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const int h = ph[topv[t]];
+    atomicMin(&lim[0], h);
+    atomicMax(&lim[1], h);
+  }
+  __syncthreads();
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_bead(const SweepArgs<T>& a, int32_t code, T* v) {
+  const int32_t b = a.perm[leaf_pos(code)];
+  v[0] = a.in[b];
+  v[1] = a.in[a.N + b];
+  v[2] = a.in[2 * a.N + b];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
+  __shared__ int lim[2];
+  const int32_t j = blockIdx.x;
+  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
+  for (int h = lim[0]; h <= lim[1]; ++h) {
+    for (int32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+      const int32_t p = a.topv[t];
+      if (a.ph[p] != h) continue;
+      const int2 cc = a.pc[p];
+      T X[6], Y[6], P[6];
+      if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X);
+      if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y);
+      up_dispatch(a, p, cc, X, Y, P);
+      store6(a.xs + 6 * (int64_t)p, P);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------- downward
+template <typename T>
+__device__ __forceinline__ void down_dispatch(const SweepArgs<T>& a, int64_t p, int2 cc, const T* Lp, T* Lx,
+                                              T* Ly) {
+  const T* r = a.rec + 4 * (int64_t)a.prw[p];
+  const T* w = a.in + a.proff[p];
+  const int type = rec_type<T>(cc);
+  if (type == 0) down_node<T, 0>(r, Lp, w, false, Lx, Ly);
+  else if (type == 1) down_node<T, 1>(r, Lp, w, cc.x >= 0, Lx, Ly);
+  else down_node<T, 2>(r, Lp, w, true, Lx, Ly);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_bead(const SweepArgs<T>& a, int32_t code, const T* L) {
+  const int32_t b = a.perm[leaf_pos(code)];
+  a.out[b] = L[0];
+  a.out[a.N + b] = L[1];
+  a.out[2 * a.N + b] = L[2];
+}
+
+// Runs first: for every body with top nodes, the root Velocity-set is 0,
+// then the top nodes from the root down.
+template <typename T>
+__global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
+  __shared__ int lim[2];
+  const int32_t j = blockIdx.x;
+  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
+  for (int h = lim[1]; h >= lim[0]; --h) {
+    for (int32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+      const int32_t p = a.topv[t];
+      if (a.ph[p] != h) continue;
+      const int2 cc = a.pc[p];
+      T Lp[6], Lx[6], Ly[6];
+      if (h == lim[1]) {  // the body root
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Lp[k] = T(0);
+      } else {
+        load6(a.xs + 6 * (int64_t)p, Lp);
+      }
+      down_dispatch(a, p, cc, Lp, Lx, Ly);
+      if (cc.x >= 0) store6(a.xs + 6 * (int64_t)cc.x, Lx); else store_bead(a, cc.x, Lx);
+      if (cc.y >= 0) store6(a.xs + 6 * (int64_t)cc.y, Ly); else store_bead(a, cc.y, Ly);
     }
     __syncthreads();
   }
 }
 
 template <typename T>
-ApplyArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
-  ApplyArgs<T> a;
-  a.N = c.N; a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.sroff = c.sroff; a.sheight = c.sheight;
-  a.sid = c.sid; a.bstart = c.bstart; a.brec = c.brec; a.root_slot = c.root_slot; a.cut = c.cut;
+__global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
+  __shared__ T info[(kSegMax - 1) * 6];
+  __shared__ int32_t hb[kMaxHeight + 2];
+  const int ns = *a.nseg;
+  for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+    const int4 sg = a.seg[i];
+    const int32_t p0 = sg.x, nn = sg.y;
+    if (threadIdx.x < 32) {
+      const uint32_t w0 = a.prw[p0], w1 = a.prw[p0 + nn];
+      prefetch_l2(a.rec + 4 * (int64_t)w0, (w1 - w0) * 4u * (uint32_t)sizeof(T));
+    }
+    if (threadIdx.x < 6)
+      info[6 * (nn - 1) + threadIdx.x] = sg.w ? T(0) : a.xs[6 * (int64_t)(p0 + nn - 1) + threadIdx.x];
+    const int H = seg_heights(a.ph, p0, nn, hb);
+    for (int h = H; h >= 1; --h) {
+      for (int32_t t = hb[h] + threadIdx.x; t < hb[h + 1]; t += blockDim.x) {
+        const int64_t p = p0 + t;
+        const int2 cc = a.pc[p];
+        T Lp[6], Lx[6], Ly[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Lp[k] = info[6 * t + k];
+        down_dispatch(a, p, cc, Lp, Lx, Ly);
+        if (cc.x >= 0) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) info[6 * (cc.x - p0) + k] = Lx[k];
+        } else {
+          store_bead(a, cc.x, Lx);
+        }
+        if (cc.y >= 0) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) info[6 * (cc.y - p0) + k] = Ly[k];
+        } else {
+          store_bead(a, cc.y, Ly);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
+  SweepArgs<T> a;
+  a.N = c.N; a.perm = c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
+  a.prw = reinterpret_cast<const uint32_t*>(c.prw);
+  a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;
   return a;
 }
 
 template <typename T>
 zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out) {
-  ApplyArgs<T> a = make_args<T>(c, rec, xs, v, out);
-  const int grid = c.num_sms * 8;
-  for (int h = 1; h <= c.cut; ++h) {
-    time_begin(c, "up_level");
-    k_up_level<T><<<grid, kThreads, 0, c.stream>>>(a, h);
-    time_end(c, "up_level");
-  }
-  time_begin(c, "up_tail");
-  k_up_tail<T><<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
-  time_end(c, "up_tail");
+  SweepArgs<T> a = make_args<T>(c, rec, xs, v, out);
+  time_begin(c, "up_seg");
+  k_up_seg<T><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
+  time_end(c, "up_seg");
+  time_begin(c, "up_top");
+  k_up_top<T><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  time_end(c, "up_top");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }
 
 template <typename T>
 zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out) {
-  ApplyArgs<T> a = make_args<T>(c, rec, xs, w, out);
-  time_begin(c, "down_tail");
-  k_down_tail<T><<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
-  time_end(c, "down_tail");
-  const int grid = c.num_sms * 8;
-  for (int h = c.cut; h >= 1; --h) {
-    time_begin(c, "down_level");
-    k_down_level<T><<<grid, kThreads, 0, c.stream>>>(a, h);
-    time_end(c, "down_level");
-  }
+  SweepArgs<T> a = make_args<T>(c, rec, xs, w, out);
+  time_begin(c, "down_top");
+  k_down_top<T><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  time_end(c, "down_top");
+  time_begin(c, "down_seg");
+  k_down_seg<T><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
+  time_end(c, "down_seg");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }

@@ -59,7 +59,7 @@ struct BuildArgs {
   const uint8_t* sheight;
   const int32_t* sid;
   const int32_t* bstart;
-  const int32_t* brec;
+  const int32_t* srw;   // record offset of each slot, 4-word units (uint32)
   const int32_t* root_slot;
   const double* ctab;   // sqrt(n) [0, kCountTab), 1/sqrt(n) [kCountTab, 2 kCountTab)
   const float2* ctab2;  // the same as double-single pairs
@@ -416,12 +416,12 @@ template <class R>
 __global__ void __launch_bounds__(kThreads) k_build_level(BuildArgs a, int h) {
   const int b0 = 3 * (h - 1);
   const int32_t s0 = a.bstart[b0], s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
-  const int32_t r0 = a.brec[b0], r1 = a.brec[b0 + 1], r2 = a.brec[b0 + 2];
   for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
        s += (int64_t)gridDim.x * blockDim.x) {
-    if (s < s1) build_slot<R>(a, s, 0, r0 + (s - s0) * rec_words(0));
-    else if (s < s2) build_slot<R>(a, s, 1, r1 + (s - s1) * rec_words(1));
-    else build_slot<R>(a, s, 2, r2 + (s - s2) * rec_words(2));
+    const int64_t rw = 4 * (int64_t)(uint32_t)a.srw[s];
+    if (s < s1) build_slot<R>(a, s, 0, rw);
+    else if (s < s2) build_slot<R>(a, s, 1, rw);
+    else build_slot<R>(a, s, 2, rw);
   }
 }
 
@@ -435,12 +435,11 @@ __global__ void __launch_bounds__(kThreads) k_build_tail(BuildArgs a) {
   id_range(a.sid, t0, t1, a.off[j] - j, a.off[j + 1] - (j + 1), &lo, &hi);
   if (lo == hi) return;
   const int H = a.sheight[a.root_slot[j]];
-  const int32_t rt = a.brec[bt];
   for (int h = a.cut + 1; h <= H; ++h) {
     for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
       if (a.sheight[s] != h) continue;
       const int2 cc = a.sc[s];
-      build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), rt + (int64_t)(s - t0) * kRecMax);
+      build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
     }
     __syncthreads();
   }
@@ -482,7 +481,7 @@ zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z
   BuildArgs a;
   a.x = x; a.y = y; a.z = z;
   a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.scnt = c.scnt; a.sheight = c.sheight; a.sid = c.sid;
-  a.bstart = c.bstart; a.brec = c.brec; a.root_slot = c.root_slot; a.cut = c.cut;
+  a.bstart = c.bstart; a.srw = c.srw; a.root_slot = c.root_slot; a.cut = c.cut;
   a.ctab = c.count_tab;
   a.ctab2 = c.count_tab2;
   a.st = c.st64;

@@ -23,6 +23,14 @@ constexpr int kDefaultCut = 15;
 constexpr int kMaxCut = 21;           // 3 * 21 + 1 = 64 buckets
 constexpr int kMaxBuckets = 3 * kMaxCut + 1;
 
+// Sweeps work on segments: the maximal subtrees of at most kSegMax beads.
+// The nodes of a segment keep the node-id range of its subtree (a subtree's
+// split positions are contiguous) but are reordered inside it by height,
+// so one thread block can sweep the segment height by height in shared
+// memory.  Nodes above all segments ("top" nodes, more than kSegMax beads)
+// keep position = node id and are swept one thread block per body.
+constexpr int kSegMax = 512;
+
 // Node records (float or double words), compact and type-specific.  With
 // A = M^T (k x 3) built from [T22_x | T22_y | K], K = sqrt(n_x n_y/n)[d]x,
 // the Householder vectors of the LQ have structural zeros; only the
@@ -34,8 +42,9 @@ constexpr int kMaxBuckets = 3 * kMaxCut + 1;
 //   type 2 (k = 9: rows 0-2 T22_x, 3-5 T22_y, 6-8 K), 20 words:
 //     [0] alpha [1] beta [2..4] tau [5..7] v1(3,7,8) [8..12] v2(3,4,6,7,8)
 //     [13..18] v3(3..8)
-// (v_j(j) = 1 implicit.)  Records of a (height, type) bucket are contiguous;
-// tail records use 20-word slots.
+// (v_j(j) = 1 implicit.)  Records are stored compactly in position order
+// (segments, heights inside segments); prw[p] is the record offset of
+// position p in units of 4 words (all record sizes are multiples of 4).
 __host__ __device__ constexpr int rec_words(int type) { return type == 0 ? 12 : (type == 1 ? 16 : 20); }
 constexpr int kRecMax = 20;
 // Dense export layout (zq_get_records): 28 doubles per node.
@@ -107,11 +116,28 @@ struct Ctx {
   int32_t* brec = nullptr;       // [kMaxBuckets + 1] first record word of each bucket
   int32_t* bhist = nullptr;      // bucket-sort histograms
   int64_t bhist_cap = 0;
+  // segments (see kSegMax), by position p (node id order with each segment
+  // reordered by height)
+  int32_t* par = nullptr;        // [nodes] parent node id (-1: body root)
+  int32_t* pos_of = nullptr;     // [nodes] node id -> position
+  int32_t* pnode = nullptr;      // [nodes] position -> node id
+  int2* pc = nullptr;            // [nodes] child codes: >= 0 child position, < 0 leaf
+  int32_t* proff = nullptr;      // [nodes] residue offset
+  uint8_t* ph = nullptr;         // [nodes] height
+  int32_t* prw = nullptr;        // [nodes + 1] record offset (4-word units, read as uint32)
+  int32_t* seg_flag = nullptr;   // [nodes] scan workspace: segment roots, then top nodes
+  int4* seg = nullptr;           // [nodes] per segment: first position, nodes, first sorted
+                                 // bead, 1 if its root is a body root (first nseg used)
+  int32_t* topv = nullptr;       // [nodes] top nodes (= positions), grouped by body
+  int32_t* top_off = nullptr;    // [m + 1] first top node of each body in topv
+  int32_t* nseg = nullptr;       // [2] device counts: segments, top nodes
+  int32_t* srw = nullptr;        // [nodes] record offset of each build slot (4-word units)
   // transforms, by slot
   double* st64 = nullptr;        // [nodes * kState]
-  double* rec64 = nullptr;       // [nodes * kRecMax] compact records
+  double* rec64 = nullptr;       // [nodes * kRecMax] compact records, by position
   float* rec32 = nullptr;        // [nodes * kRecMax]
-  // sweep scratch: Info-sets / Velocity-sets by slot
+  // sweep scratch: Info-sets / Velocity-sets of segment roots and top nodes,
+  // by position
   double* x64 = nullptr;         // [nodes * 6]
   float* x32 = nullptr;          // [nodes * 6]
   // staging for host-buffer calls (bytes)
@@ -187,6 +213,12 @@ __device__ inline double ord_decode(unsigned long long u) {
   return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
 }
 
+#define ZQ_TRY_STATUS(expr)                       \
+  do {                                            \
+    zq_status _st = (expr);                       \
+    if (_st != ZQ_OK) return _st;                 \
+  } while (0)
+
 #define ZQ_CUDA_TRY(expr)                         \
   do {                                            \
     cudaError_t _e = (expr);                      \
@@ -209,6 +241,8 @@ zq_status launch_sort(Ctx& c);
 zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
                                 int32_t* total);
 int64_t scan_tmp_words(int64_t n);
+// zq_seg.cu
+zq_status launch_segments(Ctx& c);
 // zq_build.cu
 // which: bit 0 = FP64 records, bit 1 = FP32 records
 zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which);

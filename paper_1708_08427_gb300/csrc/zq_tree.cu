@@ -317,8 +317,10 @@ __global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
                             const int32_t* __restrict__ slot_of, const int32_t* __restrict__ cl,
                             const int32_t* __restrict__ cr, const int32_t* __restrict__ roff,
                             const int32_t* __restrict__ cnt, const uint8_t* __restrict__ height,
+                            const int32_t* __restrict__ pos_of, const int32_t* __restrict__ prw,
                             int2* __restrict__ sc, int32_t* __restrict__ sroff,
-                            int32_t* __restrict__ scnt, uint8_t* __restrict__ sheight) {
+                            int32_t* __restrict__ scnt, uint8_t* __restrict__ sheight,
+                            int32_t* __restrict__ srw) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nodes) return;
   const int32_t q = sid[s];
@@ -327,6 +329,7 @@ __global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
   sroff[s] = roff[q];
   scnt[s] = cnt[q];
   sheight[s] = height[q];
+  srw[s] = prw[pos_of[q]];
 }
 
 __global__ void k_root_slots(int64_t m, const int32_t* __restrict__ root,
@@ -396,7 +399,9 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   }
   st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
   if (st != ZQ_OK) return st;
-  // schedule
+  st = launch_segments(c);
+  if (st != ZQ_OK) return st;
+  // schedule of the build
   const int nb = 3 * c.cut + 1;
   const int64_t nblk = (c.nodes + kBTile - 1) / kBTile;
   int32_t* hist = c.bhist;
@@ -417,7 +422,8 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   time_end(c, "schedule");
   time_begin(c, "schedule");
   k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.roff, c.cnt,
-                                                   c.height, c.sc, c.sroff, c.scnt, c.sheight);
+                                                   c.height, c.pos_of, c.prw, c.sc, c.sroff, c.scnt,
+                                                   c.sheight, c.srw);
   time_end(c, "schedule");
   time_begin(c, "schedule");
   k_root_slots<<<blocks(c.m), kThreads, 0, s>>>(c.m, c.root, c.slot_of, c.root_slot);
