@@ -233,15 +233,34 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
 
 // Height boundaries of a segment: hb[h] = first local index of height h,
 // hb[H + 1] = nn (the heights 1..H of a subtree are all present).  Returns H.
-__device__ __forceinline__ int seg_heights(const uint8_t* __restrict__ ph, int32_t p0, int32_t nn, int32_t* hb) {
+// Stages the segment's per-node data (children, record offset, residue
+// offset, height) into shared memory in one coalesced pass, then the
+// height boundaries.
+struct SegMeta {
+  int2 pc[kSegMax - 1];
+  uint32_t rw[kSegMax - 1];
+  int32_t ro[kSegMax - 1];
+  uint8_t h[kSegMax - 1];
+  int32_t hb[kMaxHeight + 2];
+};
+
+template <typename T>
+__device__ __forceinline__ int stage_meta(const SweepArgs<T>& a, int32_t p0, int32_t nn, SegMeta& M) {
   for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
-    const int h = ph[p0 + t];
-    const int hp = t > 0 ? ph[p0 + t - 1] : 0;
-    for (int x = hp + 1; x <= h; ++x) hb[x] = t;
-    if (t == nn - 1) hb[h + 1] = nn;
+    M.pc[t] = a.pc[p0 + t];
+    M.rw[t] = a.prw[p0 + t];
+    M.ro[t] = a.proff[p0 + t];
+    M.h[t] = a.ph[p0 + t];
   }
   __syncthreads();
-  return ph[p0 + nn - 1];
+  for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int h = M.h[t];
+    const int hp = t > 0 ? M.h[t - 1] : 0;
+    for (int x = hp + 1; x <= h; ++x) M.hb[x] = t;
+    if (t == nn - 1) M.hb[h + 1] = nn;
+  }
+  __syncthreads();
+  return M.h[nn - 1];
 }
 
 template <typename T>
@@ -249,10 +268,10 @@ __device__ __forceinline__ int rec_type(int2 cc) { return (cc.x >= 0) + (cc.y >=
 
 // ------------------------------------------------------------ upward
 template <typename T>
-__device__ __forceinline__ void up_dispatch(const SweepArgs<T>& a, int64_t p, int2 cc, const T* X, const T* Y,
-                                            T* P) {
-  const T* r = a.rec + 4 * (int64_t)a.prw[p];
-  T* res = a.out + a.proff[p];
+__device__ __forceinline__ void up_dispatch(const SweepArgs<T>& a, uint32_t rw, int32_t ro, int2 cc, const T* X,
+                                            const T* Y, T* P) {
+  const T* r = a.rec + 4 * (int64_t)rw;
+  T* res = a.out + ro;
   const int type = rec_type<T>(cc);
   if (type == 0) up_node<T, 0>(r, X, Y, false, P, res);
   else if (type == 1) up_node<T, 1>(r, X, Y, cc.x >= 0, P, res);
@@ -263,7 +282,7 @@ template <typename T>
 __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
   __shared__ T info[(kSegMax - 1) * 6];
   __shared__ T bead[kSegMax * 3];
-  __shared__ int32_t hb[kMaxHeight + 2];
+  __shared__ SegMeta M;
   const int ns = *a.nseg;
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
     const int4 sg = a.seg[i];
@@ -278,15 +297,14 @@ __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
       bead[3 * t + 1] = a.in[a.N + b];
       bead[3 * t + 2] = a.in[2 * a.N + b];
     }
-    const int H = seg_heights(a.ph, p0, nn, hb);
+    const int H = stage_meta(a, p0, nn, M);
     for (int h = 1; h <= H; ++h) {
-      for (int32_t t = hb[h] + threadIdx.x; t < hb[h + 1]; t += blockDim.x) {
-        const int64_t p = p0 + t;
-        const int2 cc = a.pc[p];
+      for (int32_t t = M.hb[h] + threadIdx.x; t < M.hb[h + 1]; t += blockDim.x) {
+        const int2 cc = M.pc[t];
         const T* X = cc.x >= 0 ? info + 6 * (cc.x - p0) : bead + 3 * (leaf_pos(cc.x) - f);
         const T* Y = cc.y >= 0 ? info + 6 * (cc.y - p0) : bead + 3 * (leaf_pos(cc.y) - f);
         T P[6];
-        up_dispatch(a, p, cc, X, Y, P);
+        up_dispatch(a, M.rw[t], M.ro[t], cc, X, Y, P);
 #pragma unroll
         for (int k = 0; k < 6; ++k) info[6 * t + k] = P[k];
       }
@@ -337,7 +355,7 @@ __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
       T X[6], Y[6], P[6];
       if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X);
       if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y);
-      up_dispatch(a, p, cc, X, Y, P);
+      up_dispatch(a, a.prw[p], a.proff[p], cc, X, Y, P);
       store6(a.xs + 6 * (int64_t)p, P);
     }
     __syncthreads();
@@ -346,10 +364,10 @@ __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
 
 // ---------------------------------------------------------- downward
 template <typename T>
-__device__ __forceinline__ void down_dispatch(const SweepArgs<T>& a, int64_t p, int2 cc, const T* Lp, T* Lx,
-                                              T* Ly) {
-  const T* r = a.rec + 4 * (int64_t)a.prw[p];
-  const T* w = a.in + a.proff[p];
+__device__ __forceinline__ void down_dispatch(const SweepArgs<T>& a, uint32_t rw, int32_t ro, int2 cc,
+                                              const T* Lp, T* Lx, T* Ly) {
+  const T* r = a.rec + 4 * (int64_t)rw;
+  const T* w = a.in + ro;
   const int type = rec_type<T>(cc);
   if (type == 0) down_node<T, 0>(r, Lp, w, false, Lx, Ly);
   else if (type == 1) down_node<T, 1>(r, Lp, w, cc.x >= 0, Lx, Ly);
@@ -384,7 +402,7 @@ __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
       } else {
         load6(a.xs + 6 * (int64_t)p, Lp);
       }
-      down_dispatch(a, p, cc, Lp, Lx, Ly);
+      down_dispatch(a, a.prw[p], a.proff[p], cc, Lp, Lx, Ly);
       if (cc.x >= 0) store6(a.xs + 6 * (int64_t)cc.x, Lx); else store_bead(a, cc.x, Lx);
       if (cc.y >= 0) store6(a.xs + 6 * (int64_t)cc.y, Ly); else store_bead(a, cc.y, Ly);
     }
@@ -395,7 +413,7 @@ __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
   __shared__ T info[(kSegMax - 1) * 6];
-  __shared__ int32_t hb[kMaxHeight + 2];
+  __shared__ SegMeta M;
   const int ns = *a.nseg;
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
     const int4 sg = a.seg[i];
@@ -406,15 +424,14 @@ __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
     }
     if (threadIdx.x < 6)
       info[6 * (nn - 1) + threadIdx.x] = sg.w ? T(0) : a.xs[6 * (int64_t)(p0 + nn - 1) + threadIdx.x];
-    const int H = seg_heights(a.ph, p0, nn, hb);
+    const int H = stage_meta(a, p0, nn, M);
     for (int h = H; h >= 1; --h) {
-      for (int32_t t = hb[h] + threadIdx.x; t < hb[h + 1]; t += blockDim.x) {
-        const int64_t p = p0 + t;
-        const int2 cc = a.pc[p];
+      for (int32_t t = M.hb[h] + threadIdx.x; t < M.hb[h + 1]; t += blockDim.x) {
+        const int2 cc = M.pc[t];
         T Lp[6], Lx[6], Ly[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) Lp[k] = info[6 * t + k];
-        down_dispatch(a, p, cc, Lp, Lx, Ly);
+        down_dispatch(a, M.rw[t], M.ro[t], cc, Lp, Lx, Ly);
         if (cc.x >= 0) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) info[6 * (cc.x - p0) + k] = Lx[k];
