@@ -74,7 +74,9 @@ typedef enum {
                            orthonormal but Q~ may miss a direction */
 } zq_status;
 
-typedef enum { ZQ_FP64 = 0, ZQ_FP32 = 1 } zq_prec;
+/* Arithmetic and storage of an apply.  ZQ_BF16: bfloat16 vectors with
+ * FP32 arithmetic and the FP32 transforms (block form only). */
+typedef enum { ZQ_FP64 = 0, ZQ_FP32 = 1, ZQ_BF16 = 2 } zq_prec;
 
 /* Human-readable name of a status code (static storage). */
 const char *zq_status_string(zq_status s);
@@ -125,6 +127,26 @@ zq_status zq_apply_Q(zq_ctx *ctx, zq_prec prec, int64_t k, const void *v, int64_
  * allocate. */
 zq_status zq_apply_QT(zq_ctx *ctx, zq_prec prec, int64_t k, const void *w, int64_t ldw,
                       void *out, int64_t ldo);
+
+/* ------------------------------------------------------------------------
+ * Block form: k right-hand sides at once (the same node transforms applied
+ * to k-column blocks; Algorithms 2 and 3 column by column).
+ *
+ * Layout: rows of k contiguous values.  Bead vectors V[(a*N + i)*k + c]
+ * (axis a of bead i, caller's bead order, column c); residue vectors
+ * out[r*k + c] (r in the residue order above).  DEVICE memory.
+ * prec: ZQ_FP32 (float), ZQ_BF16 (__nv_bfloat16 storage, FP32 arithmetic
+ * and FP32 transforms; inputs and outputs rounded to bfloat16), ZQ_FP64
+ * (double).  The transforms of the matching precision must have been built
+ * (zq_build_transforms builds both), else ZQ_ESTATE.
+ *
+ * zq_reserve_block allocates the context's block scratch for up to k_max
+ * columns (6 values per node and column, 4 or 8 bytes each) and must precede
+ * the block applies; they never allocate and return ZQ_ESTATE when k exceeds
+ * the reservation or the tree changed size since.  1 <= k. */
+zq_status zq_reserve_block(zq_ctx *ctx, zq_prec prec, int64_t k_max);
+zq_status zq_apply_Q_block(zq_ctx *ctx, zq_prec prec, int64_t k, const void *V, void *out);
+zq_status zq_apply_QT_block(zq_ctx *ctx, zq_prec prec, int64_t k, const void *W, void *out);
 
 /* One step of the whole path for m bodies: the tree (Sec. 2.1), the FP64
  * node transforms (Sec. 3), then qv = Q~ v and qtw = Q~^T w (Algorithms 2

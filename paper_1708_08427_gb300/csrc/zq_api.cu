@@ -31,7 +31,7 @@ void free_all(Ctx& c) {
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
                 c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.stage,
                 c.par, c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.topv,
-                c.top_off, c.nseg, c.srw};
+                c.top_off, c.nseg, c.srw, c.xblk};
   for (void* p : ps)
     if (p) cudaFree(p);
   Ctx fresh;
@@ -262,6 +262,46 @@ zq_status zq_apply_Q(zq_ctx* ctx, zq_prec prec, int64_t k, const void* v, int64_
     ZQ_TRY(zq::launch_apply_Q(c, prec, vi, ldv, oi));
   }
   return ZQ_OK;
+}
+
+zq_status zq_reserve_block(zq_ctx* ctx, zq_prec prec, int64_t k_max) {
+  if (!ctx || k_max < 1) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64 && prec != ZQ_BF16) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_tree) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  const int64_t es = prec == ZQ_FP64 ? 8 : 4;
+  const int64_t bytes = c.nodes * 6 * k_max * es;
+  if (bytes > c.xblk_bytes) {
+    if (c.xblk) cudaFree(c.xblk);
+    c.xblk = nullptr;
+    c.xblk_bytes = 0;
+    if (cudaMalloc(&c.xblk, (size_t)bytes) != cudaSuccess) {
+      c.xblk = nullptr;
+      return ZQ_ENOMEM;
+    }
+    c.xblk_bytes = bytes;
+  }
+  return ZQ_OK;
+}
+
+static zq_status apply_block(zq_ctx* ctx, bool up, zq_prec prec, int64_t k, const void* in, void* out) {
+  if (!ctx || !in || !out || k < 1 || k > (1 << 20)) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64 && prec != ZQ_BF16) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  c.time_started = false;
+  if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
+  const int64_t es = prec == ZQ_FP64 ? 8 : 4;
+  if (c.nodes * 6 * k * es > c.xblk_bytes) return ZQ_ESTATE;
+  return zq::launch_apply_block(c, up, prec, k, in, out);
+}
+
+zq_status zq_apply_Q_block(zq_ctx* ctx, zq_prec prec, int64_t k, const void* V, void* out) {
+  return apply_block(ctx, true, prec, k, V, out);
+}
+
+zq_status zq_apply_QT_block(zq_ctx* ctx, zq_prec prec, int64_t k, const void* W, void* out) {
+  return apply_block(ctx, false, prec, k, W, out);
 }
 
 zq_status zq_apply_QT(zq_ctx* ctx, zq_prec prec, int64_t k, const void* w, int64_t ldw, void* out,

@@ -24,6 +24,8 @@
 // Upward: segments, then top nodes; downward: top nodes, then segments.
 // The segment's records are prefetched into L2 in bulk when its block
 // starts.
+#include <cuda_bf16.h>
+
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -450,6 +452,228 @@ __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
   }
 }
 
+// ------------------------------------------------------ block form
+// k right-hand sides at once, rows of k contiguous values: bead planes
+// V[(a N + i) k + c], residues out[r k + c].  Storage TS (float, bfloat16,
+// double), arithmetic TC (float for float/bfloat16 with the FP32 records,
+// double with the FP64 records).  Thread (node, column) pairs cover each
+// height; every column of a node reads the same record (L1 broadcast).
+// Info-/Velocity-sets of all nodes live in the context's block scratch
+// xk[(position * 6 + e) k + c] (reserved by zq_reserve_block).
+template <typename TS, typename TC>
+struct BlockArgs {
+  int64_t N;
+  int32_t k;
+  const int32_t* perm;
+  const int2* pc;
+  const int32_t* proff;
+  const uint8_t* ph;
+  const uint32_t* prw;
+  const int4* seg;
+  const int32_t* nseg;
+  const int32_t* topv;
+  const int32_t* top_off;
+  const TC* rec;
+  TC* xk;
+  const TS* in;
+  TS* out;
+};
+
+__device__ __forceinline__ float to_c(float x) { return x; }
+__device__ __forceinline__ double to_c(double x) { return x; }
+__device__ __forceinline__ float to_c(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename TS> __device__ __forceinline__ TS from_c(float x);
+template <> __device__ __forceinline__ float from_c<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <typename TS> __device__ __forceinline__ TS from_c(double x);
+template <> __device__ __forceinline__ double from_c<double>(double x) { return x; }
+
+template <typename TS, typename TC>
+__device__ __forceinline__ void blk_child_up(const BlockArgs<TS, TC>& a, int32_t code, int32_t col, TC* X) {
+  if (code >= 0) {
+    const TC* p = a.xk + (int64_t)code * 6 * a.k + col;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) X[e] = p[(int64_t)e * a.k];
+  } else {
+    const int64_t b = a.perm[leaf_pos(code)];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) X[e] = to_c(a.in[((int64_t)e * a.N + b) * a.k + col]);
+  }
+}
+
+template <typename TS, typename TC>
+__device__ __forceinline__ void blk_up_one(const BlockArgs<TS, TC>& a, int64_t p, int2 cc, uint32_t rw, int32_t ro,
+                                           int32_t col) {
+  TC X[6], Y[6], P[6], res[6];
+  blk_child_up(a, cc.x, col, X);
+  blk_child_up(a, cc.y, col, Y);
+  const TC* r = a.rec + 4 * (int64_t)rw;
+  const int type = (cc.x >= 0) + (cc.y >= 0);
+  if (type == 0) up_node<TC, 0>(r, X, Y, false, P, res);
+  else if (type == 1) up_node<TC, 1>(r, X, Y, cc.x >= 0, P, res);
+  else up_node<TC, 2>(r, X, Y, true, P, res);
+  for (int e = 0; e < 3 * type; ++e) a.out[((int64_t)ro + e) * a.k + col] = from_c<TS>(res[e]);
+  TC* q = a.xk + p * 6 * a.k + col;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) q[(int64_t)e * a.k] = P[e];
+}
+
+template <typename TS, typename TC>
+__device__ __forceinline__ void blk_down_one(const BlockArgs<TS, TC>& a, int64_t p, int2 cc, uint32_t rw, int32_t ro,
+                                             int32_t col, bool zero) {
+  TC Lp[6], Lx[6], Ly[6], w[6];
+  const TC* q = a.xk + p * 6 * a.k + col;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) Lp[e] = zero ? TC(0) : q[(int64_t)e * a.k];
+  const int type = (cc.x >= 0) + (cc.y >= 0);
+  for (int e = 0; e < 3 * type; ++e) w[e] = to_c(a.in[((int64_t)ro + e) * a.k + col]);
+  const TC* r = a.rec + 4 * (int64_t)rw;
+  if (type == 0) down_node<TC, 0>(r, Lp, w, false, Lx, Ly);
+  else if (type == 1) down_node<TC, 1>(r, Lp, w, cc.x >= 0, Lx, Ly);
+  else down_node<TC, 2>(r, Lp, w, true, Lx, Ly);
+  const int32_t ch[2] = {cc.x, cc.y};
+  const TC* L[2] = {Lx, Ly};
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2) {
+    if (ch[s2] >= 0) {
+      TC* d = a.xk + (int64_t)ch[s2] * 6 * a.k + col;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) d[(int64_t)e * a.k] = L[s2][e];
+    } else {
+      const int64_t b = a.perm[leaf_pos(ch[s2])];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) a.out[((int64_t)e * a.N + b) * a.k + col] = from_c<TS>(L[s2][e]);
+    }
+  }
+}
+
+template <typename TS, typename TC>
+__device__ __forceinline__ int stage_meta_blk(const BlockArgs<TS, TC>& a, int32_t p0, int32_t nn, SegMeta& M) {
+  for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+    M.pc[t] = a.pc[p0 + t];
+    M.rw[t] = a.prw[p0 + t];
+    M.ro[t] = a.proff[p0 + t];
+    M.h[t] = a.ph[p0 + t];
+  }
+  __syncthreads();
+  for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int h = M.h[t];
+    const int hp = t > 0 ? M.h[t - 1] : 0;
+    for (int x = hp + 1; x <= h; ++x) M.hb[x] = t;
+    if (t == nn - 1) M.hb[h + 1] = nn;
+  }
+  __syncthreads();
+  return M.h[nn - 1];
+}
+
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(256) k_up_seg_blk(BlockArgs<TS, TC> a) {
+  __shared__ SegMeta M;
+  const int ns = *a.nseg;
+  const int32_t k = a.k;
+  for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+    const int4 sg = a.seg[i];
+    const int32_t p0 = sg.x, nn = sg.y;
+    const int H = stage_meta_blk(a, p0, nn, M);
+    for (int h = 1; h <= H; ++h) {
+      const int32_t b0 = M.hb[h], nh = M.hb[h + 1] - b0;
+      for (int32_t idx = threadIdx.x; idx < nh * k; idx += blockDim.x) {
+        const int32_t t = b0 + idx / k, col = idx - (idx / k) * k;
+        blk_up_one(a, p0 + t, M.pc[t], M.rw[t], M.ro[t], col);
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(256) k_down_seg_blk(BlockArgs<TS, TC> a) {
+  __shared__ SegMeta M;
+  const int ns = *a.nseg;
+  const int32_t k = a.k;
+  for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+    const int4 sg = a.seg[i];
+    const int32_t p0 = sg.x, nn = sg.y;
+    const int H = stage_meta_blk(a, p0, nn, M);
+    for (int h = H; h >= 1; --h) {
+      const int32_t b0 = M.hb[h], nh = M.hb[h + 1] - b0;
+      for (int32_t idx = threadIdx.x; idx < nh * k; idx += blockDim.x) {
+        const int32_t t = b0 + idx / k, col = idx - (idx / k) * k;
+        blk_down_one(a, p0 + t, M.pc[t], M.rw[t], M.ro[t], col, h == H && sg.w);
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(kTopThreads) k_up_top_blk(BlockArgs<TS, TC> a) {
+  __shared__ int lim[2];
+  const int32_t j = blockIdx.x;
+  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
+  const int32_t k = a.k, nt = t1 - t0;
+  for (int h = lim[0]; h <= lim[1]; ++h) {
+    for (int32_t idx = threadIdx.x; idx < nt * k; idx += blockDim.x) {
+      const int32_t p = a.topv[t0 + idx / k], col = idx - (idx / k) * k;
+      if (a.ph[p] != h) continue;
+      blk_up_one(a, p, a.pc[p], a.prw[p], a.proff[p], col);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(kTopThreads) k_down_top_blk(BlockArgs<TS, TC> a) {
+  __shared__ int lim[2];
+  const int32_t j = blockIdx.x;
+  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
+  const int32_t k = a.k, nt = t1 - t0;
+  for (int h = lim[1]; h >= lim[0]; --h) {
+    for (int32_t idx = threadIdx.x; idx < nt * k; idx += blockDim.x) {
+      const int32_t p = a.topv[t0 + idx / k], col = idx - (idx / k) * k;
+      if (a.ph[p] != h) continue;
+      blk_down_one(a, p, a.pc[p], a.prw[p], a.proff[p], col, h == lim[1]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TS, typename TC>
+BlockArgs<TS, TC> make_block_args(const Ctx& c, int32_t k, const TC* rec, const TS* in, TS* out) {
+  BlockArgs<TS, TC> a;
+  a.N = c.N; a.k = k; a.perm = c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
+  a.prw = reinterpret_cast<const uint32_t*>(c.prw);
+  a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
+  a.rec = rec; a.xk = static_cast<TC*>(c.xblk); a.in = in; a.out = out;
+  return a;
+}
+
+template <typename TS, typename TC>
+zq_status run_block(Ctx& c, bool up, int32_t k, const TC* rec, const void* in, void* out) {
+  BlockArgs<TS, TC> a = make_block_args<TS, TC>(c, k, rec, static_cast<const TS*>(in), static_cast<TS*>(out));
+  if (up) {
+    time_begin(c, "up_seg_blk");
+    k_up_seg_blk<TS, TC><<<c.num_sms * 8, 256, 0, c.stream>>>(a);
+    time_end(c, "up_seg_blk");
+    time_begin(c, "up_top_blk");
+    k_up_top_blk<TS, TC><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+    time_end(c, "up_top_blk");
+  } else {
+    time_begin(c, "down_top_blk");
+    k_down_top_blk<TS, TC><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+    time_end(c, "down_top_blk");
+    time_begin(c, "down_seg_blk");
+    k_down_seg_blk<TS, TC><<<c.num_sms * 8, 256, 0, c.stream>>>(a);
+    time_end(c, "down_seg_blk");
+  }
+  ZQ_CUDA_TRY(cudaGetLastError());
+  return ZQ_OK;
+}
+
 template <typename T>
 SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   SweepArgs<T> a;
@@ -498,6 +722,12 @@ zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_
   if (prec == ZQ_FP64)
     return run_down<double>(c, c.rec64, c.x64, static_cast<const double*>(w), static_cast<double*>(out));
   return run_down<float>(c, c.rec32, c.x32, static_cast<const float*>(w), static_cast<float*>(out));
+}
+
+zq_status launch_apply_block(Ctx& c, bool up, zq_prec prec, int64_t k, const void* in, void* out) {
+  if (prec == ZQ_FP64) return run_block<double, double>(c, up, (int32_t)k, c.rec64, in, out);
+  if (prec == ZQ_BF16) return run_block<__nv_bfloat16, float>(c, up, (int32_t)k, c.rec32, in, out);
+  return run_block<float, float>(c, up, (int32_t)k, c.rec32, in, out);
 }
 
 }  // namespace zq

@@ -140,6 +140,9 @@ struct Ctx {
   // by position
   double* x64 = nullptr;         // [nodes * 6]
   float* x32 = nullptr;          // [nodes * 6]
+  // block form (k right-hand sides): Info-/Velocity-sets of every node
+  void* xblk = nullptr;          // [nodes * 6 * k] of the arithmetic type
+  int64_t xblk_bytes = 0;
   // staging for host-buffer calls (bytes)
   void* stage = nullptr;
   int64_t stage_cap = 0;
@@ -249,5 +252,7 @@ zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z
 // zq_apply.cu
 zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t ldv, void* out);
 zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t ldo);
+// up: out = Q~ V, else out = Q~^T W; rows of k values (see include/zq.h)
+zq_status launch_apply_block(Ctx& c, bool up, zq_prec prec, int64_t k, const void* in, void* out);
 
 }  // namespace zq

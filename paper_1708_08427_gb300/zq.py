@@ -19,7 +19,7 @@ import numpy as np
 _LIB_PATH = Path(__file__).resolve().parent / "_build" / "libzq.so"
 
 ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE = range(7)
-ZQ_FP64, ZQ_FP32 = 0, 1
+ZQ_FP64, ZQ_FP32, ZQ_BF16 = 0, 1, 2
 ZQ_HOST_BUFFERS, ZQ_KEEP_TREE = 1, 2
 ZQ_BUILD_DD, ZQ_BUILD_FP64 = 0, 1
 
@@ -80,6 +80,12 @@ def _lib() -> ctypes.CDLL:
         L.zq_set_build_arith.argtypes = [_vp, ctypes.c_int]
         L.zq_launch_count.restype = ctypes.c_int
         L.zq_launch_count.argtypes = [_vp, _i64p]
+        L.zq_reserve_block.restype = ctypes.c_int
+        L.zq_reserve_block.argtypes = [_vp, ctypes.c_int, _i64]
+        for name in ("zq_apply_Q_block", "zq_apply_QT_block"):
+            f = getattr(L, name)
+            f.restype = ctypes.c_int
+            f.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp]
         L.zq_apply_Q_noalloc.restype = ctypes.c_int
         L.zq_apply_Q_noalloc.argtypes = [ctypes.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
         _L = L
@@ -175,6 +181,42 @@ class Context:
         oo = out.reshape(k, R)
         _check(_lib().zq_apply_Q(self._h, self._prec(v), k, _ptr(vv), 3 * N, _ptr(oo), R), "zq_apply_Q")
         return out.reshape(R) if squeeze and out.dim() == 2 else out
+
+    # ------------------------------------------------------- block form
+    @staticmethod
+    def _bprec(t):
+        import torch
+
+        return {torch.float64: ZQ_FP64, torch.float32: ZQ_FP32, torch.bfloat16: ZQ_BF16}[t.dtype]
+
+    def reserve_block(self, k_max: int, dtype):
+        """Block scratch for up to k_max columns of this dtype."""
+        import torch
+
+        p = {torch.float64: ZQ_FP64, torch.float32: ZQ_FP32, torch.bfloat16: ZQ_BF16}[dtype]
+        _check(_lib().zq_reserve_block(self._h, p, int(k_max)), "zq_reserve_block")
+
+    def apply_Q_block(self, V, out=None):
+        """V: (3N, k) device tensor (rows of k; row a*N + i) -> (R, k)."""
+        N, m, R, _ = self.sizes()
+        assert V.is_cuda and V.is_contiguous() and V.dim() == 2 and V.shape[0] == 3 * N
+        k = V.shape[1]
+        if out is None:
+            out = self._torch.empty((R, k), dtype=V.dtype, device=V.device)
+        assert out.is_contiguous() and tuple(out.shape) == (R, k) and out.dtype == V.dtype
+        _check(_lib().zq_apply_Q_block(self._h, self._bprec(V), k, _ptr(V), _ptr(out)), "zq_apply_Q_block")
+        return out
+
+    def apply_QT_block(self, W, out=None):
+        """W: (R, k) device tensor -> (3N, k)."""
+        N, m, R, _ = self.sizes()
+        assert W.is_cuda and W.is_contiguous() and W.dim() == 2 and W.shape[0] == R
+        k = W.shape[1]
+        if out is None:
+            out = self._torch.empty((3 * N, k), dtype=W.dtype, device=W.device)
+        assert out.is_contiguous() and tuple(out.shape) == (3 * N, k) and out.dtype == W.dtype
+        _check(_lib().zq_apply_QT_block(self._h, self._bprec(W), k, _ptr(W), _ptr(out)), "zq_apply_QT_block")
+        return out
 
     def apply_QT(self, w, out=None):
         """w: (R,) or (k, R) device tensor -> (3, N) or (k, 3, N)."""
