@@ -407,6 +407,8 @@ def run_ours(args, world, rank, local):
         out["fp64_step"] = fp64_step(args, ctx, bt, stream, flush, rng, world, dev)
         out["apply"] = apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev)
         out["e2e"] = e2e(args, ctx, bt, stream, world, dev)
+        out["multirhs"] = multirhs(args, stream, flush, world, dev, rank)
+        out["bd_loop"] = bd_loop(args, stream, flush, world, dev, rank)
     if rank == 0 and not args.no_extras:
         out["cpu_baseline"] = cpu_baseline(bt, args.cpu_seconds)
     ctx.close()
@@ -545,6 +547,179 @@ def e2e(args, ctx, bt, stream, world, dev):
     return {"value": tot / t, "unit": "beads/s", "ms_per_step": 1e3 * t / steps,
             "h2d_bytes_per_step": 24 * N + 12 * N + 4 * R, "d2h_bytes_per_step": 4 * R + 12 * N,
             "steps": steps}
+
+
+# ------------------------------------------------- multi-RHS and BD loop
+
+
+def multirhs(args, stream, flush, world, dev, rank, k=64):
+    """Block form on 500 shells with n_j uniform in [500, 2000] and k = 64
+    right-hand sides: Q~V + Q~^T W with the transforms built, in FP32, BF16
+    (bfloat16 storage, FP32 arithmetic) and FP64, each with its error against
+    the FP64 oracle on sampled columns (rank 0), and FP32 column by column
+    through the single-vector path for comparison.  Unit: bead-columns/s."""
+    import torch
+
+    import oracle
+    from paper_1708_08427_gb300 import workloads as W
+    from paper_1708_08427_gb300 import zq
+
+    bt = W.uniform_batch(m=500, nmin=500, nmax=2000, seed=rank)
+    N, R = bt.N, bt.n_residues
+    x, y, z = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (bt.x, bt.y, bt.z))
+    ctx = zq.Context(dev.index, stream)
+    ctx.build_tree_batched(bt.off, x, y, z, args.cut)
+    ctx.build_transforms(x, y, z)
+    census = node_census(ctx)
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    rng = np.random.default_rng(11)
+    V64 = torch.from_numpy(rng.standard_normal((3 * N, k))).to(dev)
+    W64 = torch.from_numpy(rng.standard_normal((R, k))).to(dev)
+    res = {"workload": f"m=500 shells, n_j uniform [500,2000], N={N}, k={k}", "unit": "bead-columns/s"}
+    cols = [0, k - 1]
+    for name, dt, es, rs in (("fp32", torch.float32, 4, 4), ("bf16", torch.bfloat16, 2, 4),
+                             ("fp64", torch.float64, 8, 8)):
+        ctx.reserve_block(k, dt)
+        V, Wr = V64.to(dt), W64.to(dt)
+        oq = torch.empty((R, k), dtype=dt, device=dev)
+        oqt = torch.empty((3 * N, k), dtype=dt, device=dev)
+        stream.synchronize()
+
+        def fn():
+            ctx.apply_Q_block(V, oq)
+            ctx.apply_QT_block(Wr, oqt)
+
+        r = timed(args, fn, stream, flush, world, dev, N * k, graph=not args.no_graph)
+        r["unit"] = "bead-columns/s"
+        rec = sum(census[t] * RECORD_FLOATS[t] * rs for t in census)
+        nodes = sum(census.values())
+        byt = 2 * (k * es * (3 * N + R) + rec + 12 * nodes + 4 * N)
+        r["hbm_achieved_gbs"] = byt / (r["ms_per_step"] / 1e3) / 1e9
+        r["hbm_frac"] = r["hbm_achieved_gbs"] / hbm
+        if rank == 0:
+            ctx.sync()
+            qv = oq.double().cpu().numpy()
+            qtw = oqt.double().cpu().numpy()
+            vin = V.double().cpu().numpy()
+            win = Wr.double().cpu().numpy()
+            err = 0.0
+            for c in cols:
+                rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z,
+                                             W.interleave(*vin[:, c].reshape(3, N)), win[:, c])
+                err = max(err, np.linalg.norm(qv[:, c] - rq) / np.linalg.norm(rq),
+                          np.linalg.norm(W.interleave(*qtw[:, c].reshape(3, N)) - rqt) / np.linalg.norm(rqt))
+            r["rel_err_vs_fp64_oracle"] = err
+            r["error_columns"] = cols
+        res[name] = r
+    # the same work as k single-vector sweeps (FP32), for comparison
+    Vc = V64.t().contiguous().to(torch.float32).reshape(k, 3, N)
+    Wc = W64.t().contiguous().to(torch.float32)
+    oqc = torch.empty((k, R), dtype=torch.float32, device=dev)
+    oqtc = torch.empty((k, 3, N), dtype=torch.float32, device=dev)
+
+    def fn_cols():
+        ctx.apply_Q(Vc, oqc)
+        ctx.apply_QT(Wc, oqtc)
+
+    r = timed(args, fn_cols, stream, flush, world, dev, N * k, graph=not args.no_graph, steps=3)
+    r["unit"] = "bead-columns/s"
+    res["fp32_column_by_column"] = r
+    ctx.close()
+    return res
+
+
+def bd_loop(args, stream, flush, world, dev, rank, steps_in_graph=10):
+    """Brownian-dynamics style loop on 1000 shells of 1000 beads with the tree
+    kept: per step every body gets a rigid motion (unit quaternion from
+    normalised N(0, I_4) about its centroid, N(0, 0.1^2) translation; applied
+    with torch as the workload driver), the transforms are rebuilt on the
+    kept tree, and Q~^T (Q~ f) is computed in FP32 for an N(0, 1) force f.
+    The loop is captured in a CUDA graph (steps_in_graph steps per replay).
+    The projector error |Q~^T Q~ f - (f - Z^T (Z Z^T)^-1 Z f)| / |f| is
+    measured (FP64, torch) after the timed replays."""
+    import torch
+
+    from paper_1708_08427_gb300 import workloads as W
+    from paper_1708_08427_gb300 import zq
+
+    m, n = 1000, 1000
+    bt = W.fixed_batch(m=m, n=n, seed=rank)
+    N, R = bt.N, bt.n_residues
+    body = torch.arange(m, device=dev).repeat_interleave(n)
+    P = torch.from_numpy(np.stack([bt.x, bt.y, bt.z], 1)).to(dev)          # (N, 3) float64
+    ctx = zq.Context(dev.index, stream)
+    x, y, z = (P[:, a].contiguous() for a in range(3))
+    ctx.build_tree_batched(bt.off, x, y, z, args.cut)
+    ctx.build_transforms(x, y, z)
+    torch.cuda.manual_seed(1234 + rank)  # the default generator: CUDA-graph safe
+    f = torch.empty((3, N), dtype=torch.float32, device=dev)
+    qf = torch.empty(R, dtype=torch.float32, device=dev)
+    out = torch.empty((3, N), dtype=torch.float32, device=dev)
+
+    def rot(q):  # (m, 4) unit quaternions -> (m, 3, 3)
+        a, b, c, d = q.unbind(1)
+        return torch.stack([
+            torch.stack([a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)], 1),
+            torch.stack([2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)], 1),
+            torch.stack([2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d], 1)], 1)
+
+    def one_step():
+        q = torch.randn((m, 4), device=dev, dtype=torch.float64)
+        q = q / q.norm(dim=1, keepdim=True)
+        t = 0.1 * torch.randn((m, 3), device=dev, dtype=torch.float64)
+        P3 = P.view(m, n, 3)
+        cen = P3.mean(1, keepdim=True)
+        P3.copy_(torch.bmm(P3 - cen, rot(q).transpose(1, 2)) + cen + t[:, None, :])
+        x.copy_(P[:, 0]); y.copy_(P[:, 1]); z.copy_(P[:, 2])
+        ctx.build_transforms(x, y, z)
+        f.copy_(torch.randn((3, N), device=dev, dtype=torch.float32))
+        ctx.apply_Q(f, qf)
+        ctx.apply_QT(qf, out)
+
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            one_step()
+    stream.synchronize()
+    g = None
+    if not args.no_graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(steps_in_graph):
+                one_step()
+        stream.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    ms = []
+    for _ in range(reps):
+        s0.record(stream)
+        with torch.cuda.stream(stream):
+            if g is not None:
+                g.replay()
+            else:
+                for _ in range(steps_in_graph):
+                    one_step()
+        s1.record(stream)
+        stream.synchronize()
+        ms.append(s0.elapsed_time(s1))
+    ctx.sync()
+    t_step = max_over_ranks(world, sum(ms) / 1e3, dev) / (reps * steps_in_graph)
+    # projector error of the last step, in FP64
+    Pc = P - (torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, P) / n)[body]
+    fd = f.double().t()                                            # (N, 3)
+    Fsum = torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, fd)
+    Tsum = torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, torch.cross(Pc, fd, dim=1))
+    r2 = (Pc * Pc).sum(1)
+    J = torch.zeros((m, 3, 3), device=dev, dtype=torch.float64).index_add_(
+        0, body, r2[:, None, None] * torch.eye(3, device=dev, dtype=torch.float64) - Pc[:, :, None] * Pc[:, None, :])
+    om = torch.linalg.solve(J, Tsum)
+    Pf = (Fsum / n)[body] + torch.cross(om[body], Pc, dim=1)
+    err = float(((out.double().t() - (fd - Pf)).norm() / fd.norm()).item())
+    ctx.close()
+    return {"workload": "m=1000 shells x 1000 beads, tree kept, per step: rigid motion, transforms rebuilt, "
+                        "Q~^T(Q~ f) FP32", "steps_per_s": 1.0 / t_step, "ms_per_step": 1e3 * t_step,
+            "beads_per_s": N / t_step, "graph": g is not None, "steps_timed": reps * steps_in_graph,
+            "projector_rel_err_fp32": err}
 
 
 # ------------------------------------------------------------ CPU oracle
