@@ -4,7 +4,10 @@
 //   2. 21-bit quantisation and bisection keys (z, then y, then x per octree
 //      level, most significant first);
 //   3. stable LSD radix sort of (key, body-local index) in shared memory,
-//      eight passes of 8-bit digits: equal keys keep index order;
+//      8-bit digits: four passes over the high 32 key bits, then each run of
+//      equal high halves (rare: beads closer than 2^-10 of the box) sorted
+//      by insertion; bodies with a run of more than 32 such beads take all
+//      eight passes instead.  Equal keys keep index order;
 //   4. LCP of sorted neighbours (63 coordinate levels, then 32 index levels);
 //   5. bottom-up construction: a node's parent is the neighbouring split
 //      with the larger LCP; each child deposits (code, range end, height) in
@@ -186,11 +189,14 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   const int lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int per_warp = (n + NW - 1) / NW;
+  __shared__ int long_run;
+  int pass_lo = 4;  // first the high 32 key bits only (see the fix-up below)
+  for (;;) {
   uint64_t* kin = keyA;
   uint64_t* kout = keyB;
   uint16_t* iin = idxA;
   uint16_t* iout = idxB;
-  for (int pass = 0; pass < 8; ++pass) {
+  for (int pass = pass_lo; pass < 8; ++pass) {
     const int shift = 8 * pass;
     for (int d = lane; d < 256; d += 32) whist[warp * 256 + d] = 0;
     __syncwarp();
@@ -253,7 +259,49 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
     uint64_t* tk = kin; kin = kout; kout = tk;
     uint16_t* ti = iin; iin = iout; iout = ti;
   }
-  // after 8 passes the sorted data is back in keyA / idxA
+  // after 4 or 8 passes the sorted data is back in keyA / idxA
+  if (pass_lo == 0) break;
+  // Fix-up of the 4-pass order: beads whose keys share the high 32 bits
+  // (the first 10 2/3 octree levels) are in index order; each such run is
+  // sorted by the low bits (stable, so equal keys keep index order).  A run
+  // longer than 32 beads sends the body through all 8 passes instead.
+  if (tid == 0) long_run = 0;
+  __syncthreads();
+  for (int p = tid; p < n; p += THREADS) {
+    const uint32_t hk = (uint32_t)(keyA[p] >> 32);
+    if (p > 0 && (uint32_t)(keyA[p - 1] >> 32) == hk) continue;   // not a run start
+    int L = 1;
+    while (p + L < n && L <= 32 && (uint32_t)(keyA[p + L] >> 32) == hk) ++L;
+    if (L == 1) continue;
+    if (L > 32) {
+      long_run = 1;
+      continue;
+    }
+    for (int u = p + 1; u < p + L; ++u) {  // insertion sort by the low half
+      const uint64_t k = keyA[u];
+      const uint16_t ix = idxA[u];
+      int v = u - 1;
+      while (v >= p && keyA[v] > k) {
+        keyA[v + 1] = keyA[v];
+        idxA[v + 1] = idxA[v];
+        --v;
+      }
+      keyA[v + 1] = k;
+      idxA[v + 1] = ix;
+    }
+  }
+  __syncthreads();
+  if (!long_run) break;
+  // back to index order, then the full sort
+  for (int p = tid; p < n; p += THREADS) keyB[idxA[p]] = keyA[p];
+  __syncthreads();
+  for (int i = tid; i < n; i += THREADS) {
+    keyA[i] = keyB[i];
+    idxA[i] = (uint16_t)i;
+  }
+  __syncthreads();
+  pass_lo = 0;
+  }
 
   // ---- 4. permutation and LCP of neighbours
   uint8_t* lcp = reinterpret_cast<uint8_t*>(keyB);   // keyB is free now

@@ -150,7 +150,7 @@ def rel_err_per_body(got, ref, bt, kind):
     return np.array(errs)
 
 
-def check_apply(ctx, bt, dtype, k=1, seed=0):
+def check_apply(ctx, bt, dtype, k=1, seed=0, tol=None):
     dev = _dev()
     rng = np.random.default_rng(seed)
     v = rng.standard_normal((k, 3, bt.N))
@@ -166,7 +166,7 @@ def check_apply(ctx, bt, dtype, k=1, seed=0):
         e1 = rel_err_per_body(qv[c], rq, bt, "res")
         e2 = rel_err_per_body(W.interleave(*qtw[c]), rqt, bt, "bead")
         worst = max(worst, e1.max(), e2.max())
-    assert worst <= TOL[dtype], (dtype, worst)
+    assert worst <= (tol or TOL[dtype]), (dtype, worst)
     return worst
 
 
@@ -254,6 +254,30 @@ def test_edge_geometries(arith):
     check_tree(ctx, bt, bodies)
     check_records(ctx, bt, bodies, arith, skip=(2,))
     check_apply(ctx, bt, np.float64)
+
+
+@pytest.mark.parametrize("cluster", [20, 60])
+def test_tight_clusters_sort_exactly(cluster):
+    """A cluster of beads inside one cell of the first 10 2/3 octree levels
+    (their keys share the high 32 bits) among spread-out beads: runs of at
+    most 32 such beads are sorted by the fix-up, longer ones by the full
+    sort; the tree is bit-exact either way.
+
+    The sweeps are held to the conditioning of the input: a node's offset
+    d = c_x - c_y between centroids of size |c| carries the last-bit
+    rounding of the centroids (|c| 2^-53 each, in a different order of
+    operations in the oracle and the kernels), so inside a cluster of extent
+    delta the relative error of d, and of the rows of G built from it, is up
+    to about 2 |c| 2^-53 / delta; the tolerance is 8 times that."""
+    rng = np.random.default_rng(cluster)
+    pts = [np.r_[rng.uniform(0, 1, (40, 3)), 0.5 + 1e-7 * rng.uniform(0, 1, (cluster, 3))],
+           np.r_[rng.uniform(-3, 3, (900, 3)), 1.0 + 1e-6 * rng.uniform(0, 1, (cluster, 3))]]
+    bt = _batch_from_points(pts)
+    ctx, _ = make_ctx(bt, cut=3)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    tol = max(TOL[np.float64], 8 * 2 * 3.0 * 2.0 ** -53 / 1e-7)
+    check_apply(ctx, bt, np.float64, tol=tol)
 
 
 def test_coincident_beads_warn():
