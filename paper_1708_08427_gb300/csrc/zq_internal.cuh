@@ -118,14 +118,13 @@ struct Ctx {
   int64_t bhist_cap = 0;
   // segments (see kSegMax), by position p (node id order with each segment
   // reordered by height)
-  int32_t* par = nullptr;        // [nodes] parent node id (-1: body root)
   int32_t* pos_of = nullptr;     // [nodes] node id -> position
   int32_t* pnode = nullptr;      // [nodes] position -> node id
   int2* pc = nullptr;            // [nodes] child codes: >= 0 child position, < 0 leaf
   int32_t* proff = nullptr;      // [nodes] residue offset
   uint8_t* ph = nullptr;         // [nodes] height
   int32_t* prw = nullptr;        // [nodes + 1] record offset (4-word units, read as uint32)
-  int32_t* seg_flag = nullptr;   // [nodes] scan workspace: segment roots, then top nodes
+  int32_t* seg_flag = nullptr;   // [nodes] workspace: top-node counts and fill per body
   int4* seg = nullptr;           // [nodes] per segment: first position, nodes, first sorted
                                  // bead, 1 if its root is a body root (first nseg used)
   int32_t* topv = nullptr;       // [nodes] top nodes (= positions), grouped by body

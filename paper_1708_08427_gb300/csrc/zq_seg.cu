@@ -7,12 +7,24 @@
 // subtree), so the segments and the nodes above them ("top" nodes) tile
 // the node ids.  Positions: a top node keeps its id; the nodes of a segment
 // are permuted inside the segment's id range so that heights increase
-// (any order within one height).  The sweeps then take a segment per
-// thread block, height by height, and the top nodes per body.
+// (any order within one height), which puts the segment root, the only
+// node of the largest height, at the last position of the range.  The
+// sweeps then take a segment per thread block, height by height, and the
+// top nodes per body.
 //
-// Built after the tree, per call of zq_build_tree_batched; everything stays
-// on the device (no host synchronisation): the number of segments is a
-// device value that the grid-stride sweep kernels read.
+// Four kernels and two scans, all on the device (no host synchronisation:
+// the number of segments is a device value that the grid-stride kernels
+// read):
+//   classify     per node: parents mark their children that are segment
+//                roots (and body roots mark themselves); top nodes are
+//                counted per body and get their per-position data here
+//                (a child segment root sits at the last position of its
+//                segment, which follows from its count alone);
+//   scan         top counts per body -> offsets;
+//   top_scatter  top nodes listed per body;
+//   seg_order    one block per segment: height order, positions, and the
+//                per-position data of its nodes;
+//   scan         record sizes -> record offsets.
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -23,73 +35,92 @@ constexpr int kThreads = 256;
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-__device__ __forceinline__ bool seg_root_of(const int32_t* __restrict__ cnt, const int32_t* __restrict__ par,
-                                            int64_t q) {
-  if (cnt[q] > kSegMax) return false;
-  const int32_t p = par[q];
-  return p < 0 || cnt[p] > kSegMax;
+// Appends the flagged lanes' values (one atomic per warp; all 32 lanes of
+// the warp must call).
+__device__ __forceinline__ void warp_append(bool flag, int32_t value, int32_t* __restrict__ count,
+                                            int4* __restrict__ list) {
+  const unsigned b = __ballot_sync(0xffffffffu, flag);
+  if (!b) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(b) - 1;
+  int32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (flag) list[base + __popc(b & ((1u << lane) - 1u))] = make_int4(value, 0, 0, 0);
 }
 
-// Parents; top nodes keep position = id.
-__global__ void k_parents(int64_t nodes, const int32_t* __restrict__ cl, const int32_t* __restrict__ cr,
-                          const int32_t* __restrict__ cnt, int32_t* __restrict__ par,
-                          int32_t* __restrict__ pos_of, int32_t* __restrict__ pnode) {
+// Position of a child code as the sweeps see it: a leaf stays a leaf, a
+// top node keeps its id, a segment root is the last position of its range.
+__device__ __forceinline__ int32_t child_pos(int32_t c, const int32_t* __restrict__ cnt,
+                                             const int32_t* __restrict__ first,
+                                             const int32_t* __restrict__ bead_body) {
+  if (c < 0) return c;
+  const int32_t k = cnt[c];
+  if (k > kSegMax) return c;
+  const int32_t f = first[c];
+  return f - bead_body[f] + k - 2;
+}
+
+__global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const int32_t* __restrict__ cl,
+                           const int32_t* __restrict__ cr, const int32_t* __restrict__ cnt,
+                           const int32_t* __restrict__ first, const int32_t* __restrict__ bead_body,
+                           const int32_t* __restrict__ roff, const uint8_t* __restrict__ height,
+                           int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* __restrict__ top_cnt,
+                           int32_t* __restrict__ pos_of, int32_t* __restrict__ pnode, int2* __restrict__ pc,
+                           int32_t* __restrict__ proff, uint8_t* __restrict__ ph, int32_t* __restrict__ units) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nodes) return;
-  const int32_t a = cl[q], b = cr[q];
-  if (a >= 0) par[a] = (int32_t)q;
-  if (b >= 0) par[b] = (int32_t)q;
-  if (cnt[q] > kSegMax) {
-    pos_of[q] = (int32_t)q;
-    pnode[q] = (int32_t)q;
+  bool self_root = false, left_root = false, right_root = false;
+  int32_t a = -1, b = -1;
+  if (q < nodes) {
+    a = cl[q];
+    b = cr[q];
+    const int32_t c = cnt[q];
+    const int32_t f = first[q];
+    const int32_t j = bead_body[f];
+    if (c <= kSegMax) {
+      self_root = c == (int32_t)(off[j + 1] - off[j]);  // a whole body of at most kSegMax beads
+    } else {
+      left_root = a >= 0 && cnt[a] <= kSegMax;
+      right_root = b >= 0 && cnt[b] <= kSegMax;
+      atomicAdd(&top_cnt[j], 1);
+      pos_of[q] = (int32_t)q;
+      pnode[q] = (int32_t)q;
+      pc[q] = make_int2(child_pos(a, cnt, first, bead_body), child_pos(b, cnt, first, bead_body));
+      proff[q] = roff[q];
+      ph[q] = height[q];
+      units[q] = rec_words((a >= 0) + (b >= 0)) / 4;
+    }
   }
+  warp_append(self_root, (int32_t)q, nseg, seg);
+  warp_append(left_root, a, nseg, seg);
+  warp_append(right_root, b, nseg, seg);
 }
 
-__global__ void k_seg_flags(int64_t nodes, const int32_t* __restrict__ cnt, const int32_t* __restrict__ par,
-                            int32_t* __restrict__ flag) {
+__global__ void k_top_scatter(int64_t nodes, const int32_t* __restrict__ cnt, const int32_t* __restrict__ first,
+                              const int32_t* __restrict__ bead_body, const int32_t* __restrict__ top_off,
+                              int32_t* __restrict__ fill, int32_t* __restrict__ topv) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nodes) flag[q] = seg_root_of(cnt, par, q) ? 1 : 0;
+  if (q >= nodes || cnt[q] <= kSegMax) return;
+  const int32_t j = bead_body[first[q]];
+  topv[top_off[j] + atomicAdd(&fill[j], 1)] = (int32_t)q;
 }
 
-__global__ void k_seg_list(int64_t nodes, const int32_t* __restrict__ cnt, const int32_t* __restrict__ par,
-                           const int32_t* __restrict__ idx, int4* __restrict__ seg) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nodes && seg_root_of(cnt, par, q)) seg[idx[q]] = make_int4((int32_t)q, 0, 0, 0);
-}
-
-__global__ void k_top_flags(int64_t nodes, const int32_t* __restrict__ cnt, int32_t* __restrict__ flag) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nodes) flag[q] = cnt[q] > kSegMax ? 1 : 0;
-}
-
-__global__ void k_top_list(int64_t nodes, const int32_t* __restrict__ cnt, const int32_t* __restrict__ idx,
-                           int32_t* __restrict__ topv) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nodes && cnt[q] > kSegMax) topv[idx[q]] = (int32_t)q;
-}
-
-// top_off[j] = number of top nodes in bodies before j (node ids of body j
-// start at off[j] - j); top_off[m] = all.
-__global__ void k_top_off(int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ idx,
-                          const int32_t* __restrict__ total, int32_t* __restrict__ top_off) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < m) top_off[j] = idx[off[j] - j];
-  else if (j == m) top_off[m] = *total;
-}
-
-// One block per segment: body, range, and the height order inside it.
+// One block per segment: range, height order, positions, per-position data.
 __global__ void __launch_bounds__(kThreads)
 k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, const int64_t* __restrict__ off,
-            int64_t m, const int32_t* __restrict__ first, const int32_t* __restrict__ cnt,
-            const uint8_t* __restrict__ height, int32_t* __restrict__ pos_of, int32_t* __restrict__ pnode) {
+            const int32_t* __restrict__ bead_body, const int32_t* __restrict__ first,
+            const int32_t* __restrict__ cnt, const int32_t* __restrict__ cl, const int32_t* __restrict__ cr,
+            const int32_t* __restrict__ roff, const uint8_t* __restrict__ height, int32_t* __restrict__ pos_of,
+            int32_t* __restrict__ pnode, int2* __restrict__ pc, int32_t* __restrict__ proff,
+            uint8_t* __restrict__ ph, int32_t* __restrict__ units) {
   __shared__ int32_t hist[kMaxHeight + 1];
   __shared__ int4 info;
   const int ns = *nseg;
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
     if (threadIdx.x == 0) {
       const int32_t r = seg[i].x;
-      const int32_t j = body_of_node(off, m, r);
       const int32_t f = first[r], c = cnt[r];
+      const int32_t j = bead_body[f];
       info = make_int4(f - j, c - 1, f, c == (int32_t)(off[j + 1] - off[j]) ? 1 : 0);
       seg[i] = info;
     }
@@ -113,50 +144,39 @@ k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, const int6
       pos_of[q] = p;
       pnode[p] = q;
     }
+    __syncthreads();  // pos_of of the whole segment is visible to the block
+    for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+      const int32_t q = a + t;
+      const int32_t l = cl[q], r = cr[q];
+      const int32_t p = pos_of[q];
+      pc[p] = make_int2(l >= 0 ? pos_of[l] : l, r >= 0 ? pos_of[r] : r);
+      proff[p] = roff[q];
+      ph[p] = height[q];
+      units[p] = rec_words((l >= 0) + (r >= 0)) / 4;
+    }
     __syncthreads();
   }
-}
-
-// Per position: children as positions, residue offset, height and the
-// record size in 4-word units (scanned into offsets afterwards).
-__global__ void k_pos_data(int64_t nodes, const int32_t* __restrict__ pnode, const int32_t* __restrict__ pos_of,
-                           const int32_t* __restrict__ cl, const int32_t* __restrict__ cr,
-                           const int32_t* __restrict__ roff, const uint8_t* __restrict__ height,
-                           int2* __restrict__ pc, int32_t* __restrict__ proff, uint8_t* __restrict__ ph,
-                           int32_t* __restrict__ prw) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nodes) return;
-  const int32_t q = pnode[p];
-  const int32_t a = cl[q], b = cr[q];
-  pc[p] = make_int2(a >= 0 ? pos_of[a] : a, b >= 0 ? pos_of[b] : b);
-  proff[p] = roff[q];
-  ph[p] = height[q];
-  prw[p] = rec_words((a >= 0) + (b >= 0)) / 4;
 }
 
 }  // namespace
 
 zq_status launch_segments(Ctx& c) {
   cudaStream_t s = c.stream;
-  const int64_t n = c.nodes;
-  ZQ_CUDA_TRY(cudaMemsetAsync(c.par, 0xff, n * sizeof(int32_t), s));
+  const int64_t n = c.nodes, m = c.m;
+  int32_t* top_cnt = c.seg_flag;  // [m], then the fill counters [m]
+  ZQ_CUDA_TRY(cudaMemsetAsync(c.nseg, 0, 2 * sizeof(int32_t), s));
+  ZQ_CUDA_TRY(cudaMemsetAsync(top_cnt, 0, 2 * m * sizeof(int32_t), s));
   time_begin(c, "segments");
-  k_parents<<<blocks(n), kThreads, 0, s>>>(n, c.cl, c.cr, c.cnt, c.par, c.pos_of, c.pnode);
-  k_seg_flags<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.par, c.seg_flag);
-  time_end(c, "segments");
-  ZQ_TRY_STATUS(launch_exclusive_scan(c, c.seg_flag, c.seg_flag, n, c.scan_tmp, c.nseg));
-  time_begin(c, "segments");
-  k_seg_list<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.par, c.seg_flag, c.seg);
-  k_top_flags<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.seg_flag);
-  time_end(c, "segments");
-  ZQ_TRY_STATUS(launch_exclusive_scan(c, c.seg_flag, c.seg_flag, n, c.scan_tmp, c.nseg + 1));
-  time_begin(c, "segments");
-  k_top_list<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.seg_flag, c.topv);
-  k_top_off<<<blocks(c.m + 1), kThreads, 0, s>>>(c.m, c.off, c.seg_flag, c.nseg + 1, c.top_off);
-  k_seg_order<<<c.num_sms * 8, kThreads, 0, s>>>(c.nseg, c.seg, c.off, c.m, c.first, c.cnt, c.height,
-                                                 c.pos_of, c.pnode);
-  k_pos_data<<<blocks(n), kThreads, 0, s>>>(n, c.pnode, c.pos_of, c.cl, c.cr, c.roff, c.height, c.pc,
+  k_classify<<<blocks(n), kThreads, 0, s>>>(n, c.off, c.cl, c.cr, c.cnt, c.first, c.bead_body, c.roff,
+                                            c.height, c.nseg, c.seg, top_cnt, c.pos_of, c.pnode, c.pc,
                                             c.proff, c.ph, c.prw);
+  time_end(c, "segments");
+  ZQ_TRY_STATUS(launch_exclusive_scan(c, top_cnt, c.top_off, m, c.scan_tmp, c.top_off + m));
+  time_begin(c, "segments");
+  k_top_scatter<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.first, c.bead_body, c.top_off, top_cnt + m, c.topv);
+  k_seg_order<<<c.num_sms * 8, kThreads, 0, s>>>(c.nseg, c.seg, c.off, c.bead_body, c.first, c.cnt, c.cl,
+                                                 c.cr, c.roff, c.height, c.pos_of, c.pnode, c.pc, c.proff,
+                                                 c.ph, c.prw);
   time_end(c, "segments");
   ZQ_TRY_STATUS(launch_exclusive_scan(c, c.prw, c.prw, n, c.scan_tmp, c.prw + n));
   ZQ_CUDA_TRY(cudaGetLastError());

@@ -14,7 +14,8 @@
 //      the parent's 64-bit shared-memory slot with one atomic exchange, and
 //      the child that finds the sibling's deposit completes the parent.
 // Output: the same global node arrays as the device-wide path (perm, child
-// codes, first, count, height, residue size, root).
+// codes, first, count, height, residue size, root); when the batch has no
+// larger bodies, the residue offsets themselves (6.).
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -36,6 +37,7 @@ struct SmallTreeArgs {
   int32_t* res;
   int32_t* root;
   int32_t* err;
+  int final_roff;  // 1: write residue offsets (no device-wide scan follows)
 };
 
 __device__ __forceinline__ uint32_t quantise_exact(double p, double lo, double hi) {
@@ -381,6 +383,24 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
     l = lo_;
     r = hi_;
   }
+
+  // ---- 6. residue offsets (when every body of the batch is built here):
+  // body j's residues start at 3 off[j] - 6 j; inside the body, an exclusive
+  // prefix of the residue sizes in node-id order
+  if (a.final_roff) {
+    __syncthreads();
+    const int nn = n - 1;
+    const int per = (nn + THREADS - 1) / THREADS;
+    const int g0 = min(nn, tid * per), g1 = min(nn, g0 + per);
+    int32_t sum = 0;
+    for (int g = g0; g < g1; ++g) sum += a.res[nb + g];
+    int32_t run = block_excl_scan<THREADS>(sum, sh, nullptr) + (int32_t)(3 * o - 6 * (int64_t)j);
+    for (int g = g0; g < g1; ++g) {
+      const int32_t v = a.res[nb + g];
+      a.res[nb + g] = run;
+      run += v;
+    }
+  }
 }
 
 template <int MAXN, int THREADS>
@@ -414,6 +434,7 @@ zq_status launch_small_trees(Ctx& c, const double* x, const double* y, const dou
   a.x = x; a.y = y; a.z = z;
   a.off = c.off; a.bodies = nullptr; a.perm = c.perm; a.cl = c.cl; a.cr = c.cr; a.first = c.first;
   a.cnt = c.cnt; a.height = c.height; a.res = c.roff; a.root = c.root; a.err = c.counters + 2;
+  a.final_roff = c.big_bodies.empty() ? 1 : 0;
   const int* cs = c.small_class_start;
   zq_status st;
   if ((st = launch_class<8192, 1024>(c, a, c.small_d + cs[3], cs[4] - cs[3])) != ZQ_OK) return st;

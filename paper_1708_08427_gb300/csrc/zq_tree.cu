@@ -397,8 +397,10 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
     time_end(c, "bottom_up");
     ZQ_CUDA_TRY(cudaGetLastError());
   }
-  st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
-  if (st != ZQ_OK) return st;
+  if (!c.big_bodies.empty()) {  // else the per-body kernels wrote the offsets
+    st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
+    if (st != ZQ_OK) return st;
+  }
   st = launch_segments(c);
   if (st != ZQ_OK) return st;
   // schedule of the build
