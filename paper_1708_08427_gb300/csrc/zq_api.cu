@@ -42,6 +42,20 @@ void free_all(Ctx& c) {
   c = fresh;
 }
 
+void destroy_streams(Ctx& c) {
+  for (int i = 0; i < 3; ++i) {
+    if (c.side[i]) {
+      cudaStreamSynchronize(c.side[i]);
+      cudaStreamDestroy(c.side[i]);
+    }
+    if (c.join_ev[i]) cudaEventDestroy(c.join_ev[i]);
+    c.side[i] = nullptr;
+    c.join_ev[i] = nullptr;
+  }
+  if (c.fork_ev) cudaEventDestroy(c.fork_ev);
+  c.fork_ev = nullptr;
+}
+
 #define ZQ_TRY(expr)                  \
   do {                                \
     zq_status _s = (expr);            \
@@ -147,6 +161,16 @@ zq_status zq_create(zq_ctx** ctx, int device, void* cuda_stream) {
     delete h;
     return ZQ_ECUDA;
   }
+  bool ok = cudaEventCreateWithFlags(&h->c.fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 3 && ok; ++i) {
+    ok = cudaStreamCreateWithFlags(&h->c.side[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->c.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    destroy_streams(h->c);
+    delete h;
+    return ZQ_ECUDA;
+  }
   *ctx = h;
   return ZQ_OK;
 }
@@ -155,6 +179,7 @@ zq_status zq_destroy(zq_ctx* ctx) {
   if (!ctx) return ZQ_EINVAL;
   cudaSetDevice(ctx->c.device);
   cudaStreamSynchronize(ctx->c.stream);
+  destroy_streams(ctx->c);
   free_all(ctx->c);
   delete ctx;
   return ZQ_OK;

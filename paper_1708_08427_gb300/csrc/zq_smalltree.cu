@@ -409,16 +409,15 @@ constexpr size_t small_tree_smem() {
 }
 
 template <int MAXN, int THREADS>
-zq_status launch_class(Ctx& c, const SmallTreeArgs& a, const int32_t* bodies, int count) {
+zq_status launch_class(Ctx& c, const SmallTreeArgs& a, const int32_t* bodies, int count, cudaStream_t s) {
   if (count <= 0) return ZQ_OK;
   constexpr size_t smem = small_tree_smem<MAXN, THREADS>();
   ZQ_CUDA_TRY(cudaFuncSetAttribute(k_small_tree<MAXN, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   SmallTreeArgs b = a;
   b.bodies = bodies;
-  time_begin(c, "small_tree");
-  k_small_tree<MAXN, THREADS><<<(unsigned)count, THREADS, smem, c.stream>>>(b);
-  time_end(c, "small_tree");
+  ++c.launches;
+  k_small_tree<MAXN, THREADS><<<(unsigned)count, THREADS, smem, s>>>(b);
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }
@@ -436,11 +435,24 @@ zq_status launch_small_trees(Ctx& c, const double* x, const double* y, const dou
   a.cnt = c.cnt; a.height = c.height; a.res = c.roff; a.root = c.root; a.err = c.counters + 2;
   a.final_roff = c.big_bodies.empty() ? 1 : 0;
   const int* cs = c.small_class_start;
+  // The size classes are independent (disjoint bodies): the three smaller
+  // ones run on side streams forked from the context stream, so their
+  // blocks fill the SMs that the largest class leaves free; all join back
+  // before anything that reads the tree.  One timing span covers the four.
+  time_begin(c, "small_tree");
+  --c.launches;  // time_begin counted a launch; launch_class counts each one
+  ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+  for (int i = 0; i < 3; ++i) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[i], c.fork_ev, 0));
   zq_status st;
-  if ((st = launch_class<8192, 1024>(c, a, c.small_d + cs[3], cs[4] - cs[3])) != ZQ_OK) return st;
-  if ((st = launch_class<4096, 512>(c, a, c.small_d + cs[2], cs[3] - cs[2])) != ZQ_OK) return st;
-  if ((st = launch_class<2048, 256>(c, a, c.small_d + cs[1], cs[2] - cs[1])) != ZQ_OK) return st;
-  if ((st = launch_class<1024, 256>(c, a, c.small_d + cs[0], cs[1] - cs[0])) != ZQ_OK) return st;
+  if ((st = launch_class<8192, 1024>(c, a, c.small_d + cs[3], cs[4] - cs[3], c.stream)) != ZQ_OK) return st;
+  if ((st = launch_class<4096, 512>(c, a, c.small_d + cs[2], cs[3] - cs[2], c.side[0])) != ZQ_OK) return st;
+  if ((st = launch_class<2048, 256>(c, a, c.small_d + cs[1], cs[2] - cs[1], c.side[1])) != ZQ_OK) return st;
+  if ((st = launch_class<1024, 256>(c, a, c.small_d + cs[0], cs[1] - cs[0], c.side[2])) != ZQ_OK) return st;
+  for (int i = 0; i < 3; ++i) {
+    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[i], c.side[i]));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[i], 0));
+  }
+  time_end(c, "small_tree");
   return ZQ_OK;
 }
 
