@@ -29,7 +29,7 @@ void free_all(Ctx& c) {
   void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
-                c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.stage,
+                c.sheight, c.bstart, c.brec, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage,
                 c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.topv,
                 c.top_off, c.nseg, c.srw, c.xblk};
   for (void* p : ps)
@@ -107,6 +107,8 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.rec32, nodes * zq::kRecMax));
     ZQ_TRY(grow(&c.x64, nodes * 6));
     ZQ_TRY(grow(&c.x32, nodes * 6));
+    ZQ_TRY(grow(&c.x64b, nodes * 6));
+    ZQ_TRY(grow(&c.x32b, nodes * 6));
     ZQ_TRY(grow(&c.pos_of, nodes));
     ZQ_TRY(grow(&c.pnode, nodes));
     ZQ_TRY(grow(&c.pc, nodes));
@@ -398,8 +400,27 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
   c.have_xform = true;
   c.have64 = prec == ZQ_FP64;
   c.have32 = prec == ZQ_FP32;
-  if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
-  if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));
+  if (dv && dw) {
+    // the two products are independent: Q~^T w on a side stream (with its
+    // own scratch) while Q~ v runs on the context stream, joined after
+    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[0], c.fork_ev, 0));
+    ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
+    cudaStream_t main = c.stream;
+    std::swap(c.x32, c.x32b);
+    std::swap(c.x64, c.x64b);
+    c.stream = c.side[0];
+    const zq_status st = zq::launch_apply_QT(c, prec, dw, dqtw, 3 * N);
+    c.stream = main;
+    std::swap(c.x32, c.x32b);
+    std::swap(c.x64, c.x64b);
+    ZQ_TRY(st);
+    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[0], c.side[0]));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[0], 0));
+  } else {
+    if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
+    if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));
+  }
   if (host) {
     if (qv) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));
     if (qtw) ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));

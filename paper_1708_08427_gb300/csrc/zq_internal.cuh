@@ -144,6 +144,8 @@ struct Ctx {
   // by position
   double* x64 = nullptr;         // [nodes * 6]
   float* x32 = nullptr;          // [nodes * 6]
+  double* x64b = nullptr;        // second copies: Q~^T w on a side stream while
+  float* x32b = nullptr;         // Q~ v runs on the context stream (zq_pipeline)
   // block form (k right-hand sides): Info-/Velocity-sets of every node
   void* xblk = nullptr;          // [nodes * 6 * k] of the arithmetic type
   int64_t xblk_bytes = 0;
