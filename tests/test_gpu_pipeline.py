@@ -1,0 +1,154 @@
+"""zq_pipeline, the one-call step the benchmark times: tree, transforms and
+both products (Q~v on the context stream, Q~^T w concurrently on a side
+stream with its own scratch), from device or pinned host buffers, with the
+tree rebuilt or kept.
+
+Against the FP64 oracle per body (1e-12 FP64, 1e-5 FP32).  With the tree
+kept, the oracle's own tree (built from the moved coordinates) is not the
+kept one, so the result is checked against the separate calls on a context
+that built its tree from the original coordinates (bitwise), and against
+the basis-free projector identity Q~^T Q~ f = f - Z^T (Z Z^T)^-1 Z f.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_08427_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _zq():
+    from paper_1708_08427_gb300 import zq
+
+    return zq
+
+
+def _per_body(got, ref, bt, kind):
+    errs, ro = [], 0
+    for j in range(bt.m):
+        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
+        if kind == "res":
+            a, b = got[ro:ro + 3 * n - 6], ref[ro:ro + 3 * n - 6]
+        else:
+            a, b = got[3 * o:3 * (o + n)], ref[3 * o:3 * (o + n)]
+        ro += 3 * n - 6
+        errs.append(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    return max(errs)
+
+
+@pytest.mark.parametrize("dtype,host", [(torch.float32, False), (torch.float64, False), (torch.float32, True)])
+def test_pipeline_matches_oracle(dtype, host):
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=24, nmin=20, nmax=1800, seed=31)
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal((3, bt.N))
+    w = rng.standard_normal(bt.n_residues)
+    if host:
+        mk = lambda a, dt=dtype: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+        x, y, z = (mk(a, torch.float64) for a in (bt.x, bt.y, bt.z))
+        tv, tw = mk(v), mk(w)
+        qv = torch.empty(bt.n_residues, dtype=dtype).pin_memory()
+        qtw = torch.empty((3, bt.N), dtype=dtype).pin_memory()
+    else:
+        mk = lambda a, dt=dtype: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+        x, y, z = (mk(a, torch.float64) for a in (bt.x, bt.y, bt.z))
+        tv, tw = mk(v), mk(w)
+        qv = torch.empty(bt.n_residues, dtype=dtype, device=dev)
+        qtw = torch.empty((3, bt.N), dtype=dtype, device=dev)
+    ctx = zq.Context(0)
+    for _ in range(2):  # a second call reuses the plan and the buffers
+        ctx.pipeline(bt.off, x, y, z, tv, qv, tw, qtw, host=host)
+        ctx.sync()
+        rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*v), w)
+        e1 = _per_body(qv.double().cpu().numpy(), rq, bt, "res")
+        e2 = _per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt, "bead")
+        assert max(e1, e2) <= TOL[dtype], (e1, e2)
+    ctx.close()
+
+
+def test_pipeline_single_products_match_pair():
+    """Only Q~v, only Q~^T w, and both at once give the same bits."""
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=9, nmin=30, nmax=900, seed=5)
+    rng = np.random.default_rng(8)
+    x, y, z = (torch.from_numpy(a.copy()).to(dev) for a in (bt.x, bt.y, bt.z))
+    v = torch.from_numpy(rng.standard_normal((3, bt.N))).to(dev, torch.float32)
+    w = torch.from_numpy(rng.standard_normal(bt.n_residues)).to(dev, torch.float32)
+    out = {}
+    for mode in ("both", "v", "w"):
+        ctx = zq.Context(0)
+        qv = torch.full((bt.n_residues,), float("nan"), device=dev)
+        qtw = torch.full((3, bt.N), float("nan"), device=dev)
+        ctx.pipeline(bt.off, x, y, z, v if mode != "w" else None, qv if mode != "w" else None,
+                     w if mode != "v" else None, qtw if mode != "v" else None)
+        ctx.sync()
+        out[mode] = (qv.cpu(), qtw.cpu())
+        ctx.close()
+    assert torch.equal(out["both"][0], out["v"][0])
+    assert torch.equal(out["both"][1], out["w"][1])
+
+
+def _projector_residual(P, f, off):
+    """|f - Z^T (Z Z^T)^-1 Z f| per body, P (N, 3) positions, f (N, 3)."""
+    res = np.empty_like(f)
+    for j in range(len(off) - 1):
+        a, b = off[j], off[j + 1]
+        p = P[a:b] - P[a:b].mean(0)
+        g = f[a:b]
+        J = (p * p).sum() * np.eye(3) - p.T @ p
+        om = np.linalg.solve(J, np.cross(p, g).sum(0))
+        res[a:b] = g - (g.mean(0) + np.cross(om, p))
+    return res
+
+
+def test_pipeline_keep_tree_after_rigid_motion():
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=12, nmin=40, nmax=1200, seed=13)
+    qs, ts = W.random_rigid_motions(bt.m, 1, seed=4)
+    P = np.stack([bt.x, bt.y, bt.z], 1)
+    Pm = P.copy()
+    for j in range(bt.m):
+        a, b = bt.off[j], bt.off[j + 1]
+        q0, q1, q2, q3 = qs[0, j]
+        R = np.array([[q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 - q0 * q3), 2 * (q1 * q3 + q0 * q2)],
+                      [2 * (q1 * q2 + q0 * q3), q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3, 2 * (q2 * q3 - q0 * q1)],
+                      [2 * (q1 * q3 - q0 * q2), 2 * (q2 * q3 + q0 * q1), q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3]])
+        c = P[a:b].mean(0)
+        Pm[a:b] = (P[a:b] - c) @ R.T + c + ts[0, j]
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    x0, y0, z0 = d(P[:, 0]), d(P[:, 1]), d(P[:, 2])
+    x1, y1, z1 = d(Pm[:, 0]), d(Pm[:, 1]), d(Pm[:, 2])
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((3, bt.N))
+    v = d(f)
+    ctx = zq.Context(0)
+    qv = torch.empty(bt.n_residues, dtype=torch.float64, device=dev)
+    out = torch.empty((3, bt.N), dtype=torch.float64, device=dev)
+    ctx.pipeline(bt.off, x0, y0, z0, v, qv)                      # tree from the original positions
+    ctx.pipeline(bt.off, x1, y1, z1, v, qv, keep_tree=True)      # moved beads, kept tree
+    ctx.apply_QT(qv, out)
+    ctx.sync()
+    ref = zq.Context(0)
+    ref.build_tree_batched(bt.off, x0, y0, z0)
+    ref.build_transforms(x1, y1, z1)
+    rqv = ref.apply_Q(v)
+    ref.sync()
+    assert torch.equal(qv, rqv)
+    got = out.cpu().numpy().T
+    want = _projector_residual(Pm, f.T, bt.off)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(f).max() * 10
+    ctx.close()
+    ref.close()
