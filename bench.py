@@ -492,7 +492,8 @@ def timed(args, fn, stream, flush, world, dev, N, graph=True, steps=None):
 
 def apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev):
     """Q~v + Q~^T w with the transforms already built (as inside a Krylov
-    solve), FP32 and FP64, with the sweep bytes achieved against HBM."""
+    solve), FP32 and FP64, through zq_apply_pair (the two sweeps run
+    concurrently), with the sweep bytes achieved against HBM."""
     import torch
 
     N, R, m = bt.N, bt.n_residues, bt.m
@@ -510,8 +511,7 @@ def apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev):
         stream.synchronize()
 
         def fn():
-            ctx.apply_Q(vv, oq)
-            ctx.apply_QT(ww, oqt)
+            ctx.apply_pair(vv, ww, oq, oqt)
 
         r = timed(args, fn, stream, flush, world, dev, N, graph=not args.no_graph)
         byt = 2 * sweep_bytes(census, N, R, es)

@@ -128,6 +128,13 @@ zq_status zq_apply_Q(zq_ctx *ctx, zq_prec prec, int64_t k, const void *v, int64_
 zq_status zq_apply_QT(zq_ctx *ctx, zq_prec prec, int64_t k, const void *w, int64_t ldw,
                       void *out, int64_t ldo);
 
+/* qv = Q~ v and qtw = Q~^T w for one column each (Algorithms 2 and 3), the
+ * two sweeps running concurrently (Q~^T w on a stream forked from and
+ * joined back into the context stream, with its own scratch).  Layouts as
+ * for zq_apply_Q / zq_apply_QT with ldv = 3N, ldw = R.  Does not allocate;
+ * ZQ_ESTATE before the transforms of this precision exist. */
+zq_status zq_apply_pair(zq_ctx *ctx, zq_prec prec, const void *v, void *qv, const void *w, void *qtw);
+
 /* ------------------------------------------------------------------------
  * Block form: k right-hand sides at once (the same node transforms applied
  * to k-column blocks; Algorithms 2 and 3 column by column).

@@ -347,6 +347,32 @@ zq_status zq_apply_QT(zq_ctx* ctx, zq_prec prec, int64_t k, const void* w, int64
   return ZQ_OK;
 }
 
+zq_status zq_apply_pair(zq_ctx* ctx, zq_prec prec, const void* v, void* qv, const void* w, void* qtw) {
+  if (!ctx || !v || !qv || !w || !qtw) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  c.time_started = false;
+  if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  // the two products are independent: Q~^T w on a side stream (with its
+  // own scratch) while Q~ v runs on the context stream, joined after
+  ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+  ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[0], c.fork_ev, 0));
+  ZQ_TRY(zq::launch_apply_Q(c, prec, v, 3 * c.N, qv));
+  cudaStream_t main = c.stream;
+  std::swap(c.x32, c.x32b);
+  std::swap(c.x64, c.x64b);
+  c.stream = c.side[0];
+  const zq_status st = zq::launch_apply_QT(c, prec, w, qtw, 3 * c.N);
+  c.stream = main;
+  std::swap(c.x32, c.x32b);
+  std::swap(c.x64, c.x64b);
+  ZQ_TRY(st);
+  ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[0], c.side[0]));
+  ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[0], 0));
+  return ZQ_OK;
+}
+
 zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
                       const double* y, const double* z, const void* v, void* qv, const void* w,
                       void* qtw, int32_t level_cut, int32_t flags) {
@@ -401,22 +427,7 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
   c.have64 = prec == ZQ_FP64;
   c.have32 = prec == ZQ_FP32;
   if (dv && dw) {
-    // the two products are independent: Q~^T w on a side stream (with its
-    // own scratch) while Q~ v runs on the context stream, joined after
-    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
-    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[0], c.fork_ev, 0));
-    ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
-    cudaStream_t main = c.stream;
-    std::swap(c.x32, c.x32b);
-    std::swap(c.x64, c.x64b);
-    c.stream = c.side[0];
-    const zq_status st = zq::launch_apply_QT(c, prec, dw, dqtw, 3 * N);
-    c.stream = main;
-    std::swap(c.x32, c.x32b);
-    std::swap(c.x64, c.x64b);
-    ZQ_TRY(st);
-    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[0], c.side[0]));
-    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[0], 0));
+    ZQ_TRY(zq_apply_pair(ctx, prec, dv, dqv, dw, dqtw));
   } else {
     if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
     if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));

@@ -80,6 +80,8 @@ def _lib() -> ctypes.CDLL:
         L.zq_set_build_arith.argtypes = [_vp, ctypes.c_int]
         L.zq_launch_count.restype = ctypes.c_int
         L.zq_launch_count.argtypes = [_vp, _i64p]
+        L.zq_apply_pair.restype = ctypes.c_int
+        L.zq_apply_pair.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.zq_reserve_block.restype = ctypes.c_int
         L.zq_reserve_block.argtypes = [_vp, ctypes.c_int, _i64]
         for name in ("zq_apply_Q_block", "zq_apply_QT_block"):
@@ -181,6 +183,19 @@ class Context:
         oo = out.reshape(k, R)
         _check(_lib().zq_apply_Q(self._h, self._prec(v), k, _ptr(vv), 3 * N, _ptr(oo), R), "zq_apply_Q")
         return out.reshape(R) if squeeze and out.dim() == 2 else out
+
+    def apply_pair(self, v, w, qv=None, qtw=None):
+        """Q~ v and Q~^T w together (concurrent sweeps): v (3, N), w (R,)."""
+        N, m, R, _ = self.sizes()
+        assert v.is_cuda and w.is_cuda and v.dtype == w.dtype and v.numel() == 3 * N and w.numel() == R
+        assert v.is_contiguous() and w.is_contiguous()
+        if qv is None:
+            qv = self._torch.empty(R, dtype=v.dtype, device=v.device)
+        if qtw is None:
+            qtw = self._torch.empty((3, N), dtype=v.dtype, device=v.device)
+        _check(_lib().zq_apply_pair(self._h, self._prec(v), _ptr(v), _ptr(qv), _ptr(w), _ptr(qtw)),
+               "zq_apply_pair")
+        return qv, qtw
 
     # ------------------------------------------------------- block form
     @staticmethod

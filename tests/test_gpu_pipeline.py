@@ -152,3 +152,22 @@ def test_pipeline_keep_tree_after_rigid_motion():
     assert np.abs(got - want).max() <= 1e-12 * np.abs(f).max() * 10
     ctx.close()
     ref.close()
+
+
+def test_apply_pair_equals_separate_calls():
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=10, nmin=30, nmax=1500, seed=17)
+    x, y, z = (torch.from_numpy(a.copy()).to(dev) for a in (bt.x, bt.y, bt.z))
+    rng = np.random.default_rng(21)
+    ctx = zq.Context(0)
+    ctx.build_tree_batched(bt.off, x, y, z)
+    ctx.build_transforms(x, y, z)
+    for dt in (torch.float32, torch.float64):
+        v = torch.from_numpy(rng.standard_normal((3, bt.N))).to(dev, dt)
+        w = torch.from_numpy(rng.standard_normal(bt.n_residues)).to(dev, dt)
+        qv, qtw = ctx.apply_pair(v, w)
+        rqv, rqtw = ctx.apply_Q(v), ctx.apply_QT(w)
+        ctx.sync()
+        assert torch.equal(qv, rqv) and torch.equal(qtw, rqtw)
+    ctx.close()
