@@ -212,8 +212,7 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
     ZQ_TRY(zq::launch_tree(c, x, y, z));
     return ZQ_OK;
   }
-  const int64_t nblk = (max_big + 4095) / 4096;
-  const int64_t hist_words = 16 * nblk + zq::scan_tmp_words(16 * nblk);
+  const int64_t hist_words = zq::sort_hist_words(max_big);
   ZQ_TRY(ensure_capacity(c, N, m, hist_words));
   c.N = N;
   c.m = m;

@@ -246,6 +246,7 @@ zq_status launch_count_table_dd(Ctx& c);
 int64_t bucket_hist_words(int64_t nodes);
 // zq_sort.cu
 zq_status launch_sort(Ctx& c);
+int64_t sort_hist_words(int64_t n_max);  // histogram + scan workspace of the largest body
 // zq_scan.cu
 zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
                                 int32_t* total);

@@ -3,8 +3,8 @@
 // separated by their index bits).
 //
 // Bodies above kSmallSortMax beads (smaller ones are sorted inside the
-// per-body tree kernel, zq_smalltree.cu): stable LSD radix sort, 16 passes
-// of 4 bits over the 64-bit key; stability keeps equal keys in bead (=
+// per-body tree kernel, zq_smalltree.cu): stable LSD radix sort, 8 passes
+// of 8 bits over the 64-bit key; stability keeps equal keys in bead (=
 // index) order.
 #include "zq_internal.cuh"
 
@@ -13,98 +13,110 @@ namespace zq {
 namespace {
 
 // ------------------------------------------------------------ radix (big)
+// Eight passes of 8-bit digits.  A block owns a tile of kTile keys (kept in
+// shared memory for the pass); warp w owns the w-th slice of the tile, in
+// order.  Counting: per-block histogram.  Scatter: within a warp, lanes
+// with the same digit are ranked by __match_any_sync in lane order, and
+// the slices of a tile follow each other, so equal digits keep their input
+// order (a stable pass); the global position of (digit, tile) comes from
+// a scan of the per-tile histograms (digit-major).
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;
-constexpr int kDigits = 16;
+constexpr int kWarps = kRadixThreads / 32;
+constexpr int kSlice = 512;                 // keys per warp
+constexpr int kTile = kWarps * kSlice;      // 4096 keys per block
+constexpr int kDigits = 256;
 
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_count(const uint64_t* __restrict__ kin, int64_t n, int shift, int32_t* __restrict__ hist,
               int64_t nblk) {
   __shared__ int32_t cnt[kDigits];
-  if (threadIdx.x < kDigits) cnt[threadIdx.x] = 0;
+  cnt[threadIdx.x] = 0;
   __syncthreads();
-  int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)threadIdx.x * kRadixItems;
-  for (int i = 0; i < kRadixItems; ++i) {
-    int64_t e = base + i;
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  for (int i = threadIdx.x; i < kTile; i += kRadixThreads) {
+    const int64_t e = base + i;
     if (e < n) atomicAdd(&cnt[(kin[e] >> shift) & (kDigits - 1)], 1);
   }
   __syncthreads();
-  if (threadIdx.x < kDigits) hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
-}
-
-__device__ inline int32_t blk_excl(int32_t v, int32_t* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t inc = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    int32_t t = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d) inc += t;
-  }
-  if (lane == 31) sh[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    int32_t w = (lane < (kRadixThreads >> 5)) ? sh[lane] : 0;
-    int32_t wi = w;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      int32_t t = __shfl_up_sync(0xffffffffu, wi, d);
-      if (lane >= d) wi += t;
-    }
-    sh[lane] = wi - w;
-  }
-  __syncthreads();
-  int32_t r = inc - v + sh[warp];
-  __syncthreads();
-  return r;
+  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n,
                 int64_t vbase, int shift, const int32_t* __restrict__ hist, int64_t nblk,
                 uint64_t* __restrict__ kout, int32_t* __restrict__ vout) {
-  __shared__ int32_t sh[33];
-  int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)threadIdx.x * kRadixItems;
-  int32_t c[kDigits];
+  __shared__ uint64_t sk[kTile];
+  __shared__ int32_t sv[kTile];
+  __shared__ int32_t whist[kWarps][kDigits];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  const int cnt = (int)(n - base < (int64_t)kTile ? n - base : (int64_t)kTile);
+  for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
+    sk[i] = kin[base + i];
+    sv[i] = vin ? vin[base + i] : (int32_t)(vbase + base + i);
+  }
+  for (int d = lane; d < kDigits; d += 32) whist[warp][d] = 0;
+  __syncthreads();
+  const int c0 = min(cnt, warp * kSlice), c1 = min(cnt, c0 + kSlice);
+  for (int b = c0; b < c1; b += 32) {
+    const int i = b + lane;
+    const bool v = i < c1;
+    const int dg = v ? (int)((sk[i] >> shift) & (kDigits - 1)) : kDigits + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, dg);
+    if (v && (peers & lt) == 0) whist[warp][dg] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // thread d: first output position of (digit d, warp w) for every w
+    const int d = threadIdx.x;
+    int32_t run = hist[(int64_t)d * nblk + blockIdx.x];
 #pragma unroll
-  for (int d = 0; d < kDigits; ++d) c[d] = 0;
-  for (int i = 0; i < kRadixItems; ++i) {
-    int64_t e = base + i;
-    if (e < n) {
-      int d = (int)((kin[e] >> shift) & (kDigits - 1));
-#pragma unroll
-      for (int dd = 0; dd < kDigits; ++dd) c[dd] += (dd == d);
+    for (int w = 0; w < kWarps; ++w) {
+      const int32_t c = whist[w][d];
+      whist[w][d] = run;
+      run += c;
     }
   }
-  int32_t pos[kDigits];
-#pragma unroll
-  for (int d = 0; d < kDigits; ++d)
-    pos[d] = blk_excl(c[d], sh) + hist[(int64_t)d * nblk + blockIdx.x];
-  for (int i = 0; i < kRadixItems; ++i) {
-    int64_t e = base + i;
-    if (e < n) {
-      uint64_t kk = kin[e];
-      int d = (int)((kk >> shift) & (kDigits - 1));
-      int32_t p = 0;
-#pragma unroll
-      for (int dd = 0; dd < kDigits; ++dd)
-        if (dd == d) p = pos[dd]++;
-      kout[p] = kk;
-      vout[p] = vin ? vin[e] : (int32_t)(vbase + e);
+  __syncthreads();
+  for (int b = c0; b < c1; b += 32) {
+    const int i = b + lane;
+    const bool v = i < c1;
+    uint64_t k = 0;
+    int32_t val = 0;
+    int dg = kDigits + lane;
+    if (v) {
+      k = sk[i];
+      val = sv[i];
+      dg = (int)((k >> shift) & (kDigits - 1));
     }
+    const unsigned peers = __match_any_sync(0xffffffffu, dg);
+    if (v) {
+      const int32_t pos = whist[warp][dg] + __popc(peers & lt);
+      kout[pos] = k;
+      vout[pos] = val;
+    }
+    __syncwarp();
+    if (v && (peers & lt) == 0) whist[warp][dg] += __popc(peers);
+    __syncwarp();
   }
 }
 
 }  // namespace
 
+int64_t sort_hist_words(int64_t n_max) {
+  const int64_t nblk = (n_max + kTile - 1) / kTile;
+  return kDigits * nblk + scan_tmp_words(kDigits * nblk);
+}
+
 zq_status launch_sort(Ctx& c) {
   cudaStream_t s = c.stream;
   for (int32_t j : c.big_bodies) {
     int64_t o = c.off_h[j], n = c.off_h[j + 1] - o;
-    int64_t nblk = (n + kRadixTile - 1) / kRadixTile;
+    int64_t nblk = (n + kTile - 1) / kTile;
     int32_t* hist = c.sort_hist;
     int32_t* tmp = c.sort_hist + kDigits * nblk;
-    for (int pass = 0; pass < 16; ++pass) {
+    for (int pass = 0; pass < 8; ++pass) {
       const uint64_t* kin;
       const int32_t* vin;
       uint64_t* kout;
@@ -116,7 +128,7 @@ zq_status launch_sort(Ctx& c) {
       } else {
         kin = c.skey + o; vin = c.perm + o; kout = c.key_tmp + o; vout = c.perm_tmp + o;
       }
-      int shift = 4 * pass;
+      int shift = 8 * pass;
       time_begin(c, "sort_radix_count");
       k_radix_count<<<(unsigned)nblk, kRadixThreads, 0, s>>>(kin, n, shift, hist, nblk);
       time_end(c, "sort_radix_count");
