@@ -344,21 +344,33 @@ __device__ __forceinline__ void load_bead(const SweepArgs<T>& a, int32_t code, T
 }
 
 template <typename T>
+__device__ __forceinline__ void up_top_node(const SweepArgs<T>& a, int32_t p) {
+  const int2 cc = a.pc[p];
+  T X[6], Y[6], P[6];
+  if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X);
+  if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y);
+  up_dispatch(a, a.prw[p], a.proff[p], cc, X, Y, P);
+  store6(a.xs + 6 * (int64_t)p, P);
+}
+
+// Body blockIdx.x's top nodes, height by height (sorted by height in
+// shared memory; bodies with more than kHeightSorted top nodes scan their
+// list at every height).
+template <typename T>
 __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
-  __shared__ int lim[2];
+  __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
-  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
-  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
-  for (int h = lim[0]; h <= lim[1]; ++h) {
-    for (int32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-      const int32_t p = a.topv[t];
-      if (a.ph[p] != h) continue;
-      const int2 cc = a.pc[p];
-      T X[6], Y[6], P[6];
-      if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X);
-      if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y);
-      up_dispatch(a, a.prw[p], a.proff[p], cc, X, Y, P);
-      store6(a.xs + 6 * (int64_t)p, P);
+  const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
+  if (n == 0) return;
+  const int32_t* list = a.topv + t0;
+  const uint8_t* ph = a.ph;
+  const bool sorted = sort_by_height(n, [&](int32_t t) { const int32_t p = list[t]; return make_int2(p, ph[p]); }, S);
+  for (int h = S.lim[0]; h <= S.lim[1]; ++h) {
+    if (sorted) {
+      for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x) up_top_node(a, S.ids[k]);
+    } else {
+      for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
+        if (ph[list[t]] == h) up_top_node(a, list[t]);
     }
     __syncthreads();
   }
@@ -384,29 +396,41 @@ __device__ __forceinline__ void store_bead(const SweepArgs<T>& a, int32_t code, 
   a.out[2 * a.N + b] = L[2];
 }
 
+template <typename T>
+__device__ __forceinline__ void down_top_node(const SweepArgs<T>& a, int32_t p, bool root) {
+  const int2 cc = a.pc[p];
+  T Lp[6], Lx[6], Ly[6];
+  if (root) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Lp[k] = T(0);
+  } else {
+    load6(a.xs + 6 * (int64_t)p, Lp);
+  }
+  down_dispatch(a, a.prw[p], a.proff[p], cc, Lp, Lx, Ly);
+  if (cc.x >= 0) store6(a.xs + 6 * (int64_t)cc.x, Lx); else store_bead(a, cc.x, Lx);
+  if (cc.y >= 0) store6(a.xs + 6 * (int64_t)cc.y, Ly); else store_bead(a, cc.y, Ly);
+}
+
 // Runs first: for every body with top nodes, the root Velocity-set is 0,
-// then the top nodes from the root down.
+// then the top nodes from the root down (the root: the only top node of
+// the largest height).
 template <typename T>
 __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
-  __shared__ int lim[2];
+  __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
-  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
-  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
-  for (int h = lim[1]; h >= lim[0]; --h) {
-    for (int32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-      const int32_t p = a.topv[t];
-      if (a.ph[p] != h) continue;
-      const int2 cc = a.pc[p];
-      T Lp[6], Lx[6], Ly[6];
-      if (h == lim[1]) {  // the body root
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Lp[k] = T(0);
-      } else {
-        load6(a.xs + 6 * (int64_t)p, Lp);
-      }
-      down_dispatch(a, a.prw[p], a.proff[p], cc, Lp, Lx, Ly);
-      if (cc.x >= 0) store6(a.xs + 6 * (int64_t)cc.x, Lx); else store_bead(a, cc.x, Lx);
-      if (cc.y >= 0) store6(a.xs + 6 * (int64_t)cc.y, Ly); else store_bead(a, cc.y, Ly);
+  const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
+  if (n == 0) return;
+  const int32_t* list = a.topv + t0;
+  const uint8_t* ph = a.ph;
+  const bool sorted = sort_by_height(n, [&](int32_t t) { const int32_t p = list[t]; return make_int2(p, ph[p]); }, S);
+  const int hmax = S.lim[1];
+  for (int h = hmax; h >= S.lim[0]; --h) {
+    if (sorted) {
+      for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x)
+        down_top_node(a, S.ids[k], h == hmax);
+    } else {
+      for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
+        if (ph[list[t]] == h) down_top_node(a, list[t], h == hmax);
     }
     __syncthreads();
   }

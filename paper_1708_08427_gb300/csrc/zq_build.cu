@@ -434,12 +434,22 @@ __global__ void __launch_bounds__(kThreads) k_build_tail(BuildArgs a) {
   int32_t lo, hi;
   id_range(a.sid, t0, t1, a.off[j] - j, a.off[j + 1] - (j + 1), &lo, &hi);
   if (lo == hi) return;
-  const int H = a.sheight[a.root_slot[j]];
-  for (int h = a.cut + 1; h <= H; ++h) {
-    for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
-      if (a.sheight[s] != h) continue;
-      const int2 cc = a.sc[s];
-      build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
+  __shared__ HeightSort S;
+  const uint8_t* sh = a.sheight;
+  const bool sorted = sort_by_height(hi - lo, [&](int32_t t) { return make_int2(lo + t, sh[lo + t]); }, S);
+  for (int h = S.lim[0]; h <= S.lim[1]; ++h) {
+    if (sorted) {
+      for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x) {
+        const int32_t s = S.ids[k];
+        const int2 cc = a.sc[s];
+        build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
+      }
+    } else {
+      for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+        if (sh[s] != h) continue;
+        const int2 cc = a.sc[s];
+        build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
+      }
     }
     __syncthreads();
   }

@@ -213,6 +213,58 @@ __device__ inline int32_t body_of_node(const int64_t* __restrict__ off, int64_t 
   return (int32_t)lo;
 }
 
+// Block-local counting sort of up to kHeightSorted items by height (order
+// within a height arbitrary).  item(t) -> (id, height) for t in [0, n).
+// On return (true): ids[k] in height order, hs[h] = first k of height h
+// (hs[h + 1] its end), lim = {lowest, highest height}.  n > kHeightSorted:
+// returns false (lim still set) and the caller scans instead.  All threads
+// of the block must call.
+constexpr int kHeightSorted = 4096;
+struct HeightSort {
+  int32_t ids[kHeightSorted];
+  int32_t hs[kMaxHeight + 2];
+  int lim[2];
+};
+
+template <class Item>
+__device__ bool sort_by_height(int32_t n, Item item, HeightSort& S) {
+  __syncthreads();  // S may still be read from a previous use
+  for (int h = threadIdx.x; h < kMaxHeight + 2; h += blockDim.x) S.hs[h] = 0;
+  if (threadIdx.x == 0) {
+    S.lim[0] = kMaxHeight + 1;
+    S.lim[1] = 0;
+  }
+  __syncthreads();
+  for (int32_t t = threadIdx.x; t < n; t += blockDim.x) {
+    const int h = item(t).y;
+    atomicAdd(&S.hs[h], 1);
+    atomicMin(&S.lim[0], h);
+    atomicMax(&S.lim[1], h);
+  }
+  __syncthreads();
+  if (n > kHeightSorted) return false;
+  if (threadIdx.x == 0) {
+    int32_t run = 0;
+    for (int h = 0; h < kMaxHeight + 2; ++h) {
+      const int32_t v = S.hs[h];
+      S.hs[h] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int32_t t = threadIdx.x; t < n; t += blockDim.x) {
+    const int2 it = item(t);
+    S.ids[atomicAdd(&S.hs[it.y], 1)] = it.x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // hs[h] is now the end of height h: shift back
+    for (int h = kMaxHeight + 1; h > 0; --h) S.hs[h] = S.hs[h - 1];
+    S.hs[0] = 0;
+  }
+  __syncthreads();
+  return true;
+}
+
 // Orderable unsigned encoding of a double (for atomicMin/Max).
 __device__ inline unsigned long long ord_encode(double d) {
   unsigned long long u = (unsigned long long)__double_as_longlong(d);
