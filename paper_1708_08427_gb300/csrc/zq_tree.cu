@@ -40,8 +40,22 @@ __global__ void k_aabb(const double* __restrict__ x, const double* __restrict__ 
   const bool mine = j >= 0;
   double p[3] = {mine ? x[i] : 0.0, mine ? y[i] : 0.0, mine ? z[i] : 0.0};
   if (mine && !(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(err, kErrNonFinite);
+  // a block whose beads all belong to one large body reduces in shared
+  // memory and issues one atomic per axis; otherwise per warp or per bead
+  __shared__ int32_t jb[2];
+  __shared__ unsigned long long wmn[3][32], wmx[3][32];
+  if (threadIdx.x == 0) {
+    jb[0] = 0x7fffffff;
+    jb[1] = -2;
+  }
+  __syncthreads();
+  atomicMin(&jb[0], mine ? j : -1);
+  atomicMax(&jb[1], mine ? j : -1);
+  __syncthreads();
+  const bool block_uniform = jb[0] == jb[1] && jb[0] >= 0;
   const int32_t j0 = __shfl_sync(0xffffffffu, j, 0);
   const bool uniform = __all_sync(0xffffffffu, j == j0) && j0 >= 0;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     unsigned long long e = mine ? ord_encode(p[a]) : 0ull;
@@ -54,13 +68,31 @@ __global__ void k_aabb(const double* __restrict__ x, const double* __restrict__ 
         mn = omn < mn ? omn : mn;
         mx = omx > mx ? omx : mx;
       }
-      if (lane == 0) {
+      if (block_uniform) {
+        if (lane == 0) {
+          wmn[a][warp] = mn;
+          wmx[a][warp] = mx;
+        }
+      } else if (lane == 0) {
         atomicMin(&lo[3 * j0 + a], mn);
         atomicMax(&hi[3 * j0 + a], mx);
       }
     } else if (mine) {
       atomicMin(&lo[3 * j + a], e);
       atomicMax(&hi[3 * j + a], e);
+    }
+  }
+  if (block_uniform) {
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const int a = threadIdx.x;
+      unsigned long long mn = wmn[a][0], mx = wmx[a][0];
+      for (int w = 1; w < nwarps; ++w) {
+        mn = wmn[a][w] < mn ? wmn[a][w] : mn;
+        mx = wmx[a][w] > mx ? wmx[a][w] : mx;
+      }
+      atomicMin(&lo[3 * jb[0] + a], mn);
+      atomicMax(&hi[3 * jb[0] + a], mx);
     }
   }
 }
