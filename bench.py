@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--workload", choices=["shells2000", "ellipsoid"], default="shells2000")
     ap.add_argument("--bodies", type=int, default=2000,
                     help="bodies of the shell workload (smaller values: profiling captures)")
-    ap.add_argument("--cut", type=int, default=15, help="level cut (performance only)")
+    ap.add_argument("--cut", type=int, default=0,
+                    help="level cut (performance only); 0: chosen by the autotuner on this workload")
     ap.add_argument("--build", choices=["dd", "fp64"], default="dd",
                     help="node-transform arithmetic: double-single on FP32 pipes or native FP64")
     ap.add_argument("--no-graph", action="store_true")
@@ -290,6 +291,11 @@ def run_ours(args, world, rank, local):
     _XYZ[id(bt)] = (x, y, z)
     ctx = zq.Context(local, stream=stream)
     ctx.set_build_arith(args.build)
+    tuned = None
+    if args.cut == 0:  # the level schedule chosen by timing the step itself
+        from paper_1708_08427_gb300.tune import tune_level_cut
+
+        args.cut, tuned = tune_level_cut(ctx, bt.off, x, y, z, v, qv, w, qtw)
 
     def step(prec_t=torch.float32, vv=v, ww=w, oq=qv, oqt=qtw):
         ctx.pipeline(bt.off, x, y, z, vv, oq, ww, oqt, level_cut=args.cut)
@@ -401,6 +407,7 @@ def run_ours(args, world, rank, local):
         "dtype": "f32 sweeps; transforms " + ("double-single (2 x f32, ~48-bit)" if args.build == "dd" else "f64"),
         "data": "synthetic (seeded numpy generators; no dataset)",
         "config": {"workload": desc, "m": m, "N": N, "residues": R, "level_cut": args.cut,
+                   "level_cut_tuning_ms": tuned,
                    "graph": False, "prec": "fp32", "build": args.build,
                    "step": "tree + FP64 transforms + Q~v + Q~^T w (one C-ABI call, zq_pipeline)",
                    "l2": "512 MB buffer written before every step, outside the step events",

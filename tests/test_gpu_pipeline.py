@@ -171,3 +171,20 @@ def test_apply_pair_equals_separate_calls():
         ctx.sync()
         assert torch.equal(qv, rqv) and torch.equal(qtw, rqtw)
     ctx.close()
+
+
+def test_level_cut_tuner_picks_a_candidate():
+    from paper_1708_08427_gb300.tune import tune_level_cut
+
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=16, nmin=30, nmax=2000, seed=23)
+    x, y, z = (torch.from_numpy(a.copy()).to(dev) for a in (bt.x, bt.y, bt.z))
+    v = torch.zeros((3, bt.N), device=dev)
+    w = torch.zeros(bt.n_residues, device=dev)
+    qv = torch.empty(bt.n_residues, device=dev)
+    qtw = torch.empty((3, bt.N), device=dev)
+    ctx = zq.Context(0)
+    best, times = tune_level_cut(ctx, bt.off, x, y, z, v, qv, w, qtw, cuts=(4, 15), reps=2, warmup=1)
+    assert best in (4, 15) and set(times) == {4, 15} and all(t > 0 for t in times.values())
+    ctx.close()
