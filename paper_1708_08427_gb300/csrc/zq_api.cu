@@ -43,7 +43,7 @@ void free_all(Ctx& c) {
 }
 
 void destroy_streams(Ctx& c) {
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (c.side[i]) {
       cudaStreamSynchronize(c.side[i]);
       cudaStreamDestroy(c.side[i]);
@@ -164,7 +164,7 @@ zq_status zq_create(zq_ctx** ctx, int device, void* cuda_stream) {
     return ZQ_ECUDA;
   }
   bool ok = cudaEventCreateWithFlags(&h->c.fork_ev, cudaEventDisableTiming) == cudaSuccess;
-  for (int i = 0; i < 3 && ok; ++i) {
+  for (int i = 0; i < 4 && ok; ++i) {
     ok = cudaStreamCreateWithFlags(&h->c.side[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&h->c.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
   }
@@ -408,11 +408,17 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
     char* sqtw = sv + 3 * N * es;
     char* sw = sqtw + 3 * N * es;
     char* sqv = sw + R * es;
+    // coordinates first on the context stream (the tree needs them); the
+    // vectors on a side stream, overlapping the tree and the transforms,
+    // joined before the sweeps
+    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[3], c.fork_ev, 0));
     ZQ_CUDA_TRY(cudaMemcpyAsync(sx, x, N * 8, cudaMemcpyHostToDevice, c.stream));
     ZQ_CUDA_TRY(cudaMemcpyAsync(sy, y, N * 8, cudaMemcpyHostToDevice, c.stream));
     ZQ_CUDA_TRY(cudaMemcpyAsync(sz, z, N * 8, cudaMemcpyHostToDevice, c.stream));
-    if (v) ZQ_CUDA_TRY(cudaMemcpyAsync(sv, v, 3 * N * es, cudaMemcpyHostToDevice, c.stream));
-    if (w) ZQ_CUDA_TRY(cudaMemcpyAsync(sw, w, R * es, cudaMemcpyHostToDevice, c.stream));
+    if (v) ZQ_CUDA_TRY(cudaMemcpyAsync(sv, v, 3 * N * es, cudaMemcpyHostToDevice, c.side[3]));
+    if (w) ZQ_CUDA_TRY(cudaMemcpyAsync(sw, w, R * es, cudaMemcpyHostToDevice, c.side[3]));
+    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[3], c.side[3]));
     dx = sx; dy = sy; dz = sz;
     dv = v ? sv : nullptr;
     dw = w ? sw : nullptr;
@@ -425,15 +431,33 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
   c.have_xform = true;
   c.have64 = prec == ZQ_FP64;
   c.have32 = prec == ZQ_FP32;
+  if (host) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[3], 0));  // the vectors are in
   if (dv && dw) {
-    ZQ_TRY(zq_apply_pair(ctx, prec, dv, dqv, dw, dqtw));
+    // Q~v on the context stream, Q~^T w concurrently on a side stream; with
+    // host buffers qv goes back while Q~^T w still runs
+    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[0], c.fork_ev, 0));
+    ZQ_TRY(zq::launch_apply_Q(c, prec, dv, 3 * N, dqv));
+    if (host) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));
+    cudaStream_t main = c.stream;
+    std::swap(c.x32, c.x32b);
+    std::swap(c.x64, c.x64b);
+    c.stream = c.side[0];
+    const zq_status st = zq::launch_apply_QT(c, prec, dw, dqtw, 3 * N);
+    c.stream = main;
+    std::swap(c.x32, c.x32b);
+    std::swap(c.x64, c.x64b);
+    ZQ_TRY(st);
+    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[0], c.side[0]));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[0], 0));
+    if (host) ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
   } else {
     if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
     if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));
-  }
-  if (host) {
-    if (qv) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));
-    if (qtw) ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
+    if (host) {
+      if (qv) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));
+      if (qtw) ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
+    }
   }
   return ZQ_OK;
 }

@@ -62,11 +62,12 @@ constexpr int kErrDegenerate = 2;
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  // side streams for concurrent per-body tree launches (forked from and
-  // joined back into `stream` with events, so graph capture sees one DAG)
-  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  // side streams forked from and joined back into `stream` with events (so
+  // graph capture sees one DAG): 0..2 concurrent per-body tree launches
+  // (0 also Q~^T w next to Q~ v), 3 host-to-device copies of the vectors
+  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork_ev = nullptr;
-  cudaEvent_t join_ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   int num_sms = 0;
   // sizes of the allocated buffers
   int64_t cap_N = 0, cap_m = 0;
