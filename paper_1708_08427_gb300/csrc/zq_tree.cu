@@ -433,8 +433,16 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
     st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
     if (st != ZQ_OK) return st;
   }
+  // The sweep schedule (segments) and the build schedule (buckets) only
+  // read the tree: the former runs on a side stream next to the latter,
+  // joined before the slot data, which needs both.
+  ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, s));
+  ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[1], c.fork_ev, 0));
+  c.stream = c.side[1];
   st = launch_segments(c);
+  c.stream = s;
   if (st != ZQ_OK) return st;
+  ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[1], c.side[1]));
   // schedule of the build
   const int nb = 3 * c.cut + 1;
   const int64_t nblk = (c.nodes + kBTile - 1) / kBTile;
@@ -454,6 +462,7 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   time_begin(c, "schedule");
   k_bucket_starts<<<1, 128, 0, s>>>(hist, nblk, nb, c.nodes, c.bstart, c.brec);
   time_end(c, "schedule");
+  ZQ_CUDA_TRY(cudaStreamWaitEvent(s, c.join_ev[1], 0));
   time_begin(c, "schedule");
   k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.roff, c.cnt,
                                                    c.height, c.pos_of, c.prw, c.sc, c.sroff, c.scnt,
