@@ -53,10 +53,6 @@ struct SweepArgs {
   T* out;                  // up: residues; down: bead planes
 };
 
-template <typename T> struct V4;
-template <> struct V4<float> { using type = float4; };
-template <> struct V4<double> { using type = double2; };
-
 // Load W words of a record (16-byte vector loads, read-only path).
 template <typename T, int W>
 __device__ __forceinline__ void load_rec(const T* __restrict__ g, T (&r)[W]) {

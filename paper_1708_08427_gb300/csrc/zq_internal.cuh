@@ -119,7 +119,6 @@ struct Ctx {
   int32_t* scnt = nullptr;       // [nodes] beads below
   uint8_t* sheight = nullptr;    // [nodes] height
   int32_t* bstart = nullptr;     // [kMaxBuckets + 1] first slot of each bucket
-  int32_t* brec = nullptr;       // [kMaxBuckets + 1] first record word of each bucket
   int32_t* bhist = nullptr;      // bucket-sort histograms
   int64_t bhist_cap = 0;
   // segments (see kSegMax), by position p (node id order with each segment
@@ -200,16 +199,6 @@ __device__ inline int32_t body_of_bead(const int64_t* __restrict__ off, int64_t 
   while (lo < hi) {
     int64_t mid = (lo + hi + 1) >> 1;
     if (off[mid] <= i) lo = mid; else hi = mid - 1;
-  }
-  return (int32_t)lo;
-}
-
-// Body of an internal node id: largest j with off[j] - j <= q.
-__device__ inline int32_t body_of_node(const int64_t* __restrict__ off, int64_t m, int64_t q) {
-  int64_t lo = 0, hi = m - 1;
-  while (lo < hi) {
-    int64_t mid = (lo + hi + 1) >> 1;
-    if (off[mid] - mid <= q) lo = mid; else hi = mid - 1;
   }
   return (int32_t)lo;
 }

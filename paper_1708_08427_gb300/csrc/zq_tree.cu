@@ -328,21 +328,10 @@ k_bucket_scatter(const uint8_t* __restrict__ height, const int32_t* __restrict__
 }
 
 __global__ void k_bucket_starts(const int32_t* __restrict__ hist, int64_t nblk, int nb, int64_t nodes,
-                                int32_t* __restrict__ bstart, int32_t* __restrict__ brec) {
-  __shared__ int32_t st[kMaxBuckets + 1];
+                                int32_t* __restrict__ bstart) {
   const int b = threadIdx.x;
-  if (b < nb) st[b] = hist[(int64_t)b * nblk];
-  if (b == nb) st[nb] = (int32_t)nodes;
-  __syncthreads();
-  if (b <= nb) bstart[b] = st[b];
-  if (b == 0) {
-    int32_t w = 0;
-    for (int k = 0; k < nb; ++k) {
-      brec[k] = w;
-      w += (st[k + 1] - st[k]) * (k == nb - 1 ? kRecMax : rec_words(k % 3));
-    }
-    brec[nb] = w;
-  }
+  if (b < nb) bstart[b] = hist[(int64_t)b * nblk];
+  if (b == nb) bstart[nb] = (int32_t)nodes;
 }
 
 __global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
@@ -460,7 +449,7 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
                                                          nblk, c.sid, c.slot_of);
   time_end(c, "schedule");
   time_begin(c, "schedule");
-  k_bucket_starts<<<1, 128, 0, s>>>(hist, nblk, nb, c.nodes, c.bstart, c.brec);
+  k_bucket_starts<<<1, 128, 0, s>>>(hist, nblk, nb, c.nodes, c.bstart);
   time_end(c, "schedule");
   ZQ_CUDA_TRY(cudaStreamWaitEvent(s, c.join_ev[1], 0));
   time_begin(c, "schedule");
