@@ -128,6 +128,20 @@ zq_status zq_apply_Q(zq_ctx *ctx, zq_prec prec, int64_t k, const void *v, int64_
 zq_status zq_apply_QT(zq_ctx *ctx, zq_prec prec, int64_t k, const void *w, int64_t ldw,
                       void *out, int64_t ldo);
 
+/* The whole orthogonal Q = [Q_Z; Q~] of every body (Sec. 3: the rows of
+ * Q_Z = [I_n / sqrt(n); U] span Z's rows, Eq. 3.3; Q~ its complement).
+ * zq_apply_Q_full: out = Q~ v as zq_apply_Q (one column), and
+ *   root[6 j + i] = (Q_Z^j v)_i, the root Info-set [t; r] of body j (Eq. 4.4:
+ *   t = sum of the body's bead vectors / sqrt(n_j), r the rotational part).
+ * zq_apply_QT_full: out = Q~^T w + Q_Z^T root, the downward pass of
+ *   Algorithm 3 started from the root Velocity-sets root[6 j ..] instead of
+ *   zero (Theorem 4.3).
+ * For every v: Q_Z^T (Q_Z v) + Q~^T (Q~ v) = v.  root: DEVICE, 6 m values of
+ * the precision's type.  Does not allocate; ZQ_ESTATE before the transforms
+ * of this precision exist. */
+zq_status zq_apply_Q_full(zq_ctx *ctx, zq_prec prec, const void *v, void *out, void *root);
+zq_status zq_apply_QT_full(zq_ctx *ctx, zq_prec prec, const void *w, const void *root, void *out);
+
 /* qv = Q~ v and qtw = Q~^T w for one column each (Algorithms 2 and 3), the
  * two sweeps running concurrently (Q~^T w on a stream forked from and
  * joined back into the context stream, with its own scratch).  Layouts as

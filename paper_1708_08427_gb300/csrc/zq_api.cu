@@ -288,6 +288,26 @@ zq_status zq_apply_Q(zq_ctx* ctx, zq_prec prec, int64_t k, const void* v, int64_
   return ZQ_OK;
 }
 
+zq_status zq_apply_Q_full(zq_ctx* ctx, zq_prec prec, const void* v, void* out, void* root) {
+  if (!ctx || !v || !out || !root) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  c.time_started = false;
+  if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  return zq::launch_apply_Q(c, prec, v, 3 * c.N, out, root);
+}
+
+zq_status zq_apply_QT_full(zq_ctx* ctx, zq_prec prec, const void* w, const void* root, void* out) {
+  if (!ctx || !w || !out || !root) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  c.time_started = false;
+  if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  return zq::launch_apply_QT(c, prec, w, out, 3 * c.N, root);
+}
+
 zq_status zq_reserve_block(zq_ctx* ctx, zq_prec prec, int64_t k_max) {
   if (!ctx || k_max < 1) return ZQ_EINVAL;
   if (prec != ZQ_FP32 && prec != ZQ_FP64 && prec != ZQ_BF16) return ZQ_EINVAL;

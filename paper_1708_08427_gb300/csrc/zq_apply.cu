@@ -51,6 +51,9 @@ struct SweepArgs {
   T* xs;                   // Info-/Velocity-sets of segment roots and top nodes, by position
   const T* in;             // up: bead planes; down: residues
   T* out;                  // up: residues; down: bead planes
+  const int32_t* bead_body;  // sorted position -> body
+  T* root_out;             // up: the root Info-set [t; r] = Q_Z v per body (6 m), or null
+  const T* root_in;        // down: the root Velocity-set per body (6 m), or null (zero)
 };
 
 // Load W words of a record (16-byte vector loads, read-only path).
@@ -309,6 +312,8 @@ __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
       __syncthreads();
     }
     if (!sg.w && threadIdx.x < 6) a.xs[6 * (int64_t)(p0 + nn - 1) + threadIdx.x] = info[6 * (nn - 1) + threadIdx.x];
+    if (sg.w && a.root_out && threadIdx.x < 6)  // a whole body: its root Info-set is Q_Z v
+      a.root_out[6 * (int64_t)a.bead_body[f] + threadIdx.x] = info[6 * (nn - 1) + threadIdx.x];
     __syncthreads();
   }
 }
@@ -340,13 +345,14 @@ __device__ __forceinline__ void load_bead(const SweepArgs<T>& a, int32_t code, T
 }
 
 template <typename T>
-__device__ __forceinline__ void up_top_node(const SweepArgs<T>& a, int32_t p) {
+__device__ __forceinline__ void up_top_node(const SweepArgs<T>& a, int32_t p, bool root) {
   const int2 cc = a.pc[p];
   T X[6], Y[6], P[6];
   if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X);
   if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y);
   up_dispatch(a, a.prw[p], a.proff[p], cc, X, Y, P);
   store6(a.xs + 6 * (int64_t)p, P);
+  if (root && a.root_out) store6(a.root_out + 6 * (int64_t)blockIdx.x, P);  // Q_Z v of body blockIdx.x
 }
 
 // Body blockIdx.x's top nodes, height by height (sorted by height in
@@ -363,10 +369,11 @@ __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
   const bool sorted = sort_by_height(n, [&](int32_t t) { const int32_t p = list[t]; return make_int2(p, ph[p]); }, S);
   for (int h = S.lim[0]; h <= S.lim[1]; ++h) {
     if (sorted) {
-      for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x) up_top_node(a, S.ids[k]);
+      for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x)
+        up_top_node(a, S.ids[k], h == S.lim[1]);
     } else {
       for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
-        if (ph[list[t]] == h) up_top_node(a, list[t]);
+        if (ph[list[t]] == h) up_top_node(a, list[t], h == S.lim[1]);
     }
     __syncthreads();
   }
@@ -398,7 +405,7 @@ __device__ __forceinline__ void down_top_node(const SweepArgs<T>& a, int32_t p, 
   T Lp[6], Lx[6], Ly[6];
   if (root) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) Lp[k] = T(0);
+    for (int k = 0; k < 6; ++k) Lp[k] = a.root_in ? a.root_in[6 * (int64_t)blockIdx.x + k] : T(0);
   } else {
     load6(a.xs + 6 * (int64_t)p, Lp);
   }
@@ -445,7 +452,9 @@ __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
       prefetch_l2(a.rec + 4 * (int64_t)w0, (w1 - w0) * 4u * (uint32_t)sizeof(T));
     }
     if (threadIdx.x < 6)
-      info[6 * (nn - 1) + threadIdx.x] = sg.w ? T(0) : a.xs[6 * (int64_t)(p0 + nn - 1) + threadIdx.x];
+      info[6 * (nn - 1) + threadIdx.x] =
+          sg.w ? (a.root_in ? a.root_in[6 * (int64_t)a.bead_body[sg.z] + threadIdx.x] : T(0))
+               : a.xs[6 * (int64_t)(p0 + nn - 1) + threadIdx.x];
     const int H = stage_meta(a, p0, nn, M);
     for (int h = H; h >= 1; --h) {
       for (int32_t t = M.hb[h] + threadIdx.x; t < M.hb[h + 1]; t += blockDim.x) {
@@ -701,12 +710,14 @@ SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   a.prw = reinterpret_cast<const uint32_t*>(c.prw);
   a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;
+  a.bead_body = c.bead_body; a.root_out = nullptr; a.root_in = nullptr;
   return a;
 }
 
 template <typename T>
-zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out) {
+zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out, T* root_out) {
   SweepArgs<T> a = make_args<T>(c, rec, xs, v, out);
+  a.root_out = root_out;
   time_begin(c, "up_seg");
   k_up_seg<T><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
   time_end(c, "up_seg");
@@ -718,8 +729,9 @@ zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out) {
 }
 
 template <typename T>
-zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out) {
+zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out, const T* root_in) {
   SweepArgs<T> a = make_args<T>(c, rec, xs, w, out);
+  a.root_in = root_in;
   time_begin(c, "down_top");
   k_down_top<T><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
   time_end(c, "down_top");
@@ -732,16 +744,20 @@ zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out) {
 
 }  // namespace
 
-zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t /*ldv*/, void* out) {
+zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t /*ldv*/, void* out, void* root_out) {
   if (prec == ZQ_FP64)
-    return run_up<double>(c, c.rec64, c.x64, static_cast<const double*>(v), static_cast<double*>(out));
-  return run_up<float>(c, c.rec32, c.x32, static_cast<const float*>(v), static_cast<float*>(out));
+    return run_up<double>(c, c.rec64, c.x64, static_cast<const double*>(v), static_cast<double*>(out),
+                          static_cast<double*>(root_out));
+  return run_up<float>(c, c.rec32, c.x32, static_cast<const float*>(v), static_cast<float*>(out),
+                       static_cast<float*>(root_out));
 }
 
-zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t /*ldo*/) {
+zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t /*ldo*/, const void* root_in) {
   if (prec == ZQ_FP64)
-    return run_down<double>(c, c.rec64, c.x64, static_cast<const double*>(w), static_cast<double*>(out));
-  return run_down<float>(c, c.rec32, c.x32, static_cast<const float*>(w), static_cast<float*>(out));
+    return run_down<double>(c, c.rec64, c.x64, static_cast<const double*>(w), static_cast<double*>(out),
+                            static_cast<const double*>(root_in));
+  return run_down<float>(c, c.rec32, c.x32, static_cast<const float*>(w), static_cast<float*>(out),
+                         static_cast<const float*>(root_in));
 }
 
 zq_status launch_apply_block(Ctx& c, bool up, zq_prec prec, int64_t k, const void* in, void* out) {

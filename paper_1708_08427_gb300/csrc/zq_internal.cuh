@@ -299,8 +299,12 @@ zq_status launch_segments(Ctx& c);
 // which: bit 0 = FP64 records, bit 1 = FP32 records
 zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which);
 // zq_apply.cu
-zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t ldv, void* out);
-zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t ldo);
+// root_out / root_in (6 m values, may be null): the root Info-set Q_Z v of
+// every body / the root Velocity-set fed to Q~^T (null: zero)
+zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t ldv, void* out,
+                         void* root_out = nullptr);
+zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t ldo,
+                          const void* root_in = nullptr);
 // up: out = Q~ V, else out = Q~^T W; rows of k values (see include/zq.h)
 zq_status launch_apply_block(Ctx& c, bool up, zq_prec prec, int64_t k, const void* in, void* out);
 

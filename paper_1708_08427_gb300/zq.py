@@ -80,6 +80,10 @@ def _lib() -> ctypes.CDLL:
         L.zq_set_build_arith.argtypes = [_vp, ctypes.c_int]
         L.zq_launch_count.restype = ctypes.c_int
         L.zq_launch_count.argtypes = [_vp, _i64p]
+        L.zq_apply_Q_full.restype = ctypes.c_int
+        L.zq_apply_Q_full.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+        L.zq_apply_QT_full.restype = ctypes.c_int
+        L.zq_apply_QT_full.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
         L.zq_apply_pair.restype = ctypes.c_int
         L.zq_apply_pair.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.zq_reserve_block.restype = ctypes.c_int
@@ -183,6 +187,28 @@ class Context:
         oo = out.reshape(k, R)
         _check(_lib().zq_apply_Q(self._h, self._prec(v), k, _ptr(vv), 3 * N, _ptr(oo), R), "zq_apply_Q")
         return out.reshape(R) if squeeze and out.dim() == 2 else out
+
+    def apply_Q_full(self, v, out=None, root=None):
+        """Q~ v (R,) and the root Info-sets Q_Z v per body (m, 6); v: (3, N)."""
+        N, m, R, _ = self.sizes()
+        assert v.is_cuda and v.is_contiguous() and v.numel() == 3 * N
+        if out is None:
+            out = self._torch.empty(R, dtype=v.dtype, device=v.device)
+        if root is None:
+            root = self._torch.empty((m, 6), dtype=v.dtype, device=v.device)
+        _check(_lib().zq_apply_Q_full(self._h, self._prec(v), _ptr(v), _ptr(out), _ptr(root)), "zq_apply_Q_full")
+        return out, root
+
+    def apply_QT_full(self, w, root, out=None):
+        """Q~^T w + Q_Z^T root -> (3, N); w: (R,), root: (m, 6)."""
+        N, m, R, _ = self.sizes()
+        assert w.is_cuda and w.is_contiguous() and w.numel() == R
+        assert root.is_cuda and root.is_contiguous() and root.numel() == 6 * m and root.dtype == w.dtype
+        if out is None:
+            out = self._torch.empty((3, N), dtype=w.dtype, device=w.device)
+        _check(_lib().zq_apply_QT_full(self._h, self._prec(w), _ptr(w), _ptr(root), _ptr(out)),
+               "zq_apply_QT_full")
+        return out
 
     def apply_pair(self, v, w, qv=None, qtw=None):
         """Q~ v and Q~^T w together (concurrent sweeps): v (3, N), w (R,)."""
