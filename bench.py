@@ -428,6 +428,7 @@ def run_ours(args, world, rank, local):
         out["e2e"] = e2e(args, ctx, bt, stream, world, dev)
         out["multirhs"] = multirhs(args, stream, flush, world, dev, rank)
         out["bd_loop"] = bd_loop(args, stream, flush, world, dev, rank)
+        out["bd_loop_rotation_reuse"] = bd_loop(args, stream, flush, world, dev, rank, reuse=True)
     if rank == 0 and not args.no_extras:
         out["cpu_baseline"] = cpu_baseline(bt, args.cpu_seconds)
     ctx.close()
@@ -648,15 +649,18 @@ def multirhs(args, stream, flush, world, dev, rank, k=64):
     return res
 
 
-def bd_loop(args, stream, flush, world, dev, rank, steps_in_graph=10):
+def bd_loop(args, stream, flush, world, dev, rank, steps_in_graph=10, reuse=False):
     """Brownian-dynamics style loop on 1000 shells of 1000 beads with the tree
     kept: per step every body gets a rigid motion (unit quaternion from
     normalised N(0, I_4) about its centroid, N(0, 0.1^2) translation; applied
-    with torch as the workload driver), the transforms are rebuilt on the
-    kept tree, and Q~^T (Q~ f) is computed in FP32 for an N(0, 1) force f.
-    The loop is captured in a CUDA graph (steps_in_graph steps per replay).
-    The projector error |Q~^T Q~ f - (f - Z^T (Z Z^T)^-1 Z f)| / |f| is
-    measured (FP64, torch) after the timed replays."""
+    with torch as the workload driver) and Q~^T (Q~ f) is computed in FP32
+    for an N(0, 1) force f.  reuse=False: the transforms are rebuilt on the
+    kept tree every step.  reuse=True: the transforms of the first positions
+    are kept and every body's accumulated rotation is applied to the bead
+    vectors instead (zq_apply_rotated).  The loop is captured in a CUDA
+    graph (steps_in_graph steps per replay).  The projector error
+    |Q~^T Q~ f - (f - Z^T (Z Z^T)^-1 Z f)| / |f| is measured (FP64, torch)
+    after the timed replays."""
     import torch
 
     from paper_1708_08427_gb300 import workloads as W
@@ -683,18 +687,26 @@ def bd_loop(args, stream, flush, world, dev, rank, steps_in_graph=10):
             torch.stack([2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)], 1),
             torch.stack([2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d], 1)], 1)
 
+    Racc = torch.eye(3, dtype=torch.float64, device=dev).repeat(m, 1, 1).contiguous()
+
     def one_step():
         q = torch.randn((m, 4), device=dev, dtype=torch.float64)
         q = q / q.norm(dim=1, keepdim=True)
         t = 0.1 * torch.randn((m, 3), device=dev, dtype=torch.float64)
         P3 = P.view(m, n, 3)
         cen = P3.mean(1, keepdim=True)
-        P3.copy_(torch.bmm(P3 - cen, rot(q).transpose(1, 2)) + cen + t[:, None, :])
-        x.copy_(P[:, 0]); y.copy_(P[:, 1]); z.copy_(P[:, 2])
-        ctx.build_transforms(x, y, z)
+        Rq = rot(q)
+        P3.copy_(torch.bmm(P3 - cen, Rq.transpose(1, 2)) + cen + t[:, None, :])
         f.copy_(torch.randn((3, N), device=dev, dtype=torch.float32))
-        ctx.apply_Q(f, qf)
-        ctx.apply_QT(qf, out)
+        if reuse:
+            Racc.copy_(torch.bmm(Rq, Racc))
+            ctx.apply_rotated(Racc, v=f, qv=qf)
+            ctx.apply_rotated(Racc, w=qf, qtw=out)
+        else:
+            x.copy_(P[:, 0]); y.copy_(P[:, 1]); z.copy_(P[:, 2])
+            ctx.build_transforms(x, y, z)
+            ctx.apply_Q(f, qf)
+            ctx.apply_QT(qf, out)
 
     for _ in range(2):
         with torch.cuda.stream(stream):
@@ -735,7 +747,9 @@ def bd_loop(args, stream, flush, world, dev, rank, steps_in_graph=10):
     Pf = (Fsum / n)[body] + torch.cross(om[body], Pc, dim=1)
     err = float(((out.double().t() - (fd - Pf)).norm() / fd.norm()).item())
     ctx.close()
-    return {"workload": "m=1000 shells x 1000 beads, tree kept, per step: rigid motion, transforms rebuilt, "
+    what = ("transforms kept, accumulated rotation applied to the bead vectors" if reuse
+            else "transforms rebuilt")
+    return {"workload": f"m=1000 shells x 1000 beads, tree kept, per step: rigid motion, {what}, "
                         "Q~^T(Q~ f) FP32", "steps_per_s": 1.0 / t_step, "ms_per_step": 1e3 * t_step,
             "beads_per_s": N / t_step, "graph": g is not None, "steps_timed": reps * steps_in_graph,
             "projector_rel_err_fp32": err}

@@ -149,6 +149,28 @@ zq_status zq_apply_QT_full(zq_ctx *ctx, zq_prec prec, const void *w, const void 
  * ZQ_ESTATE before the transforms of this precision exist. */
 zq_status zq_apply_pair(zq_ctx *ctx, zq_prec prec, const void *v, void *qv, const void *w, void *qtw);
 
+/* Products for rigidly moved bodies without rebuilding the transforms.
+ * Body j moved rigidly: bead k goes to R_j r_k^j + d_j for a rotation R_j
+ * and any translation d_j.  From Z's definition (Sec. 1, Eq. 1.2),
+ * [R r]x = R [r]x R^T gives Z_moved blockdiag(R_j) = diag(R_j, R_j) Z_ref.
+ * So Q~_ref blockdiag(R_j^T) has orthonormal rows orthogonal to the moved
+ * body's Z rows: it is a valid Q~ of the moved body.  The projector
+ * Q~^T Q~ is the same as after a rebuild; the basis is not.
+ *   qv  = Q~_ref blockdiag(R^T) v   (each bead vector rotated by R_j^T,
+ *                                     then Algorithm 2),
+ *   qtw = blockdiag(R) Q~_ref^T w   (Algorithm 3, then each bead vector
+ *                                     rotated by R_j).
+ * Q~_ref are the transforms last built (zq_build_transforms / zq_pipeline)
+ * on the reference coordinates.  R: DEVICE, 9 m doubles, body j's R_j
+ * row-major at R[9 j]; it is used as given (not checked for orthogonality;
+ * a non-orthogonal R_j gives rows that are not orthonormal).  Other
+ * layouts as zq_apply_pair.  v/qv or w/qtw may both be NULL (not all
+ * four); with both, the two sweeps run concurrently as in zq_apply_pair.
+ * Does not allocate; ZQ_EINVAL for R == NULL, ZQ_ESTATE before the
+ * transforms of this precision exist. */
+zq_status zq_apply_rotated(zq_ctx *ctx, zq_prec prec, const double *R, const void *v, void *qv,
+                           const void *w, void *qtw);
+
 /* ------------------------------------------------------------------------
  * Block form: k right-hand sides at once (the same node transforms applied
  * to k-column blocks; Algorithms 2 and 3 column by column).

@@ -22,6 +22,11 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
                   force/torque-free outputs, round trips (Table 1).
   qgen            pinned: Q Q^T = I, Q Z^T = 0 and agreement with the
                   implicit passes (Table 1 columns 2-7).
+  batch_apply_rotated
+                  pinned: for bodies moved rigidly, the moved body's Z
+                  (Eq. 1.2, from the moved coordinates) annihilates the
+                  rows, the rows stay orthonormal, Q~^T Q~ is the moved
+                  body's projector, and R = I gives batch_apply exactly.
   residue basis   rows 4..k of G are the LAPACK completion; the paper fixes
                   them only through "Matlab qr", so they are pinned exactly
                   as far as LAPACK is, and otherwise only through the
@@ -216,4 +221,25 @@ def batch_apply(off, x, y, z, f=None, w=None, lib: ctypes.CDLL | None = None):
                              None if wa is None else _dp(wa), None if qtw is None else _dp(qtw))
     if rc != 0:
         raise ValueError("oracle batch failed (a body with < 3 beads?)")
+    return qf, qtw
+
+
+def batch_apply_rotated(off, x, y, z, Rm, f=None, w=None, lib: ctypes.CDLL | None = None):
+    """Q~ f and Q~^T w of bodies moved rigidly from (x, y, z): body j's beads
+    taken to R_j r + d_j.  From Z's definition (Sec. 1, Eq. 1.2),
+    Z_moved blockdiag(R_j) = diag(R_j, R_j) Z, so Q~ blockdiag(R_j^T) is an
+    orthonormal complement of the moved body's Z rows.  Each bead vector of
+    f is rotated by R_j^T before Q~; each bead vector of Q~^T w is rotated by
+    R_j after.  Rm: (m, 3, 3); f, w, results as batch_apply."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    Rm = np.asarray(Rm, dtype=np.float64).reshape(-1, 3, 3)
+    N = int(off[-1])
+    body = np.repeat(np.arange(off.shape[0] - 1), np.diff(off))
+    fr = None
+    if f is not None:
+        fb = _f64(f).reshape(N, 3)
+        fr = np.einsum("nba,nb->na", Rm[body], fb).reshape(-1)     # R_j^T f_i
+    qf, qtw = batch_apply(off, x, y, z, fr, w, lib)
+    if qtw is not None:
+        qtw = np.einsum("nab,nb->na", Rm[body], qtw.reshape(N, 3)).reshape(-1)  # R_j u_i
     return qf, qtw

@@ -365,23 +365,29 @@ zq_status zq_apply_QT(zq_ctx* ctx, zq_prec prec, int64_t k, const void* w, int64
   return ZQ_OK;
 }
 
-zq_status zq_apply_pair(zq_ctx* ctx, zq_prec prec, const void* v, void* qv, const void* w, void* qtw) {
-  if (!ctx || !v || !qv || !w || !qtw) return ZQ_EINVAL;
+// Q~ v and/or Q~^T w (null pairs skipped), with optional per-body rotations.
+// With both, the two products are independent: Q~^T w runs on a side
+// stream (with its own scratch) while Q~ v runs on the context stream,
+// joined after.
+static zq_status apply_two(zq_ctx* ctx, zq_prec prec, const double* rot, const void* v, void* qv, const void* w,
+                           void* qtw) {
+  if (!ctx) return ZQ_EINVAL;
+  if ((v == nullptr) != (qv == nullptr) || (w == nullptr) != (qtw == nullptr) || (!v && !w)) return ZQ_EINVAL;
   if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
   Ctx& c = ctx->c;
   c.time_started = false;
   if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
-  // the two products are independent: Q~^T w on a side stream (with its
-  // own scratch) while Q~ v runs on the context stream, joined after
+  if (!v) return zq::launch_apply_QT(c, prec, w, qtw, 3 * c.N, nullptr, rot);
+  if (!w) return zq::launch_apply_Q(c, prec, v, 3 * c.N, qv, nullptr, rot);
   ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
   ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[0], c.fork_ev, 0));
-  ZQ_TRY(zq::launch_apply_Q(c, prec, v, 3 * c.N, qv));
+  ZQ_TRY(zq::launch_apply_Q(c, prec, v, 3 * c.N, qv, nullptr, rot));
   cudaStream_t main = c.stream;
   std::swap(c.x32, c.x32b);
   std::swap(c.x64, c.x64b);
   c.stream = c.side[0];
-  const zq_status st = zq::launch_apply_QT(c, prec, w, qtw, 3 * c.N);
+  const zq_status st = zq::launch_apply_QT(c, prec, w, qtw, 3 * c.N, nullptr, rot);
   c.stream = main;
   std::swap(c.x32, c.x32b);
   std::swap(c.x64, c.x64b);
@@ -389,6 +395,17 @@ zq_status zq_apply_pair(zq_ctx* ctx, zq_prec prec, const void* v, void* qv, cons
   ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[0], c.side[0]));
   ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[0], 0));
   return ZQ_OK;
+}
+
+zq_status zq_apply_pair(zq_ctx* ctx, zq_prec prec, const void* v, void* qv, const void* w, void* qtw) {
+  if (!v || !w) return ZQ_EINVAL;
+  return apply_two(ctx, prec, nullptr, v, qv, w, qtw);
+}
+
+zq_status zq_apply_rotated(zq_ctx* ctx, zq_prec prec, const double* R, const void* v, void* qv, const void* w,
+                           void* qtw) {
+  if (!R) return ZQ_EINVAL;
+  return apply_two(ctx, prec, R, v, qv, w, qtw);
 }
 
 zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,

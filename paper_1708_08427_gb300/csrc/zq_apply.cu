@@ -54,7 +54,46 @@ struct SweepArgs {
   const int32_t* bead_body;  // sorted position -> body
   T* root_out;             // up: the root Info-set [t; r] = Q_Z v per body (6 m), or null
   const T* root_in;        // down: the root Velocity-set per body (6 m), or null (zero)
+  const double* rot;       // per body R_j (9 m, row-major), or null: bead vectors enter as
+                           // R_j^T v_i (up) and leave as R_j L_i (down)
 };
+
+// A body's rotation in registers (on = false: the identity, nothing applied).
+template <typename T>
+struct Rot {
+  T r[9];
+  bool on;
+};
+
+// ROT = false (no rotations given) compiles the rotation away.
+template <bool ROT, typename T>
+__device__ __forceinline__ Rot<T> body_rot(const SweepArgs<T>& a, int64_t j) {
+  Rot<T> R;
+  R.on = ROT;
+  if (ROT) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R.r[k] = (T)__ldg(a.rot + 9 * j + k);
+  }
+  return R;
+}
+
+// v <- R^T v (a bead vector into the reference frame of the transforms)
+template <typename T>
+__device__ __forceinline__ void rot_in(const Rot<T>& R, T* v) {
+  if (!R.on) return;
+  const T a = v[0], b = v[1], c = v[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = R.r[i] * a + R.r[3 + i] * b + R.r[6 + i] * c;
+}
+
+// v <- R v (a bead velocity out of the reference frame)
+template <typename T>
+__device__ __forceinline__ void rot_out(const Rot<T>& R, T* v) {
+  if (!R.on) return;
+  const T a = v[0], b = v[1], c = v[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = R.r[3 * i] * a + R.r[3 * i + 1] * b + R.r[3 * i + 2] * c;
+}
 
 // Load W words of a record (16-byte vector loads, read-only path).
 template <typename T, int W>
@@ -279,7 +318,7 @@ __device__ __forceinline__ void up_dispatch(const SweepArgs<T>& a, uint32_t rw, 
   else up_node<T, 2>(r, X, Y, true, P, res);
 }
 
-template <typename T>
+template <typename T, bool ROT>
 __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
   __shared__ T info[(kSegMax - 1) * 6];
   __shared__ T bead[kSegMax * 3];
@@ -292,11 +331,14 @@ __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
       const uint32_t w0 = a.prw[p0], w1 = a.prw[p0 + nn];
       prefetch_l2(a.rec + 4 * (int64_t)w0, (w1 - w0) * 4u * (uint32_t)sizeof(T));
     }
+    const Rot<T> R = body_rot<ROT>(a, ROT ? a.bead_body[f] : 0);
     for (int32_t t = threadIdx.x; t <= nn; t += blockDim.x) {
       const int32_t b = a.perm[f + t];
-      bead[3 * t] = a.in[b];
-      bead[3 * t + 1] = a.in[a.N + b];
-      bead[3 * t + 2] = a.in[2 * a.N + b];
+      T v[3] = {a.in[b], a.in[a.N + b], a.in[2 * a.N + b]};
+      rot_in(R, v);
+      bead[3 * t] = v[0];
+      bead[3 * t + 1] = v[1];
+      bead[3 * t + 2] = v[2];
     }
     const int H = stage_meta(a, p0, nn, M);
     for (int h = 1; h <= H; ++h) {
@@ -337,19 +379,26 @@ __device__ __forceinline__ bool top_range(const int32_t* __restrict__ topv, cons
 }
 
 template <typename T>
-__device__ __forceinline__ void load_bead(const SweepArgs<T>& a, int32_t code, T* v) {
+__device__ __forceinline__ void load_bead(const SweepArgs<T>& a, int32_t code, T* v, const Rot<T>& R) {
   const int32_t b = a.perm[leaf_pos(code)];
   v[0] = a.in[b];
   v[1] = a.in[a.N + b];
   v[2] = a.in[2 * a.N + b];
+  rot_in(R, v);
 }
 
-template <typename T>
+template <bool ROT, typename T>
 __device__ __forceinline__ void up_top_node(const SweepArgs<T>& a, int32_t p, bool root) {
   const int2 cc = a.pc[p];
   T X[6], Y[6], P[6];
-  if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X);
-  if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y);
+  if (cc.x >= 0 && cc.y >= 0) {
+    load6(a.xs + 6 * (int64_t)cc.x, X);
+    load6(a.xs + 6 * (int64_t)cc.y, Y);
+  } else {
+    const Rot<T> R = body_rot<ROT>(a, blockIdx.x);
+    if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X, R);
+    if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y, R);
+  }
   up_dispatch(a, a.prw[p], a.proff[p], cc, X, Y, P);
   store6(a.xs + 6 * (int64_t)p, P);
   if (root && a.root_out) store6(a.root_out + 6 * (int64_t)blockIdx.x, P);  // Q_Z v of body blockIdx.x
@@ -358,7 +407,7 @@ __device__ __forceinline__ void up_top_node(const SweepArgs<T>& a, int32_t p, bo
 // Body blockIdx.x's top nodes, height by height (sorted by height in
 // shared memory; bodies with more than kHeightSorted top nodes scan their
 // list at every height).
-template <typename T>
+template <typename T, bool ROT>
 __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
   __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
@@ -370,10 +419,10 @@ __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
   for (int h = S.lim[0]; h <= S.lim[1]; ++h) {
     if (sorted) {
       for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x)
-        up_top_node(a, S.ids[k], h == S.lim[1]);
+        up_top_node<ROT>(a, S.ids[k], h == S.lim[1]);
     } else {
       for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
-        if (ph[list[t]] == h) up_top_node(a, list[t], h == S.lim[1]);
+        if (ph[list[t]] == h) up_top_node<ROT>(a, list[t], h == S.lim[1]);
     }
     __syncthreads();
   }
@@ -392,14 +441,16 @@ __device__ __forceinline__ void down_dispatch(const SweepArgs<T>& a, uint32_t rw
 }
 
 template <typename T>
-__device__ __forceinline__ void store_bead(const SweepArgs<T>& a, int32_t code, const T* L) {
+__device__ __forceinline__ void store_bead(const SweepArgs<T>& a, int32_t code, const T* L, const Rot<T>& R) {
   const int32_t b = a.perm[leaf_pos(code)];
-  a.out[b] = L[0];
-  a.out[a.N + b] = L[1];
-  a.out[2 * a.N + b] = L[2];
+  T u[3] = {L[0], L[1], L[2]};
+  rot_out(R, u);
+  a.out[b] = u[0];
+  a.out[a.N + b] = u[1];
+  a.out[2 * a.N + b] = u[2];
 }
 
-template <typename T>
+template <bool ROT, typename T>
 __device__ __forceinline__ void down_top_node(const SweepArgs<T>& a, int32_t p, bool root) {
   const int2 cc = a.pc[p];
   T Lp[6], Lx[6], Ly[6];
@@ -410,14 +461,20 @@ __device__ __forceinline__ void down_top_node(const SweepArgs<T>& a, int32_t p, 
     load6(a.xs + 6 * (int64_t)p, Lp);
   }
   down_dispatch(a, a.prw[p], a.proff[p], cc, Lp, Lx, Ly);
-  if (cc.x >= 0) store6(a.xs + 6 * (int64_t)cc.x, Lx); else store_bead(a, cc.x, Lx);
-  if (cc.y >= 0) store6(a.xs + 6 * (int64_t)cc.y, Ly); else store_bead(a, cc.y, Ly);
+  if (cc.x >= 0 && cc.y >= 0) {
+    store6(a.xs + 6 * (int64_t)cc.x, Lx);
+    store6(a.xs + 6 * (int64_t)cc.y, Ly);
+  } else {
+    const Rot<T> R = body_rot<ROT>(a, blockIdx.x);
+    if (cc.x >= 0) store6(a.xs + 6 * (int64_t)cc.x, Lx); else store_bead(a, cc.x, Lx, R);
+    if (cc.y >= 0) store6(a.xs + 6 * (int64_t)cc.y, Ly); else store_bead(a, cc.y, Ly, R);
+  }
 }
 
 // Runs first: for every body with top nodes, the root Velocity-set is 0,
 // then the top nodes from the root down (the root: the only top node of
 // the largest height).
-template <typename T>
+template <typename T, bool ROT>
 __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
   __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
@@ -430,16 +487,16 @@ __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
   for (int h = hmax; h >= S.lim[0]; --h) {
     if (sorted) {
       for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x)
-        down_top_node(a, S.ids[k], h == hmax);
+        down_top_node<ROT>(a, S.ids[k], h == hmax);
     } else {
       for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
-        if (ph[list[t]] == h) down_top_node(a, list[t], h == hmax);
+        if (ph[list[t]] == h) down_top_node<ROT>(a, list[t], h == hmax);
     }
     __syncthreads();
   }
 }
 
-template <typename T>
+template <typename T, bool ROT>
 __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
   __shared__ T info[(kSegMax - 1) * 6];
   __shared__ SegMeta M;
@@ -455,6 +512,7 @@ __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
       info[6 * (nn - 1) + threadIdx.x] =
           sg.w ? (a.root_in ? a.root_in[6 * (int64_t)a.bead_body[sg.z] + threadIdx.x] : T(0))
                : a.xs[6 * (int64_t)(p0 + nn - 1) + threadIdx.x];
+    const Rot<T> R = body_rot<ROT>(a, ROT ? a.bead_body[sg.z] : 0);
     const int H = stage_meta(a, p0, nn, M);
     for (int h = H; h >= 1; --h) {
       for (int32_t t = M.hb[h] + threadIdx.x; t < M.hb[h + 1]; t += blockDim.x) {
@@ -467,13 +525,13 @@ __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) info[6 * (cc.x - p0) + k] = Lx[k];
         } else {
-          store_bead(a, cc.x, Lx);
+          store_bead(a, cc.x, Lx, R);
         }
         if (cc.y >= 0) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) info[6 * (cc.y - p0) + k] = Ly[k];
         } else {
-          store_bead(a, cc.y, Ly);
+          store_bead(a, cc.y, Ly, R);
         }
       }
       __syncthreads();
@@ -710,33 +768,39 @@ SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   a.prw = reinterpret_cast<const uint32_t*>(c.prw);
   a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;
-  a.bead_body = c.bead_body; a.root_out = nullptr; a.root_in = nullptr;
+  a.bead_body = c.bead_body; a.root_out = nullptr; a.root_in = nullptr; a.rot = nullptr;
   return a;
 }
 
 template <typename T>
-zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out, T* root_out) {
+zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out, T* root_out, const double* rot) {
   SweepArgs<T> a = make_args<T>(c, rec, xs, v, out);
   a.root_out = root_out;
+  a.rot = rot;
   time_begin(c, "up_seg");
-  k_up_seg<T><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
+  if (rot) k_up_seg<T, true><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
+  else k_up_seg<T, false><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
   time_end(c, "up_seg");
   time_begin(c, "up_top");
-  k_up_top<T><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  if (rot) k_up_top<T, true><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  else k_up_top<T, false><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
   time_end(c, "up_top");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }
 
 template <typename T>
-zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out, const T* root_in) {
+zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out, const T* root_in, const double* rot) {
   SweepArgs<T> a = make_args<T>(c, rec, xs, w, out);
   a.root_in = root_in;
+  a.rot = rot;
   time_begin(c, "down_top");
-  k_down_top<T><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  if (rot) k_down_top<T, true><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  else k_down_top<T, false><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
   time_end(c, "down_top");
   time_begin(c, "down_seg");
-  k_down_seg<T><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
+  if (rot) k_down_seg<T, true><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
+  else k_down_seg<T, false><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
   time_end(c, "down_seg");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
@@ -744,20 +808,22 @@ zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out, const T* roo
 
 }  // namespace
 
-zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t /*ldv*/, void* out, void* root_out) {
+zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t /*ldv*/, void* out, void* root_out,
+                         const double* rot) {
   if (prec == ZQ_FP64)
     return run_up<double>(c, c.rec64, c.x64, static_cast<const double*>(v), static_cast<double*>(out),
-                          static_cast<double*>(root_out));
+                          static_cast<double*>(root_out), rot);
   return run_up<float>(c, c.rec32, c.x32, static_cast<const float*>(v), static_cast<float*>(out),
-                       static_cast<float*>(root_out));
+                       static_cast<float*>(root_out), rot);
 }
 
-zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t /*ldo*/, const void* root_in) {
+zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t /*ldo*/, const void* root_in,
+                          const double* rot) {
   if (prec == ZQ_FP64)
     return run_down<double>(c, c.rec64, c.x64, static_cast<const double*>(w), static_cast<double*>(out),
-                            static_cast<const double*>(root_in));
+                            static_cast<const double*>(root_in), rot);
   return run_down<float>(c, c.rec32, c.x32, static_cast<const float*>(w), static_cast<float*>(out),
-                         static_cast<const float*>(root_in));
+                         static_cast<const float*>(root_in), rot);
 }
 
 zq_status launch_apply_block(Ctx& c, bool up, zq_prec prec, int64_t k, const void* in, void* out) {

@@ -300,11 +300,13 @@ zq_status launch_segments(Ctx& c);
 zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which);
 // zq_apply.cu
 // root_out / root_in (6 m values, may be null): the root Info-set Q_Z v of
-// every body / the root Velocity-set fed to Q~^T (null: zero)
+// every body / the root Velocity-set fed to Q~^T (null: zero).  rot (9 m
+// FP64, may be null): per-body rotations R_j, the products taken with
+// Q~ blockdiag(R_j^T) (bead vectors rotated by R_j^T in, R_j out).
 zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t ldv, void* out,
-                         void* root_out = nullptr);
+                         void* root_out = nullptr, const double* rot = nullptr);
 zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t ldo,
-                          const void* root_in = nullptr);
+                          const void* root_in = nullptr, const double* rot = nullptr);
 // up: out = Q~ V, else out = Q~^T W; rows of k values (see include/zq.h)
 zq_status launch_apply_block(Ctx& c, bool up, zq_prec prec, int64_t k, const void* in, void* out);
 

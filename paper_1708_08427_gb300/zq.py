@@ -86,6 +86,8 @@ def _lib() -> ctypes.CDLL:
         L.zq_apply_QT_full.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
         L.zq_apply_pair.restype = ctypes.c_int
         L.zq_apply_pair.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.zq_apply_rotated.restype = ctypes.c_int
+        L.zq_apply_rotated.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
         L.zq_reserve_block.restype = ctypes.c_int
         L.zq_reserve_block.argtypes = [_vp, ctypes.c_int, _i64]
         for name in ("zq_apply_Q_block", "zq_apply_QT_block"):
@@ -222,6 +224,30 @@ class Context:
         _check(_lib().zq_apply_pair(self._h, self._prec(v), _ptr(v), _ptr(qv), _ptr(w), _ptr(qtw)),
                "zq_apply_pair")
         return qv, qtw
+
+    def apply_rotated(self, Rm, v=None, w=None, qv=None, qtw=None):
+        """Products for rigidly moved bodies on the transforms built for the
+        reference coordinates: Q~ blockdiag(R_j^T) v and blockdiag(R_j) Q~^T w.
+        Rm: (m, 3, 3) or (m, 9) float64 CUDA rotations; v (3, N), w (R,) of one
+        dtype (either may be None).  Returns (qv, qtw), None for a skipped one."""
+        import torch
+
+        N, m, R, _ = self.sizes()
+        assert Rm.is_cuda and Rm.dtype == torch.float64 and Rm.is_contiguous() and Rm.numel() == 9 * m
+        assert v is not None or w is not None
+        ref = v if v is not None else w
+        if v is not None:
+            assert v.is_cuda and v.is_contiguous() and v.numel() == 3 * N
+            if qv is None:
+                qv = torch.empty(R, dtype=v.dtype, device=v.device)
+        if w is not None:
+            assert w.is_cuda and w.is_contiguous() and w.numel() == R and w.dtype == ref.dtype
+            if qtw is None:
+                qtw = torch.empty((3, N), dtype=w.dtype, device=w.device)
+        p = lambda t: _ptr(t) if t is not None else None
+        _check(_lib().zq_apply_rotated(self._h, self._prec(ref), _ptr(Rm), p(v), p(qv), p(w), p(qtw)),
+               "zq_apply_rotated")
+        return (qv if v is not None else None), (qtw if w is not None else None)
 
     # ------------------------------------------------------- block form
     @staticmethod

@@ -45,6 +45,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.zq_build_tree_batched(None, 1, None, None, None, None, 0) == 1  # ZQ_EINVAL
     assert lib.zq_sync(None) == 1
     assert lib.zq_apply_Q(None, 0, 1, None, 0, None, 0) == 1
+    lib.zq_apply_rotated.restype = ctypes.c_int
+    assert lib.zq_apply_rotated(None, 0, None, None, None, None, None) == 1
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
