@@ -142,6 +142,35 @@ zq_status zq_apply_QT(zq_ctx *ctx, zq_prec prec, int64_t k, const void *w, int64
 zq_status zq_apply_Q_full(zq_ctx *ctx, zq_prec prec, const void *v, void *out, void *root);
 zq_status zq_apply_QT_full(zq_ctx *ctx, zq_prec prec, const void *w, const void *root, void *out);
 
+/* The explicit Q~ (Algorithm 1, Eqs. 3.7-3.8) as a CSR matrix of R rows and
+ * 3N columns.
+ * Rows: the R residue rows in the order of zq_apply_Q's output (body j's
+ *   rows from 3 off[j] - 6 j; inside a body node by node, each node's
+ *   k - 3 rows together).
+ * Columns: bead i's axis a is column 3 i + a (bead i in the caller's
+ *   order, all bodies; the paper's interleaved ordering).  So Q~ times the
+ *   interleaved vector [v_0; v_1; ...] equals zq_apply_Q of the planes.
+ * Structure: a row of node p is nonzero only on p's n_p beads.  It holds
+ *   3 n_p entries: the beads in the tree's order (ascending positions of
+ *   the sorted keys, not ascending columns), three axes each.  Entries that
+ *   happen to be 0 are stored.  So nnz = sum_p (k_p - 3) 3 n_p, which is
+ *   O(n log n) (Sec. 3, the complexity of Algorithm 1).
+ * zq_qgen_nnz: *nnz (HOST) = that count.  It needs the tree only, and
+ *   synchronises the context stream.
+ * zq_qgen: fills DEVICE buffers.
+ *   row_ptr: R + 1 int64; row r is [row_ptr[r], row_ptr[r + 1]).
+ *   col: nnz int32.
+ *   val: nnz values of the precision's type.  The FP32 values are computed
+ *     from the FP32 transforms in FP32.
+ *   uz: optional (may be NULL), 9 N values.  Body j's U_j is the 3 x 3 n_j
+ *     block of the rotational rows of Q_Z = [I / sqrt(n_j); U_j] (Eq. 3.3).
+ *     It is row-major at uz[9 off[j]], column 3 i + a for local bead i.
+ * Scratch of about 12 (N + nodes) bytes is allocated and freed
+ * stream-ordered.  ZQ_EINVAL if 3N exceeds INT32_MAX; ZQ_ESTATE before the
+ * transforms of this precision exist. */
+zq_status zq_qgen_nnz(zq_ctx *ctx, int64_t *nnz);
+zq_status zq_qgen(zq_ctx *ctx, zq_prec prec, int64_t *row_ptr, int32_t *col, void *val, void *uz);
+
 /* qv = Q~ v and qtw = Q~^T w for one column each (Algorithms 2 and 3), the
  * two sweeps running concurrently (Q~^T w on a stream forked from and
  * joined back into the context stream, with its own scratch).  Layouts as

@@ -308,6 +308,26 @@ zq_status zq_apply_QT_full(zq_ctx* ctx, zq_prec prec, const void* w, const void*
   return zq::launch_apply_QT(c, prec, w, out, 3 * c.N, root);
 }
 
+zq_status zq_qgen_nnz(zq_ctx* ctx, int64_t* nnz) {
+  if (!ctx || !nnz) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  c.time_started = false;
+  if (!c.have_tree) return ZQ_ESTATE;
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  return zq::launch_qgen_nnz(c, nnz);
+}
+
+zq_status zq_qgen(zq_ctx* ctx, zq_prec prec, int64_t* row_ptr, int32_t* col, void* val, void* uz) {
+  if (!ctx || !row_ptr || !col || !val) return ZQ_EINVAL;
+  if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  c.time_started = false;
+  if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;
+  if (3 * c.N > INT32_MAX) return ZQ_EINVAL;  // column indices are int32
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  return zq::launch_qgen(c, prec, row_ptr, col, val, uz);
+}
+
 zq_status zq_reserve_block(zq_ctx* ctx, zq_prec prec, int64_t k_max) {
   if (!ctx || k_max < 1) return ZQ_EINVAL;
   if (prec != ZQ_FP32 && prec != ZQ_FP64 && prec != ZQ_BF16) return ZQ_EINVAL;

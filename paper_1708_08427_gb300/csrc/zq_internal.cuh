@@ -292,7 +292,12 @@ int64_t sort_hist_words(int64_t n_max);  // histogram + scan workspace of the la
 // zq_scan.cu
 zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
                                 int32_t* total);
+zq_status launch_exclusive_scan64(Ctx& c, const int64_t* in, int64_t* out, int64_t n, int64_t* tmp,
+                                  int64_t* total);
 int64_t scan_tmp_words(int64_t n);
+// zq_qgen.cu: the explicit Q~ in CSR form (include/zq.h, zq_qgen)
+zq_status launch_qgen_nnz(Ctx& c, int64_t* nnz_host);  // synchronises c.stream
+zq_status launch_qgen(Ctx& c, zq_prec prec, int64_t* row_ptr, int32_t* col, void* val, void* uz);
 // zq_seg.cu
 zq_status launch_segments(Ctx& c);
 // zq_build.cu

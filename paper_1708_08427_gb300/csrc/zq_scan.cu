@@ -1,5 +1,5 @@
-// zq_scan.cu -- exclusive prefix sum of int32 (residue offsets, list
-// compaction).  Three launches: per-block totals, one block scanning the
+// zq_scan.cu -- exclusive prefix sums of int32 (residue offsets, list
+// compaction) and int64 (nonzero counts of the explicit Q~).  Three launches: per-block totals, one block scanning the
 // totals with a running carry, per-block scan plus carry.
 #include "zq_internal.cuh"
 
@@ -11,11 +11,12 @@ constexpr int kThreads = 1024;
 constexpr int kItems = 4;
 constexpr int kTileN = kThreads * kItems;
 
-__device__ inline int32_t warp_incl_scan(int32_t v) {
+template <typename I>
+__device__ inline I warp_incl_scan(I v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    int32_t t = __shfl_up_sync(0xffffffffu, v, d);
+    I t = __shfl_up_sync(0xffffffffu, v, d);
     if (lane >= d) v += t;
   }
   return v;
@@ -23,63 +24,66 @@ __device__ inline int32_t warp_incl_scan(int32_t v) {
 
 // Exclusive scan of one value per thread over the block; returns the prefix
 // and writes the block total to *total.
-__device__ inline int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
+template <typename I>
+__device__ inline I block_excl_scan(I v, I* sh, I* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t inc = warp_incl_scan(v);
+  I inc = warp_incl_scan(v);
   if (lane == 31) sh[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    int32_t w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
-    int32_t wi = warp_incl_scan(w);
+    I w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+    I wi = warp_incl_scan(w);
     sh[lane] = wi - w;
     if (lane == 31) sh[32] = wi;
   }
   __syncthreads();
-  int32_t r = inc - v + sh[warp];
+  I r = inc - v + sh[warp];
   *total = sh[32];
   __syncthreads();
   return r;
 }
 
-__global__ void k_block_totals(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ tot) {
-  __shared__ int32_t sh[33];
+template <typename I>
+__global__ void k_block_totals(const I* __restrict__ in, int64_t n, I* __restrict__ tot) {
+  __shared__ I sh[33];
   int64_t base = (int64_t)blockIdx.x * kTileN + (int64_t)threadIdx.x * kItems;
-  int32_t s = 0;
+  I s = 0;
 #pragma unroll
   for (int i = 0; i < kItems; ++i)
     if (base + i < n) s += in[base + i];
-  int32_t t;
+  I t;
   block_excl_scan(s, sh, &t);
   if (threadIdx.x == 0) tot[blockIdx.x] = t;
 }
 
-__global__ void k_scan_totals(int32_t* __restrict__ tot, int64_t nb, int32_t* __restrict__ total) {
-  __shared__ int32_t sh[33];
-  int32_t carry = 0;
+template <typename I>
+__global__ void k_scan_totals(I* __restrict__ tot, int64_t nb, I* __restrict__ total) {
+  __shared__ I sh[33];
+  I carry = 0;
   for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
     int64_t i = b0 + threadIdx.x;
-    int32_t v = (i < nb) ? tot[i] : 0;
-    int32_t t;
-    int32_t e = block_excl_scan(v, sh, &t);
+    I v = (i < nb) ? tot[i] : 0;
+    I t;
+    I e = block_excl_scan(v, sh, &t);
     if (i < nb) tot[i] = carry + e;
     carry += t;
   }
   if (threadIdx.x == 0 && total) *total = carry;
 }
 
-__global__ void k_block_scan(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ tot,
-                             int32_t* __restrict__ out) {
-  __shared__ int32_t sh[33];
+template <typename I>
+__global__ void k_block_scan(const I* __restrict__ in, int64_t n, const I* __restrict__ tot, I* __restrict__ out) {
+  __shared__ I sh[33];
   int64_t base = (int64_t)blockIdx.x * kTileN + (int64_t)threadIdx.x * kItems;
-  int32_t v[kItems];
-  int32_t s = 0;
+  I v[kItems];
+  I s = 0;
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     v[i] = (base + i < n) ? in[base + i] : 0;
     s += v[i];
   }
-  int32_t t;
-  int32_t e = block_excl_scan(s, sh, &t) + tot[blockIdx.x];
+  I t;
+  I e = block_excl_scan(s, sh, &t) + tot[blockIdx.x];
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     if (base + i < n) out[base + i] = e;
@@ -91,27 +95,37 @@ __global__ void k_block_scan(const int32_t* __restrict__ in, int64_t n, const in
 
 int64_t scan_tmp_words(int64_t n) { return (n + kTileN - 1) / kTileN + 1; }
 
-// out[i] = sum_{k<i} in[k]; *total (device, may be NULL) = sum of all.
-// in and out may alias.  tmp: scan_tmp_words(n) ints of device scratch.
-zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
-                                int32_t* total) {
+template <typename I>
+zq_status scan_impl(Ctx& c, const I* in, I* out, int64_t n, I* tmp, I* total) {
   cudaStream_t s = c.stream;
   if (n <= 0) {
-    if (total) ZQ_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(int32_t), s));
+    if (total) ZQ_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(I), s));
     return ZQ_OK;
   }
   int64_t nb = (n + kTileN - 1) / kTileN;
   time_begin(c, "scan");
-  k_block_totals<<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp);
+  k_block_totals<I><<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp);
   time_end(c, "scan");
   time_begin(c, "scan");
-  k_scan_totals<<<1, kThreads, 0, s>>>(tmp, nb, total);
+  k_scan_totals<I><<<1, kThreads, 0, s>>>(tmp, nb, total);
   time_end(c, "scan");
   time_begin(c, "scan");
-  k_block_scan<<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp, out);
+  k_block_scan<I><<<(unsigned)nb, kThreads, 0, s>>>(in, n, tmp, out);
   time_end(c, "scan");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
+}
+
+// out[i] = sum_{k<i} in[k]; *total (device, may be NULL) = sum of all.
+// in and out may alias.  tmp: scan_tmp_words(n) values of device scratch.
+zq_status launch_exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                                int32_t* total) {
+  return scan_impl<int32_t>(c, in, out, n, tmp, total);
+}
+
+zq_status launch_exclusive_scan64(Ctx& c, const int64_t* in, int64_t* out, int64_t n, int64_t* tmp,
+                                  int64_t* total) {
+  return scan_impl<int64_t>(c, in, out, n, tmp, total);
 }
 
 }  // namespace zq

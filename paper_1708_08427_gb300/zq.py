@@ -87,6 +87,10 @@ def _lib() -> ctypes.CDLL:
         L.zq_apply_pair.restype = ctypes.c_int
         L.zq_apply_pair.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.zq_apply_rotated.restype = ctypes.c_int
+        L.zq_qgen_nnz.restype = ctypes.c_int
+        L.zq_qgen_nnz.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+        L.zq_qgen.restype = ctypes.c_int
+        L.zq_qgen.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.zq_apply_rotated.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
         L.zq_reserve_block.restype = ctypes.c_int
         L.zq_reserve_block.argtypes = [_vp, ctypes.c_int, _i64]
@@ -248,6 +252,32 @@ class Context:
         _check(_lib().zq_apply_rotated(self._h, self._prec(ref), _ptr(Rm), p(v), p(qv), p(w), p(qtw)),
                "zq_apply_rotated")
         return (qv if v is not None else None), (qtw if w is not None else None)
+
+    def qgen_nnz(self) -> int:
+        """Nonzeros of the explicit Q~ (synchronises the context stream)."""
+        n = ctypes.c_int64()
+        _check(_lib().zq_qgen_nnz(self._h, ctypes.byref(n)), "zq_qgen_nnz")
+        return int(n.value)
+
+    def qgen(self, dtype=None, with_u: bool = False, device=None):
+        """The explicit Q~ as CSR arrays (row_ptr int64 (R+1), col int32,
+        val): columns 3 i + a in the caller's bead order.  with_u: also the
+        rotational rows U_j of Q_Z, 9 N values (body j's 3 x 3 n_j block at
+        9 off[j]).  Returns (row_ptr, col, val, U or None)."""
+        import torch
+
+        dtype = dtype or torch.float64
+        dev = device or torch.device("cuda", self.device)
+        N, m, R, _ = self.sizes()
+        nnz = self.qgen_nnz()
+        row_ptr = torch.empty(R + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(nnz, dtype=torch.int32, device=dev)
+        val = torch.empty(nnz, dtype=dtype, device=dev)
+        U = torch.empty(9 * N, dtype=dtype, device=dev) if with_u else None
+        p = {torch.float64: ZQ_FP64, torch.float32: ZQ_FP32}[dtype]
+        _check(_lib().zq_qgen(self._h, p, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(U) if U is not None else None),
+               "zq_qgen")
+        return row_ptr, col, val, U
 
     # ------------------------------------------------------- block form
     @staticmethod

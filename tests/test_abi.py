@@ -47,6 +47,10 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.zq_apply_Q(None, 0, 1, None, 0, None, 0) == 1
     lib.zq_apply_rotated.restype = ctypes.c_int
     assert lib.zq_apply_rotated(None, 0, None, None, None, None, None) == 1
+    lib.zq_qgen.restype = ctypes.c_int
+    lib.zq_qgen_nnz.restype = ctypes.c_int
+    assert lib.zq_qgen(None, 0, None, None, None, None) == 1
+    assert lib.zq_qgen_nnz(None, None) == 1
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
