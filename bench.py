@@ -61,6 +61,9 @@ def parse():
                     help="node-transform arithmetic: double-single on FP32 pipes or native FP64")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / apply-only / e2e / CPU legs")
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated subset of the extra legs: build_other, fp64_step, apply, qgen, e2e, "
+                         "multirhs, bd_loop, cpu (default all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the per-kernel timing pass (the dominant kernel is then build_level)")
@@ -418,18 +421,28 @@ def run_ours(args, world, rank, local):
 
     if not args.no_graph:
         out["graph_replay"] = timed(args, step, stream, flush, world, dev, N, graph=True)
-    if not args.no_extras:
+    legs = set() if args.no_extras else (
+        {"build_other", "fp64_step", "apply", "qgen", "e2e", "multirhs", "bd_loop", "cpu"}
+        if args.extras == "all" else set(args.extras.split(",")))
+    if "build_other" in legs:
         other = "fp64" if args.build == "dd" else "dd"
         ctx.set_build_arith(other)
         out[f"build_{other}_step"] = timed(args, step, stream, flush, world, dev, N, graph=not args.no_graph)
         ctx.set_build_arith(args.build)
+    if "fp64_step" in legs:
         out["fp64_step"] = fp64_step(args, ctx, bt, stream, flush, rng, world, dev)
+    if "apply" in legs:
         out["apply"] = apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev)
+    if "qgen" in legs:
+        out["qgen"] = qgen_bench(args, ctx, bt, stream, flush, world, dev)
+    if "e2e" in legs:
         out["e2e"] = e2e(args, ctx, bt, stream, world, dev)
+    if "multirhs" in legs:
         out["multirhs"] = multirhs(args, stream, flush, world, dev, rank)
+    if "bd_loop" in legs:
         out["bd_loop"] = bd_loop(args, stream, flush, world, dev, rank)
         out["bd_loop_rotation_reuse"] = bd_loop(args, stream, flush, world, dev, rank, reuse=True)
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and "cpu" in legs:
         out["cpu_baseline"] = cpu_baseline(bt, args.cpu_seconds)
     ctx.close()
     return out
@@ -527,6 +540,42 @@ def apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev):
         r["hbm_frac"] = r["hbm_achieved_gbs"] / hbm
         r["algorithmic_bytes_per_step"] = byt
         res[name] = r
+    return res
+
+
+def qgen_bench(args, ctx, bt, stream, flush, world, dev):
+    """The explicit Q~ in CSR form (zq_qgen, Algorithm 1) on the step's batch
+    with its transforms built: FP32 and FP64 values.  The bytes counted are
+    the CSR written (values, int32 columns, int64 row pointers), the
+    kernel's unavoidable traffic; the per-bead path walks read the node
+    records through L1/L2."""
+    import torch
+
+    N, R = bt.N, bt.n_residues
+    x, y, z = xyz_of(ctx, bt, dev)
+    ctx.build_tree_batched(bt.off, x, y, z, args.cut)
+    ctx.build_transforms(x, y, z)  # both record precisions
+    nnz = ctx.qgen_nnz()
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    res = {"nnz": nnz, "nnz_per_bead": nnz / N}
+    rp = torch.empty(R + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    for name, dt, es in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+        val = torch.empty(nnz, dtype=dt, device=dev)
+
+        def fn():
+            ctx.qgen_into(rp, col, val)
+
+        r = timed(args, fn, stream, flush, world, dev, N, graph=False, steps=5)
+        byt = nnz * (es + 4) + (R + 1) * 8
+        r["written_bytes"] = byt
+        r["hbm_achieved_gbs"] = byt / (r["ms_per_step"] / 1e3) / 1e9
+        r["hbm_frac"] = r["hbm_achieved_gbs"] / hbm
+        res[name] = r
+        del val
+    del rp, col
+    torch.cuda.empty_cache()
     return res
 
 

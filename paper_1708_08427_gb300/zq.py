@@ -274,7 +274,14 @@ class Context:
         col = torch.empty(nnz, dtype=torch.int32, device=dev)
         val = torch.empty(nnz, dtype=dtype, device=dev)
         U = torch.empty(9 * N, dtype=dtype, device=dev) if with_u else None
-        p = {torch.float64: ZQ_FP64, torch.float32: ZQ_FP32}[dtype]
+        return self.qgen_into(row_ptr, col, val, U)
+
+    def qgen_into(self, row_ptr, col, val, U=None):
+        """zq_qgen into given device buffers (sizes as qgen's results)."""
+        import torch
+
+        p = {torch.float64: ZQ_FP64, torch.float32: ZQ_FP32}[val.dtype]
+        assert row_ptr.dtype == torch.int64 and col.dtype == torch.int32 and (U is None or U.dtype == val.dtype)
         _check(_lib().zq_qgen(self._h, p, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(U) if U is not None else None),
                "zq_qgen")
         return row_ptr, col, val, U
