@@ -86,15 +86,39 @@ __device__ __forceinline__ void load_leaf(const BuildArgs& a, int32_t code, Chil
   ch.c[2] = a.z[i];
 }
 
+// A slot's state is 10 words of 8 bytes (80 bytes, 16-byte aligned): the
+// centroid, T22's six values in the build type (bit patterns), a pad.  It is
+// moved as five 16-byte words.
+template <class R>
+__device__ __forceinline__ double as_word(R v) {
+  static_assert(sizeof(R) == 8, "state words are 8 bytes");
+  double d;
+  memcpy(&d, &v, 8);
+  return d;
+}
+
+template <class R>
+__device__ __forceinline__ R from_word(double d) {
+  R v;
+  memcpy(&v, &d, 8);
+  return v;
+}
+
 template <class R>
 __device__ __forceinline__ void load_node(const BuildArgs& a, int32_t slot, Child<R>& ch) {
-  const double* s = reinterpret_cast<const double*>(a.st) + (int64_t)slot * kState;
+  const double2* s = reinterpret_cast<const double2*>(reinterpret_cast<const double*>(a.st) + (int64_t)slot * kState);
   ch.n = a.scnt[slot];
+  double w[10];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) ch.c[i] = s[i];
-  const R* l = reinterpret_cast<const R*>(s + 3);
+  for (int i = 0; i < 5; ++i) {
+    const double2 q = s[i];
+    w[2 * i] = q.x;
+    w[2 * i + 1] = q.y;
+  }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) ch.L[i] = l[i];
+  for (int i = 0; i < 3; ++i) ch.c[i] = w[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) ch.L[i] = from_word<R>(w[3 + i]);
 }
 
 template <class R>
@@ -152,12 +176,15 @@ __device__ __forceinline__ void geometry_pair(const Child<R>& X, const Child<R>&
 template <class R, int W>
 __device__ __forceinline__ void store(const BuildArgs& a, int64_t slot, int64_t rw, const R (&rec)[W],
                                       const double* cp, const R* L) {
-  double* st = reinterpret_cast<double*>(a.st) + slot * kState;
+  double2* st = reinterpret_cast<double2*>(reinterpret_cast<double*>(a.st) + slot * kState);
+  double w[10];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) st[i] = cp[i];
-  R* l = reinterpret_cast<R*>(st + 3);
+  for (int i = 0; i < 3; ++i) w[i] = cp[i];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) l[i] = L[i];
+  for (int i = 0; i < 6; ++i) w[3 + i] = as_word<R>(L[i]);
+  w[9] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) st[i] = make_double2(w[2 * i], w[2 * i + 1]);
   if (a.rec64) {
     double2* r = reinterpret_cast<double2*>(a.rec64 + rw);
 #pragma unroll
@@ -412,15 +439,26 @@ __device__ __forceinline__ void build_slot(const BuildArgs& a, int64_t s, int ty
   else node_hh9<R>(a, s, cc, rw);
 }
 
+// Height 1 holds exactly the nodes with two leaf children (Case I): a
+// kernel of its own, which needs far fewer registers than the Householder
+// cases and so runs at full occupancy.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_build_case1(BuildArgs a) {
+  const int32_t s0 = a.bstart[0], s1 = a.bstart[1];
+  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s1;
+       s += (int64_t)gridDim.x * blockDim.x)
+    node_case1<R>(a, s, a.sc[s], 4 * (int64_t)(uint32_t)a.srw[s]);
+}
+
+// Heights 2..cut: only nodes with at least one internal child (k = 6, 9).
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_build_level(BuildArgs a, int h) {
   const int b0 = 3 * (h - 1);
-  const int32_t s0 = a.bstart[b0], s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
-  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
+  const int32_t s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
+  for (int64_t s = s1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int64_t rw = 4 * (int64_t)(uint32_t)a.srw[s];
-    if (s < s1) build_slot<R>(a, s, 0, rw);
-    else if (s < s2) build_slot<R>(a, s, 1, rw);
+    if (s < s2) build_slot<R>(a, s, 1, rw);
     else build_slot<R>(a, s, 2, rw);
   }
 }
@@ -465,7 +503,10 @@ __global__ void k_count_table_dd(const double* __restrict__ tab, float2* __restr
 template <class R>
 zq_status run_build(Ctx& c, const BuildArgs& a) {
   const int grid = c.num_sms * 4;
-  for (int h = 1; h <= c.cut; ++h) {
+  time_begin(c, "build_level");
+  k_build_case1<R><<<c.num_sms * 8, kThreads, 0, c.stream>>>(a);
+  time_end(c, "build_level");
+  for (int h = 2; h <= c.cut; ++h) {
     time_begin(c, "build_level");
     k_build_level<R><<<grid, kThreads, 0, c.stream>>>(a, h);
     time_end(c, "build_level");
