@@ -4,7 +4,7 @@
 //   2. 21-bit quantisation and bisection keys (z, then y, then x per octree
 //      level, most significant first);
 //   3. stable LSD radix sort of (key, body-local index) in shared memory,
-//      8-bit digits: four passes over the high 32 key bits, then each run of
+//      8-bit digits, warp-level ranks from ballots: four passes over the high 32 key bits, then each run of
 //      equal high halves (rare: beads closer than 2^-10 of the box) sorted
 //      by insertion; bodies with a run of more than 32 such beads take all
 //      eight passes instead.  Equal keys keep index order;
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   {
     unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
     bool bad = false;
+#pragma unroll 4
     for (int i = tid; i < n; i += THREADS) {
       const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
 #pragma unroll
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   // ---- 2. keys
   {
     const double inv[3] = {lim[6], lim[7], lim[8]};
+#pragma unroll 4
     for (int i = tid; i < n; i += THREADS) {
       const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
       uint32_t q[3];
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
       const int i = base + lane;
       const bool v = i < c1;
       const int dg = v ? (int)((kin[i] >> shift) & 0xff) : 256 + lane;
-      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      const unsigned peers = digit_peers(dg, v);
       if (v && (peers & lt) == 0) whist[warp * 256 + dg] += __popc(peers);
       __syncwarp();
     }
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
         ix = iin[i];
         dg = (int)((k >> shift) & 0xff);
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      const unsigned peers = digit_peers(dg, v);
       if (v) {
         const int pos = whist[warp * 256 + dg] + __popc(peers & lt);
         kout[pos] = k;

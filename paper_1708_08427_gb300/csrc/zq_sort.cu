@@ -16,7 +16,7 @@ namespace {
 // Eight passes of 8-bit digits.  A block owns a tile of kTile keys (kept in
 // shared memory for the pass); warp w owns the w-th slice of the tile, in
 // order.  Counting: per-block histogram.  Scatter: within a warp, lanes
-// with the same digit are ranked by __match_any_sync in lane order, and
+// with the same digit are ranked by digit_peers in lane order, and
 // the slices of a tile follow each other, so equal digits keep their input
 // order (a stable pass); the global position of (digit, tile) comes from
 // a scan of the per-tile histograms (digit-major).
@@ -63,7 +63,7 @@ k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vi
     const int i = b + lane;
     const bool v = i < c1;
     const int dg = v ? (int)((sk[i] >> shift) & (kDigits - 1)) : kDigits + lane;
-    const unsigned peers = __match_any_sync(0xffffffffu, dg);
+    const unsigned peers = digit_peers(dg, v);
     if (v && (peers & lt) == 0) whist[warp][dg] += __popc(peers);
     __syncwarp();
   }
@@ -90,7 +90,7 @@ k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vi
       val = sv[i];
       dg = (int)((k >> shift) & (kDigits - 1));
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, dg);
+    const unsigned peers = digit_peers(dg, v);
     if (v) {
       const int32_t pos = whist[warp][dg] + __popc(peers & lt);
       kout[pos] = k;
