@@ -40,6 +40,31 @@ struct SmallTreeArgs {
   int final_roff;  // 1: write residue offsets (no device-wide scan follows)
 };
 
+// A finished node in 63 bits: left and right child (14 bits each: bit 13
+// set for a leaf, then its body-local position, else the body-local split
+// position), first position (13 bits), bead count (14 bits), height (8 bits).
+__device__ __forceinline__ uint32_t local_code(int32_t code, int64_t o, int64_t nb) {
+  return code < 0 ? (1u << 13) | (uint32_t)(-1 - code - o) : (uint32_t)(code - nb);
+}
+
+__device__ __forceinline__ int32_t global_code(uint32_t lc, int64_t o, int64_t nb) {
+  return (lc >> 13) ? (int32_t)(-1 - (o + (lc & 0x1fffu))) : (int32_t)(nb + lc);
+}
+
+__device__ __forceinline__ unsigned long long pack_node(uint32_t lc, uint32_t rc, int first, int cnt, int h) {
+  return (unsigned long long)lc | ((unsigned long long)rc << 14) | ((unsigned long long)first << 28) |
+         ((unsigned long long)cnt << 41) | ((unsigned long long)h << 55);
+}
+
+__device__ __forceinline__ uint32_t unpack(unsigned long long pk, int at, int bits) {
+  return (uint32_t)((pk >> at) & ((1ull << bits) - 1));
+}
+
+// 3 per internal child (k - 3 of Eq. 3.5)
+__device__ __forceinline__ int32_t residue_size(unsigned long long pk) {
+  return 3 * ((unpack(pk, 13, 1) ^ 1u) + (unpack(pk, 27, 1) ^ 1u));
+}
+
 __device__ __forceinline__ uint32_t quantise_exact(double p, double lo, double hi) {
   if (!(hi > lo)) return 0u;
   const double t = __ddiv_rn(__dsub_rn(p, lo), __dsub_rn(hi, lo));
@@ -324,6 +349,10 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   // ---- 5. bottom-up construction (node id of split g: o - j + g).
   // slot[g] = 0 until a child arrives; a deposit is
   //   bit 63 valid | bits 24..55 child code | bits 8..23 range end | bits 0..7 height
+  // The child that completes g overwrites slot[g] with g's packed node
+  // (pack_node; nothing else touches slot[g] after its second deposit), and
+  // the nodes go out to global memory in node order after the walk, so the
+  // stores are coalesced instead of six scattered ones per node.
   // A lane takes one step of its walk per iteration; a lane whose walk has
   // ended (it arrived first at a node, or completed the root) takes the
   // next unprocessed leaf, so warps stay full while a few walks are long.
@@ -375,32 +404,38 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
     const int32_t lc = is_left ? code : sib;
     const int32_t rc = is_left ? sib : code;
     h = 1 + (h > hs ? h : hs);
-    a.cl[q] = lc;
-    a.cr[q] = rc;
-    a.first[q] = (int32_t)(o + lo_);
-    a.cnt[q] = hi_ - lo_ + 1;
-    a.height[q] = (uint8_t)h;
-    a.res[q] = 3 * ((lc >= 0) + (rc >= 0));
+    slot[g] = pack_node(local_code(lc, o, nb), local_code(rc, o, nb), lo_, hi_ - lo_ + 1, h);
     code = (int32_t)q;
     l = lo_;
     r = hi_;
+  }
+
+  __syncthreads();
+  for (int g = tid; g < n - 1; g += THREADS) {
+    const unsigned long long pk = slot[g];
+    const int32_t lc = global_code(unpack(pk, 0, 14), o, nb), rc = global_code(unpack(pk, 14, 14), o, nb);
+    const int64_t q = nb + g;
+    a.cl[q] = lc;
+    a.cr[q] = rc;
+    a.first[q] = (int32_t)(o + unpack(pk, 28, 13));
+    a.cnt[q] = unpack(pk, 41, 14);
+    a.height[q] = (uint8_t)unpack(pk, 55, 8);
+    if (!a.final_roff) a.res[q] = 3 * ((lc >= 0) + (rc >= 0));
   }
 
   // ---- 6. residue offsets (when every body of the batch is built here):
   // body j's residues start at 3 off[j] - 6 j; inside the body, an exclusive
   // prefix of the residue sizes in node-id order
   if (a.final_roff) {
-    __syncthreads();
     const int nn = n - 1;
     const int per = (nn + THREADS - 1) / THREADS;
     const int g0 = min(nn, tid * per), g1 = min(nn, g0 + per);
     int32_t sum = 0;
-    for (int g = g0; g < g1; ++g) sum += a.res[nb + g];
+    for (int g = g0; g < g1; ++g) sum += residue_size(slot[g]);
     int32_t run = block_excl_scan<THREADS>(sum, sh, nullptr) + (int32_t)(3 * o - 6 * (int64_t)j);
     for (int g = g0; g < g1; ++g) {
-      const int32_t v = a.res[nb + g];
       a.res[nb + g] = run;
-      run += v;
+      run += residue_size(slot[g]);
     }
   }
 }
