@@ -30,7 +30,7 @@ void free_all(Ctx& c) {
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
                 c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage,
-                c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.topv,
+                c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.seg_r, c.topv,
                 c.top_off, c.nseg, c.srw, c.xblk};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -116,6 +116,7 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.prw, nodes + 1));
     ZQ_TRY(grow(&c.seg_flag, nodes));
     ZQ_TRY(grow(&c.seg, nodes));
+    ZQ_TRY(grow(&c.seg_r, nodes));
     ZQ_TRY(grow(&c.topv, nodes));
     ZQ_TRY(grow(&c.top_off, m + 1));
     ZQ_TRY(grow(&c.nseg, 2));

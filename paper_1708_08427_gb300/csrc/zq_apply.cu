@@ -37,7 +37,9 @@ struct SweepArgs {
   const uint8_t* ph;       // heights
   const uint32_t* prw;     // record offsets, 4-word units
   const int4* seg;         // segments
+  const int32_t* seg_r;    // residue offset of each segment's first node
   const int32_t* nseg;     // device count of segments
+  int64_t R;               // residues
   const int32_t* topv;     // top nodes by body
   const int32_t* top_off;  // [m + 1]
   const T* rec;
@@ -100,6 +102,19 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
                  "r"(len)
                  : "memory");
   }
+}
+
+// The same for the part of [p, p + bytes) that lies inside whole 16-byte
+// granules of the array [base, base + limit) (the bulk prefetch takes
+// 16-byte aligned ranges; nothing outside the array is touched).
+__device__ __forceinline__ void prefetch_l2_inside(const void* base, int64_t limit, const void* p, int64_t bytes) {
+  const uintptr_t b0 = reinterpret_cast<uintptr_t>(base), b1 = b0 + (uintptr_t)limit;
+  const uintptr_t p0 = reinterpret_cast<uintptr_t>(p);
+  uintptr_t lo = p0 & ~(uintptr_t)15, hi = (p0 + (uintptr_t)bytes + 15) & ~(uintptr_t)15;
+  const uintptr_t in_lo = (b0 + 15) & ~(uintptr_t)15, in_hi = b1 & ~(uintptr_t)15;
+  lo = lo < in_lo ? in_lo : lo;
+  hi = hi > in_hi ? in_hi : hi;
+  if (hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
 }
 
 // Height boundaries of a segment: hb[h] = first local index of height h,
@@ -338,6 +353,8 @@ __global__ void __launch_bounds__(kSegThreads) k_down_seg(SweepArgs<T> a) {
     if (threadIdx.x < 32) {
       const uint32_t w0 = a.prw[p0], w1 = a.prw[p0 + nn];
       prefetch_l2(a.rec + 4 * (int64_t)w0, (w1 - w0) * 4u * (uint32_t)sizeof(T));
+      // the segment's residue coefficients: 3 (nn - 1) values from seg_r
+      prefetch_l2_inside(a.in, a.R * (int64_t)sizeof(T), a.in + a.seg_r[i], 3 * (int64_t)(nn - 1) * sizeof(T));
     }
     if (threadIdx.x < 6)
       info[6 * (nn - 1) + threadIdx.x] =
@@ -597,7 +614,7 @@ SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   SweepArgs<T> a;
   a.N = c.N; a.perm = c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
   a.prw = reinterpret_cast<const uint32_t*>(c.prw);
-  a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
+  a.seg = c.seg; a.seg_r = c.seg_r; a.R = c.R; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;
   a.bead_body = c.bead_body; a.root_out = nullptr; a.root_in = nullptr; a.rot = nullptr;
   return a;

@@ -107,7 +107,8 @@ __global__ void k_top_scatter(int64_t nodes, const int32_t* __restrict__ cnt, co
 
 // One block per segment: range, height order, positions, per-position data.
 __global__ void __launch_bounds__(kThreads)
-k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, const int64_t* __restrict__ off,
+k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* __restrict__ seg_r,
+            const int64_t* __restrict__ off,
             const int32_t* __restrict__ bead_body, const int32_t* __restrict__ first,
             const int32_t* __restrict__ cnt, const int32_t* __restrict__ cl, const int32_t* __restrict__ cr,
             const int32_t* __restrict__ roff, const uint8_t* __restrict__ height, int32_t* __restrict__ pos_of,
@@ -123,6 +124,7 @@ k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, const int6
       const int32_t j = bead_body[f];
       info = make_int4(f - j, c - 1, f, c == (int32_t)(off[j + 1] - off[j]) ? 1 : 0);
       seg[i] = info;
+      seg_r[i] = roff[f - j];  // the subtree's nodes are ids [f - j, f - j + c - 1)
     }
     for (int h = threadIdx.x; h <= kMaxHeight; h += blockDim.x) hist[h] = 0;
     __syncthreads();
@@ -174,7 +176,7 @@ zq_status launch_segments(Ctx& c) {
   ZQ_TRY_STATUS(launch_exclusive_scan(c, top_cnt, c.top_off, m, c.scan_tmp, c.top_off + m));
   time_begin(c, "segments");
   k_top_scatter<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.first, c.bead_body, c.top_off, top_cnt + m, c.topv);
-  k_seg_order<<<c.num_sms * 8, kThreads, 0, s>>>(c.nseg, c.seg, c.off, c.bead_body, c.first, c.cnt, c.cl,
+  k_seg_order<<<c.num_sms * 8, kThreads, 0, s>>>(c.nseg, c.seg, c.seg_r, c.off, c.bead_body, c.first, c.cnt, c.cl,
                                                  c.cr, c.roff, c.height, c.pos_of, c.pnode, c.pc, c.proff,
                                                  c.ph, c.prw);
   time_end(c, "segments");
