@@ -131,12 +131,26 @@ k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* _
     const int32_t a = info.x, nn = info.y;
     for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) atomicAdd(&hist[height[a + t]], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int32_t run = 0;
-      for (int h = 0; h <= kMaxHeight; ++h) {
-        const int32_t v = hist[h];
-        hist[h] = run;
-        run += v;
+    if (threadIdx.x < 32) {  // exclusive scan of the height counts by the first warp
+      constexpr int kPer = (kMaxHeight + 1 + 31) / 32;
+      const int lane = threadIdx.x, h0 = lane * kPer;
+      int32_t v[kPer], t = 0;
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        v[e] = h0 + e <= kMaxHeight ? hist[h0 + e] : 0;
+        t += v[e];
+      }
+      int32_t inc = t;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+      }
+      int32_t run = inc - t;
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        if (h0 + e <= kMaxHeight) hist[h0 + e] = run;
+        run += v[e];
       }
     }
     __syncthreads();

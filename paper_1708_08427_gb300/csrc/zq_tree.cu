@@ -255,18 +255,46 @@ __device__ inline int node_bucket(const uint8_t* __restrict__ height, const int3
   return bucket_of(height[q], (cl[q] >= 0) + (cr[q] >= 0), cut);
 }
 
+// Warp w of block k takes the nodes [k kBTile + w kBRounds 32, + kBRounds 32)
+// in rounds of 32 consecutive ids (coalesced loads); lanes with the same
+// bucket are ranked by ballots in lane order, so ids keep their order
+// inside each bucket (a stable counting sort).
+constexpr int kBWarps = kThreads / 32;
+constexpr int kBRounds = kBTile / kThreads;
+static_assert(kMaxBuckets <= 64, "bucket ids are 6-bit digits");
+
+__device__ __forceinline__ void warp_bucket_counts(const uint8_t* __restrict__ height,
+                                                   const int32_t* __restrict__ cl,
+                                                   const int32_t* __restrict__ cr, int64_t nodes, int cut,
+                                                   int64_t base, int32_t* __restrict__ wc) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kBRounds; ++r) {
+    const int64_t q = base + r * 32 + lane;
+    const bool v = q < nodes;
+    const int b = v ? node_bucket(height, cl, cr, q, cut) : 0;
+    const unsigned peers = digit_peers<6>(b, v);
+    if (v && (peers & lt) == 0) wc[b] += __popc(peers);
+    __syncwarp();
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_bucket_count(const uint8_t* __restrict__ height, const int32_t* __restrict__ cl,
                const int32_t* __restrict__ cr, int64_t nodes, int cut, int nb,
                int32_t* __restrict__ hist, int64_t nblk) {
-  __shared__ int32_t cnt[kMaxBuckets];
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
+  __shared__ int32_t wc[kBWarps][kMaxBuckets];
+  for (int i = threadIdx.x; i < kBWarps * kMaxBuckets; i += blockDim.x) (&wc[0][0])[i] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kBTile + (int64_t)threadIdx.x * kBItems;
-  for (int i = 0; i < kBItems; ++i)
-    if (base + i < nodes) atomicAdd(&cnt[node_bucket(height, cl, cr, base + i, cut)], 1);
+  const int warp = threadIdx.x >> 5;
+  warp_bucket_counts(height, cl, cr, nodes, cut, (int64_t)blockIdx.x * kBTile + warp * kBRounds * 32, wc[warp]);
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(int64_t)b * nblk + blockIdx.x] = cnt[b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    int32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kBWarps; ++w) t += wc[w][b];
+    hist[(int64_t)b * nblk + blockIdx.x] = t;
+  }
 }
 
 // Stable scatter: nodes keep increasing id order inside each bucket.
@@ -275,55 +303,39 @@ k_bucket_scatter(const uint8_t* __restrict__ height, const int32_t* __restrict__
                  const int32_t* __restrict__ cr, int64_t nodes, int cut, int nb,
                  const int32_t* __restrict__ hist, int64_t nblk, int32_t* __restrict__ sid,
                  int32_t* __restrict__ slot_of) {
-  extern __shared__ int32_t cur[];  // [nb][kThreads]
-  __shared__ int32_t sh[33], bb[kMaxBuckets];
-  const int t = threadIdx.x;
-  for (int b = 0; b < nb; ++b) cur[b * kThreads + t] = 0;
-  const int64_t base = (int64_t)blockIdx.x * kBTile + (int64_t)t * kBItems;
-  for (int i = 0; i < kBItems; ++i)
-    if (base + i < nodes) ++cur[node_bucket(height, cl, cr, base + i, cut) * kThreads + t];
+  __shared__ int32_t wc[kBWarps][kMaxBuckets];
+  for (int i = threadIdx.x; i < kBWarps * kMaxBuckets; i += blockDim.x) (&wc[0][0])[i] = 0;
   __syncthreads();
-  // exclusive scan of cur in (bucket, thread) order: thread t owns entries
-  // [t * nb, (t + 1) * nb) of the flattened array
-  int32_t s = 0;
-  for (int f = t * nb; f < (t + 1) * nb; ++f) s += cur[f];
-  const int lane = t & 31, warp = t >> 5;
-  int32_t inc = s;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d) inc += o;
-  }
-  if (lane == 31) sh[warp] = inc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kBTile + warp * kBRounds * 32;
+  warp_bucket_counts(height, cl, cr, nodes, cut, base, wc[warp]);
   __syncthreads();
-  if (warp == 0) {
-    int32_t wv = (lane < kThreads / 32) ? sh[lane] : 0;
-    int32_t wi = wv;
+  // first slot of (bucket b, warp w): the block's start in b, then the
+  // counts of the warps before w
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    int32_t run = hist[(int64_t)b * nblk + blockIdx.x];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      int32_t o = __shfl_up_sync(0xffffffffu, wi, d);
-      if (lane >= d) wi += o;
+    for (int w = 0; w < kBWarps; ++w) {
+      const int32_t t = wc[w][b];
+      wc[w][b] = run;
+      run += t;
     }
-    sh[lane] = wi - wv;
   }
   __syncthreads();
-  int32_t run = inc - s + sh[warp];
-  for (int f = t * nb; f < (t + 1) * nb; ++f) {
-    const int32_t v = cur[f];
-    cur[f] = run;
-    run += v;
-  }
-  __syncthreads();
-  for (int b = t; b < nb; b += kThreads) bb[b] = cur[b * kThreads];
-  __syncthreads();
-  for (int i = 0; i < kBItems; ++i) {
-    const int64_t q = base + i;
-    if (q < nodes) {
-      const int b = node_bucket(height, cl, cr, q, cut);
-      const int32_t pos = hist[(int64_t)b * nblk + blockIdx.x] + (cur[b * kThreads + t]++ - bb[b]);
+  for (int r = 0; r < kBRounds; ++r) {
+    const int64_t q = base + r * 32 + lane;
+    const bool v = q < nodes;
+    const int b = v ? node_bucket(height, cl, cr, q, cut) : 0;
+    const unsigned peers = digit_peers<6>(b, v);
+    if (v) {
+      const int32_t pos = wc[warp][b] + __popc(peers & lt);
       sid[pos] = (int32_t)q;
       slot_of[q] = pos;
     }
+    __syncwarp();
+    if (v && (peers & lt) == 0) wc[warp][b] += __popc(peers);
+    __syncwarp();
   }
 }
 
@@ -442,11 +454,9 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   time_end(c, "schedule");
   st = launch_exclusive_scan(c, hist, hist, nb * nblk, tmp, nullptr);
   if (st != ZQ_OK) return st;
-  const size_t smem = (size_t)nb * kThreads * sizeof(int32_t);
-  ZQ_CUDA_TRY(cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   time_begin(c, "schedule");
-  k_bucket_scatter<<<(unsigned)nblk, kThreads, smem, s>>>(c.height, c.cl, c.cr, c.nodes, c.cut, nb, hist,
-                                                         nblk, c.sid, c.slot_of);
+  k_bucket_scatter<<<(unsigned)nblk, kThreads, 0, s>>>(c.height, c.cl, c.cr, c.nodes, c.cut, nb, hist, nblk,
+                                                      c.sid, c.slot_of);
   time_end(c, "schedule");
   time_begin(c, "schedule");
   k_bucket_starts<<<1, 128, 0, s>>>(hist, nblk, nb, c.nodes, c.bstart);
