@@ -15,8 +15,9 @@
 // Four kernels and two scans, all on the device (no host synchronisation:
 // the number of segments is a device value that the grid-stride kernels
 // read):
-//   classify     per node: parents mark their children that are segment
-//                roots (and body roots mark themselves); top nodes are
+//   classify     per node: parents list their children that are segment
+//                roots (and body roots list themselves) with the segment's
+//                node range, first bead and residue offset; top nodes are
 //                counted per body and get their per-position data here
 //                (a child segment root sits at the last position of its
 //                segment, which follows from its count alone);
@@ -35,10 +36,11 @@ constexpr int kThreads = 256;
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-// Appends the flagged lanes' values (one atomic per warp; all 32 lanes of
-// the warp must call).
-__device__ __forceinline__ void warp_append(bool flag, int32_t value, int32_t* __restrict__ count,
-                                            int4* __restrict__ list) {
+// Appends the flagged lanes' segments (one atomic per warp; all 32 lanes
+// of the warp must call): seg = (first node position, nodes, first sorted
+// bead, whole body?), seg_r = residue offset of the first node.
+__device__ __forceinline__ void warp_append(bool flag, int4 value, int32_t r, int32_t* __restrict__ count,
+                                            int4* __restrict__ list, int32_t* __restrict__ list_r) {
   const unsigned b = __ballot_sync(0xffffffffu, flag);
   if (!b) return;
   const int lane = threadIdx.x & 31;
@@ -46,7 +48,21 @@ __device__ __forceinline__ void warp_append(bool flag, int32_t value, int32_t* _
   int32_t base = 0;
   if (lane == leader) base = atomicAdd(count, __popc(b));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (flag) list[base + __popc(b & ((1u << lane) - 1u))] = make_int4(value, 0, 0, 0);
+  if (flag) {
+    const int32_t i = base + __popc(b & ((1u << lane) - 1u));
+    list[i] = value;
+    list_r[i] = r;
+  }
+}
+
+// The segment whose root is internal node c of body j (its nodes are the
+// ids [first - j, first - j + count - 1)).
+__device__ __forceinline__ int4 segment_of(int32_t c, int32_t j, bool whole, const int32_t* __restrict__ cnt,
+                                           const int32_t* __restrict__ first, const int32_t* __restrict__ roff,
+                                           int32_t* r) {
+  const int32_t f = first[c], k = cnt[c];
+  *r = roff[f - j];
+  return make_int4(f - j, k - 1, f, whole ? 1 : 0);
 }
 
 // Position of a child code as the sweeps see it: a leaf stays a leaf, a
@@ -65,12 +81,15 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
                            const int32_t* __restrict__ cr, const int32_t* __restrict__ cnt,
                            const int32_t* __restrict__ first, const int32_t* __restrict__ bead_body,
                            const int32_t* __restrict__ roff, const uint8_t* __restrict__ height,
-                           int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* __restrict__ top_cnt,
+                           int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* __restrict__ seg_r,
+                           int32_t* __restrict__ top_cnt,
                            int32_t* __restrict__ pos_of, int32_t* __restrict__ pnode, int2* __restrict__ pc,
                            int32_t* __restrict__ proff, uint8_t* __restrict__ ph, int32_t* __restrict__ units) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool self_root = false, left_root = false, right_root = false;
   int32_t a = -1, b = -1;
+  int4 sq = make_int4(0, 0, 0, 0), sa = sq, sb = sq;
+  int32_t rq = 0, ra = 0, rb = 0;
   if (q < nodes) {
     a = cl[q];
     b = cr[q];
@@ -79,9 +98,12 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
     const int32_t j = bead_body[f];
     if (c <= kSegMax) {
       self_root = c == (int32_t)(off[j + 1] - off[j]);  // a whole body of at most kSegMax beads
+      if (self_root) sq = segment_of((int32_t)q, j, true, cnt, first, roff, &rq);
     } else {
       left_root = a >= 0 && cnt[a] <= kSegMax;
       right_root = b >= 0 && cnt[b] <= kSegMax;
+      if (left_root) sa = segment_of(a, j, false, cnt, first, roff, &ra);
+      if (right_root) sb = segment_of(b, j, false, cnt, first, roff, &rb);
       atomicAdd(&top_cnt[j], 1);
       pos_of[q] = (int32_t)q;
       pnode[q] = (int32_t)q;
@@ -91,9 +113,9 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
       units[q] = rec_words((a >= 0) + (b >= 0)) / 4;
     }
   }
-  warp_append(self_root, (int32_t)q, nseg, seg);
-  warp_append(left_root, a, nseg, seg);
-  warp_append(right_root, b, nseg, seg);
+  warp_append(self_root, sq, rq, nseg, seg, seg_r);
+  warp_append(left_root, sa, ra, nseg, seg, seg_r);
+  warp_append(right_root, sb, rb, nseg, seg, seg_r);
 }
 
 __global__ void k_top_scatter(int64_t nodes, const int32_t* __restrict__ cnt, const int32_t* __restrict__ first,
@@ -107,10 +129,8 @@ __global__ void k_top_scatter(int64_t nodes, const int32_t* __restrict__ cnt, co
 
 // One block per segment: range, height order, positions, per-position data.
 __global__ void __launch_bounds__(kThreads)
-k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* __restrict__ seg_r,
-            const int64_t* __restrict__ off,
-            const int32_t* __restrict__ bead_body, const int32_t* __restrict__ first,
-            const int32_t* __restrict__ cnt, const int32_t* __restrict__ cl, const int32_t* __restrict__ cr,
+k_seg_order(const int32_t* __restrict__ nseg, const int4* __restrict__ seg, const int32_t* __restrict__ cl,
+            const int32_t* __restrict__ cr,
             const int32_t* __restrict__ roff, const uint8_t* __restrict__ height, int32_t* __restrict__ pos_of,
             int32_t* __restrict__ pnode, int2* __restrict__ pc, int32_t* __restrict__ proff,
             uint8_t* __restrict__ ph, int32_t* __restrict__ units) {
@@ -118,14 +138,7 @@ k_seg_order(const int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* _
   __shared__ int4 info;
   const int ns = *nseg;
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
-    if (threadIdx.x == 0) {
-      const int32_t r = seg[i].x;
-      const int32_t f = first[r], c = cnt[r];
-      const int32_t j = bead_body[f];
-      info = make_int4(f - j, c - 1, f, c == (int32_t)(off[j + 1] - off[j]) ? 1 : 0);
-      seg[i] = info;
-      seg_r[i] = roff[f - j];  // the subtree's nodes are ids [f - j, f - j + c - 1)
-    }
+    if (threadIdx.x == 0) info = seg[i];
     for (int h = threadIdx.x; h <= kMaxHeight; h += blockDim.x) hist[h] = 0;
     __syncthreads();
     const int32_t a = info.x, nn = info.y;
@@ -184,15 +197,14 @@ zq_status launch_segments(Ctx& c) {
   ZQ_CUDA_TRY(cudaMemsetAsync(top_cnt, 0, 2 * m * sizeof(int32_t), s));
   time_begin(c, "segments");
   k_classify<<<blocks(n), kThreads, 0, s>>>(n, c.off, c.cl, c.cr, c.cnt, c.first, c.bead_body, c.roff,
-                                            c.height, c.nseg, c.seg, top_cnt, c.pos_of, c.pnode, c.pc,
+                                            c.height, c.nseg, c.seg, c.seg_r, top_cnt, c.pos_of, c.pnode, c.pc,
                                             c.proff, c.ph, c.prw);
   time_end(c, "segments");
   ZQ_TRY_STATUS(launch_exclusive_scan(c, top_cnt, c.top_off, m, c.scan_tmp, c.top_off + m));
   time_begin(c, "segments");
   k_top_scatter<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.first, c.bead_body, c.top_off, top_cnt + m, c.topv);
-  k_seg_order<<<c.num_sms * 8, kThreads, 0, s>>>(c.nseg, c.seg, c.seg_r, c.off, c.bead_body, c.first, c.cnt, c.cl,
-                                                 c.cr, c.roff, c.height, c.pos_of, c.pnode, c.pc, c.proff,
-                                                 c.ph, c.prw);
+  k_seg_order<<<c.num_sms * 8, kThreads, 0, s>>>(c.nseg, c.seg, c.cl, c.cr, c.roff, c.height, c.pos_of,
+                                                 c.pnode, c.pc, c.proff, c.ph, c.prw);
   time_end(c, "segments");
   ZQ_TRY_STATUS(launch_exclusive_scan(c, c.prw, c.prw, n, c.scan_tmp, c.prw + n));
   ZQ_CUDA_TRY(cudaGetLastError());
