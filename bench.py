@@ -300,8 +300,13 @@ def run_ours(args, world, rank, local):
 
         args.cut, tuned = tune_level_cut(ctx, bt.off, x, y, z, v, qv, w, qtw)
 
-    def step(prec_t=torch.float32, vv=v, ww=w, oq=qv, oqt=qtw):
-        ctx.pipeline(bt.off, x, y, z, vv, oq, ww, oqt, level_cut=args.cut)
+    # the step is one zq_pipeline call; with graphs on, the library captures
+    # it once and replays it (ZQ_GRAPH), the timing events included
+    def step(graph=not args.no_graph):
+        ctx.pipeline(bt.off, x, y, z, v, qv, w, qtw, level_cut=args.cut, graph=graph)
+
+    def step_direct():
+        step(graph=False)
 
     for _ in range(max(args.warmup, 1)):
         step()
@@ -334,8 +339,7 @@ def run_ours(args, world, rank, local):
                    key=lambda k: phases.get(k, 0.0)) if phases else "build_level"
 
     # --- the dominant kernel is bracketed by events in every timed step
-    # (event records captured inside a CUDA graph carry no timing, so the
-    # timed steps are direct launches; the graph replay is timed separately)
+    # (external event records: in a replayed step they are graph nodes)
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0.record(stream)
     k1.record(stream)
@@ -411,7 +415,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded numpy generators; no dataset)",
         "config": {"workload": desc, "m": m, "N": N, "residues": R, "level_cut": args.cut,
                    "level_cut_tuning_ms": tuned,
-                   "graph": False, "prec": "fp32", "build": args.build,
+                   "graph": not args.no_graph, "prec": "fp32", "build": args.build,
                    "step": "tree + FP64 transforms + Q~v + Q~^T w (one C-ABI call, zq_pipeline)",
                    "l2": "512 MB buffer written before every step, outside the step events",
                    "wall_s_timed_region": wall},
@@ -420,14 +424,19 @@ def run_ours(args, world, rank, local):
     }
 
     if not args.no_graph:
-        out["graph_replay"] = timed(args, step, stream, flush, world, dev, N, graph=True)
+        # the same step without the library's graph, captured by torch instead
+        out["graph_replay"] = timed(args, step_direct, stream, flush, world, dev, N, graph=True)
+        out["direct_launches"] = timed(args, step_direct, stream, flush, world, dev, N, graph=False)
+        # the library's graph without the kernel-timing event nodes of the timed steps
+        out["library_graph_untimed"] = timed(args, step, stream, flush, world, dev, N, graph=False)
     legs = set() if args.no_extras else (
         {"build_other", "fp64_step", "apply", "qgen", "e2e", "multirhs", "bd_loop", "cpu"}
         if args.extras == "all" else set(args.extras.split(",")))
     if "build_other" in legs:
         other = "fp64" if args.build == "dd" else "dd"
         ctx.set_build_arith(other)
-        out[f"build_{other}_step"] = timed(args, step, stream, flush, world, dev, N, graph=not args.no_graph)
+        out[f"build_{other}_step"] = timed(args, step_direct, stream, flush, world, dev, N,
+                                           graph=not args.no_graph)
         ctx.set_build_arith(args.build)
     if "fp64_step" in legs:
         out["fp64_step"] = fp64_step(args, ctx, bt, stream, flush, rng, world, dev)
@@ -595,7 +604,7 @@ def e2e(args, ctx, bt, stream, world, dev):
     hqt = torch.empty((3, N), dtype=torch.float32).pin_memory()
 
     def fn():
-        ctx.pipeline(bt.off, hx, hy, hz, hv, hq, hw, hqt, level_cut=args.cut, host=True)
+        ctx.pipeline(bt.off, hx, hy, hz, hv, hq, hw, hqt, level_cut=args.cut, host=True, graph=not args.no_graph)
 
     for _ in range(2):
         fn()

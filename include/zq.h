@@ -231,6 +231,15 @@ zq_status zq_apply_QT_block(zq_ctx *ctx, zq_prec prec, int64_t k, const void *W,
  *                    device buffers it owns (allocated on first use).
  *   ZQ_KEEP_TREE     keep the current tree (same bodies, beads moved):
  *                    only the transforms are rebuilt; m and off must match.
+ *   ZQ_GRAPH         run the step as a CUDA graph: a call whose arguments
+ *                    (pointers, sizes, offsets, flags, level cut) and plan
+ *                    equal those of the captured step replays it with one
+ *                    launch; otherwise the call captures itself (or, when
+ *                    it must plan first, runs directly).  The buffers must
+ *                    hold the new inputs when the replay runs, as for any
+ *                    asynchronous call.  The zq_time_kernel events are
+ *                    recorded in every replay.  Ignored on the legacy
+ *                    default stream.
  * Only the transform copy of the requested precision is refreshed, so a
  * later zq_apply_Q / zq_apply_QT must use the same precision (else
  * ZQ_ESTATE).  Asynchronous; the results are ready after zq_sync.  When m,
@@ -239,19 +248,24 @@ zq_status zq_apply_QT_block(zq_ctx *ctx, zq_prec prec, int64_t k, const void *W,
  * only). */
 #define ZQ_HOST_BUFFERS 1
 #define ZQ_KEEP_TREE 2
+#define ZQ_GRAPH 4
 zq_status zq_pipeline(zq_ctx *ctx, zq_prec prec, int64_t m, const int64_t *off, const double *x,
                       const double *y, const double *z, const void *v, void *qv, const void *w,
                       void *qtw, int32_t level_cut, int32_t flags);
 
 /* Measurement hook: while set, every launch of the named kernel is
- * bracketed by cudaEventRecord(start_event) / cudaEventRecord(stop_event)
- * (cudaEvent_t handles owned by the caller) on the context's stream, also
- * inside a CUDA-graph capture.  Names: "bead_body", "aabb", "keys",
- * "sort_small", "sort_radix", "sort_radix_count", "lcp", "bottom_up",
- * "scan", "schedule", "build_level", "build_tail", "up_level", "up_tail",
- * "down_tail", "down_level".  When one API call launches the named kernel
- * several times (one launch per height), start is recorded before its
- * first launch and stop after its last launch in that call. */
+ * bracketed by records of start_event / stop_event (cudaEvent_t handles
+ * owned by the caller) on the stream it is launched on.  The records are
+ * external (cudaEventRecordExternal), so a captured step (ZQ_GRAPH, or a
+ * caller's own capture) records them at every replay.  Names:
+ * "small_tree" (the per-body tree kernels), "bead_body", "aabb", "keys",
+ * "sort_radix", "sort_radix_count", "lcp", "bottom_up" (bodies over 8192
+ * beads), "scan", "segments", "schedule", "build_level" (the Case I kernel
+ * and one launch per height up to the level cut), "build_tail",
+ * "up_seg", "up_top", "down_top", "down_seg", their "_blk" block-form
+ * variants, "qgen", "count_table".  When one API call launches the named
+ * kernel several times, start is recorded before its first launch and
+ * stop after its last launch in that call. */
 zq_status zq_time_kernel(zq_ctx *ctx, const char *name, void *start_event, void *stop_event);
 
 /* Arithmetic of the node-transform build.  ZQ_BUILD_FP64: native double

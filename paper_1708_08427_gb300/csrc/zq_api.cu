@@ -181,6 +181,8 @@ zq_status zq_destroy(zq_ctx* ctx) {
   if (!ctx) return ZQ_EINVAL;
   cudaSetDevice(ctx->c.device);
   cudaStreamSynchronize(ctx->c.stream);
+  if (ctx->c.gexec) cudaGraphExecDestroy(ctx->c.gexec);
+  ctx->c.gexec = nullptr;
   destroy_streams(ctx->c);
   free_all(ctx->c);
   delete ctx;
@@ -213,6 +215,7 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
     return ZQ_OK;
   }
   const int64_t hist_words = zq::sort_hist_words(max_big);
+  ++c.plan_gen;  // a new plan, possibly new buffers: captured steps are stale
   ZQ_TRY(ensure_capacity(c, N, m, hist_words));
   c.N = N;
   c.m = m;
@@ -429,9 +432,9 @@ zq_status zq_apply_rotated(zq_ctx* ctx, zq_prec prec, const double* R, const voi
   return apply_two(ctx, prec, R, v, qv, w, qtw);
 }
 
-zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
-                      const double* y, const double* z, const void* v, void* qv, const void* w,
-                      void* qtw, int32_t level_cut, int32_t flags) {
+static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
+                               const double* y, const double* z, const void* v, void* qv, const void* w,
+                               void* qtw, int32_t level_cut, int32_t flags) {
   if (!ctx || !off || !x || !y || !z || m < 1) return ZQ_EINVAL;
   if (prec != ZQ_FP32 && prec != ZQ_FP64) return ZQ_EINVAL;
   if ((v == nullptr) != (qv == nullptr) || (w == nullptr) != (qtw == nullptr)) return ZQ_EINVAL;
@@ -451,6 +454,7 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
     // staging layout: x y z (N doubles each) | v (3N) | qtw (3N) | w (R) | qv (R)
     const int64_t bytes = 3 * N * 8 + (int64_t)es * (6 * N + 2 * R);
     if (bytes > c.stage_cap) {
+      ++c.plan_gen;
       if (c.stage) cudaFree(c.stage);
       c.stage = nullptr;
       c.stage_cap = 0;
@@ -670,3 +674,61 @@ zq_status zq_get_records(zq_ctx* ctx, double* rec) {
 }
 
 }  // extern "C"
+
+// ZQ_GRAPH: the step is captured once as a CUDA graph and replayed while
+// the arguments and the plan are unchanged.  A call that would plan (new
+// bodies, level cut or buffers) runs directly; the next one captures.
+zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
+                      const double* y, const double* z, const void* v, void* qv, const void* w,
+                      void* qtw, int32_t level_cut, int32_t flags) {
+  if (!(flags & ZQ_GRAPH) || !ctx) return pipeline_body(ctx, prec, m, off, x, y, z, v, qv, w, qtw, level_cut, flags);
+  flags &= ~ZQ_GRAPH;
+  Ctx& c = ctx->c;
+  // the legacy default stream cannot be captured
+  if (!c.stream || !off || m < 1) return pipeline_body(ctx, prec, m, off, x, y, z, v, qv, w, qtw, level_cut, flags);
+  const int32_t cut = level_cut == 0 ? zq::kDefaultCut : level_cut;
+  std::vector<uintptr_t> key = {(uintptr_t)prec, (uintptr_t)m, (uintptr_t)cut, (uintptr_t)flags,
+                                (uintptr_t)c.build_dd, (uintptr_t)x, (uintptr_t)y, (uintptr_t)z, (uintptr_t)v,
+                                (uintptr_t)qv, (uintptr_t)w, (uintptr_t)qtw};
+  key.insert(key.end(), off, off + m + 1);
+  // the kernel-timing hook is part of the captured step
+  key.push_back((uintptr_t)c.time_ev0);
+  key.push_back((uintptr_t)c.time_ev1);
+  for (const char* t = c.time_name; *t; ++t) key.push_back((uintptr_t)(unsigned char)*t);
+  ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  const bool warm = c.have_tree && m == c.m && cut == c.cut && std::equal(off, off + m + 1, c.off_h.begin());
+  const int64_t N = off[m], R = 3 * N - 6 * m;
+  const int64_t stage_bytes = 3 * N * 8 + (int64_t)(prec == ZQ_FP64 ? 8 : 4) * (6 * N + 2 * R);
+  const bool staged = !(flags & ZQ_HOST_BUFFERS) || stage_bytes <= c.stage_cap;
+  key.push_back((uintptr_t)c.plan_gen);
+  if (c.gexec && warm && staged && key == c.gkey) {
+    c.time_started = false;
+    ZQ_CUDA_TRY(cudaGraphLaunch(c.gexec, c.stream));
+    c.launches += c.glaunches;
+    c.have_xform = true;
+    c.have64 = prec == ZQ_FP64;
+    c.have32 = prec == ZQ_FP32;
+    return ZQ_OK;
+  }
+  if (!warm || !staged) return pipeline_body(ctx, prec, m, off, x, y, z, v, qv, w, qtw, level_cut, flags);
+  // capture this call's work (nothing runs until the launch below)
+  ZQ_CUDA_TRY(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+  const int64_t l0 = c.launches;
+  const zq_status st = pipeline_body(ctx, prec, m, off, x, y, z, v, qv, w, qtw, level_cut, flags);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c.stream, &g);
+  if (st != ZQ_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return st != ZQ_OK ? st : ZQ_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return ZQ_ECUDA;
+  if (c.gexec) cudaGraphExecDestroy(c.gexec);
+  c.gexec = ex;
+  c.gkey = key;
+  c.glaunches = c.launches - l0;
+  ZQ_CUDA_TRY(cudaGraphLaunch(c.gexec, c.stream));
+  return ZQ_OK;
+}

@@ -154,6 +154,12 @@ struct Ctx {
   // staging for host-buffer calls (bytes)
   void* stage = nullptr;
   int64_t stage_cap = 0;
+  // a step captured as a CUDA graph (zq_pipeline with ZQ_GRAPH): replayed
+  // while every argument and the plan generation are unchanged
+  uint64_t plan_gen = 0;         // bumped whenever the launch plan or a buffer changes
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uintptr_t> gkey;
+  int64_t glaunches = 0;         // kernels in the captured step
   // kernel timing hook
   char time_name[32] = {0};
   cudaEvent_t time_ev0 = nullptr, time_ev1 = nullptr;
@@ -163,15 +169,23 @@ struct Ctx {
 
 // Every kernel launch goes through time_begin / time_end: counts the launch
 // and brackets it with the caller's events when it is the timed kernel.
+// The records are external, so inside a captured step (ZQ_GRAPH) they become
+// event-record nodes that time every replay.
+inline void time_record(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+  else cudaEventRecord(ev, s);
+}
 inline void time_begin(Ctx& c, const char* name) {
   ++c.launches;
   if (c.time_ev0 && !c.time_started && __builtin_strcmp(c.time_name, name) == 0) {
-    cudaEventRecord(c.time_ev0, c.stream);
+    time_record(c.time_ev0, c.stream);
     c.time_started = true;
   }
 }
 inline void time_end(const Ctx& c, const char* name) {
-  if (c.time_ev1 && __builtin_strcmp(c.time_name, name) == 0) cudaEventRecord(c.time_ev1, c.stream);
+  if (c.time_ev1 && __builtin_strcmp(c.time_name, name) == 0) time_record(c.time_ev1, c.stream);
 }
 
 // --------------------------------------------------------------- helpers

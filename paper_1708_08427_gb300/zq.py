@@ -20,7 +20,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "_build" / "libzq.so"
 
 ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE = range(7)
 ZQ_FP64, ZQ_FP32, ZQ_BF16 = 0, 1, 2
-ZQ_HOST_BUFFERS, ZQ_KEEP_TREE = 1, 2
+ZQ_HOST_BUFFERS, ZQ_KEEP_TREE, ZQ_GRAPH = 1, 2, 4
 ZQ_BUILD_DD, ZQ_BUILD_FP64 = 0, 1
 
 _vp = ctypes.c_void_p
@@ -335,17 +335,19 @@ class Context:
         return out.reshape(3, N) if squeeze else out
 
     def pipeline(self, off, x, y, z, v=None, qv=None, w=None, qtw=None, level_cut: int = 0,
-                 host: bool = False, keep_tree: bool = False, prec: int | None = None):
+                 host: bool = False, keep_tree: bool = False, prec: int | None = None, graph: bool = False):
         """One step: tree, FP64 transforms, qv = Q~ v, qtw = Q~^T w.  With
         host=True all tensors are (pinned) host tensors staged by the
-        library; otherwise device tensors.  off: numpy int64 (m + 1)."""
+        library; otherwise device tensors.  off: numpy int64 (m + 1).
+        graph=True: the library captures the step as a CUDA graph and
+        replays it while the arguments are unchanged (ZQ_GRAPH)."""
         off = np.ascontiguousarray(off, dtype=np.int64)
         self._off = off
         m = off.shape[0] - 1
         ref = v if v is not None else w
         if prec is None:
             prec = self._prec(ref)
-        flags = (ZQ_HOST_BUFFERS if host else 0) | (ZQ_KEEP_TREE if keep_tree else 0)
+        flags = (ZQ_HOST_BUFFERS if host else 0) | (ZQ_KEEP_TREE if keep_tree else 0) | (ZQ_GRAPH if graph else 0)
         p = lambda t: None if t is None else _ptr(t)
         _check(_lib().zq_pipeline(self._h, prec, m, off.ctypes.data_as(_i64p), _ptr(x), _ptr(y), _ptr(z),
                                   p(v), p(qv), p(w), p(qtw), int(level_cut), flags), "zq_pipeline")

@@ -188,3 +188,57 @@ def test_level_cut_tuner_picks_a_candidate():
     best, times = tune_level_cut(ctx, bt.off, x, y, z, v, qv, w, qtw, cuts=(4, 15), reps=2, warmup=1)
     assert best in (4, 15) and set(times) == {4, 15} and all(t > 0 for t in times.values())
     ctx.close()
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_pipeline_graph_replay_matches_direct(host):
+    """ZQ_GRAPH: the first call plans and runs directly, the second captures,
+    later calls replay; every call gives the bits of the direct path, also
+    after the inputs change in place.  A call with other arguments or after
+    a new plan is not replayed from the stale graph."""
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=16, nmin=20, nmax=2500, seed=41)
+    rng = np.random.default_rng(43)
+    if host:
+        mk = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+        out = lambda shape: torch.empty(shape, dtype=torch.float32).pin_memory()
+    else:
+        mk = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+        out = lambda shape: torch.empty(shape, dtype=torch.float32, device=dev)
+    x, y, z = (mk(a, torch.float64) for a in (bt.x, bt.y, bt.z))
+    v, w = mk(rng.standard_normal((3, bt.N))), mk(rng.standard_normal(bt.n_residues))
+    qv, qtw = out(bt.n_residues), out((3, bt.N))
+    g = zq.Context(0, torch.cuda.Stream(dev))  # a capturable (non-default) stream
+    d = zq.Context(0, torch.cuda.Stream(dev))
+    torch.cuda.synchronize()
+    l0 = None
+    for it in range(4):
+        if it == 2:  # new inputs in place: the replay reads them
+            v.copy_(mk(rng.standard_normal((3, bt.N))))
+            x.copy_(mk(bt.x + 0.01 * rng.standard_normal(bt.N), torch.float64))
+            torch.cuda.synchronize()
+        g.pipeline(bt.off, x, y, z, v, qv, w, qtw, host=host, graph=True)
+        g.sync()
+        rq, rqt = out(bt.n_residues), out((3, bt.N))
+        d.pipeline(bt.off, x, y, z, v, rq, w, rqt, host=host)
+        d.sync()
+        assert torch.equal(qv, rq) and torch.equal(qtw, rqt), it
+        n = g.launch_count()
+        if l0 is not None and it >= 2:
+            assert n - l0 > 0  # a replay counts the step's kernels
+        l0 = n
+    # another batch on the same context: planned afresh, not the old graph
+    bt2 = W.shell_batch(m=7, nmin=20, nmax=900, seed=44)
+    x2, y2, z2 = (mk(a, torch.float64) for a in (bt2.x, bt2.y, bt2.z))
+    v2 = mk(rng.standard_normal((3, bt2.N)))
+    q2, r2 = out(bt2.n_residues), out(bt2.n_residues)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        g.pipeline(bt2.off, x2, y2, z2, v2, q2, host=host, graph=True)
+        g.sync()
+    d.pipeline(bt2.off, x2, y2, z2, v2, r2, host=host)
+    d.sync()
+    assert torch.equal(q2, r2)
+    g.close()
+    d.close()
