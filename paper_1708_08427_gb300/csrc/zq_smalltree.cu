@@ -78,8 +78,8 @@ __device__ __forceinline__ uint32_t quantise_exact(double p, double lo, double h
 // quotient by a few ulps, so its floor is taken from the bits of s when s
 // is more than 2^-26 from an integer (integer instructions only), and the
 // exact formula is used otherwise.
+// The caller has checked hi > lo (a flat axis quantises to 0).
 __device__ __forceinline__ uint32_t quantise_bits(double p, double lo, double hi, double inv21) {
-  if (!(hi > lo)) return 0u;
   const double s = __dmul_rn(__dsub_rn(p, lo), inv21);
   const unsigned long long b = (unsigned long long)__double_as_longlong(s);
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
@@ -167,8 +167,9 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
       const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        bad |= !isfinite(p[c]);
         const unsigned long long e = ord_encode(p[c]);
+        // NaN or infinite: all exponent bits set (integer test, no FP64 op)
+        bad |= ((unsigned long long)__double_as_longlong(p[c]) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
         mn[c] = e < mn[c] ? e : mn[c];
         mx[c] = e > mx[c] ? e : mx[c];
       }
@@ -200,13 +201,19 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
 
   // ---- 2. keys
   {
+    // per-axis constants in registers; FP64 is 1/64 rate here, so the
+    // flat-axis test is made once, not per bead
+    const double lo[3] = {lim[0], lim[1], lim[2]}, hi[3] = {lim[3], lim[4], lim[5]};
     const double inv[3] = {lim[6], lim[7], lim[8]};
+    bool flat[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) flat[c] = !(hi[c] > lo[c]);
 #pragma unroll 4
     for (int i = tid; i < n; i += THREADS) {
       const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
       uint32_t q[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) q[c] = quantise_bits(p[c], lim[c], lim[3 + c], inv[c]);
+      for (int c = 0; c < 3; ++c) q[c] = flat[c] ? 0u : quantise_bits(p[c], lo[c], hi[c], inv[c]);
       keyA[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
       idxA[i] = (uint16_t)i;
     }
