@@ -47,6 +47,10 @@ namespace zq {
 namespace {
 
 constexpr int kThreads = 256;
+// The level kernel (heights 2..cut) needs 96 registers: blocks of 128 let
+// five fit an SM (20 warps) where blocks of 256 fit two (16 warps).
+constexpr int kLevelThreads = 128;
+constexpr int kLevelBlocksPerSM = 5;
 
 struct BuildArgs {
   const double* x;
@@ -452,7 +456,7 @@ __global__ void __launch_bounds__(kThreads) k_build_case1(BuildArgs a) {
 
 // Heights 2..cut: only nodes with at least one internal child (k = 6, 9).
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_build_level(BuildArgs a, int h) {
+__global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSM) k_build_level(BuildArgs a, int h) {
   const int b0 = 3 * (h - 1);
   const int32_t s1 = a.bstart[b0 + 1], s2 = a.bstart[b0 + 2], s3 = a.bstart[b0 + 3];
   for (int64_t s = s1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s3;
@@ -502,14 +506,14 @@ __global__ void k_count_table_dd(const double* __restrict__ tab, float2* __restr
 
 template <class R>
 zq_status run_build(Ctx& c, const BuildArgs& a) {
-  const int grid = c.num_sms * 4;
+  const int grid = c.num_sms * kLevelBlocksPerSM;
   // one timing bracket around all level launches (few event records in a
   // captured step)
   time_begin(c, "build_level");
   k_build_case1<R><<<c.num_sms * 8, kThreads, 0, c.stream>>>(a);
   for (int h = 2; h <= c.cut; ++h) {
     ++c.launches;
-    k_build_level<R><<<grid, kThreads, 0, c.stream>>>(a, h);
+    k_build_level<R><<<grid, kLevelThreads, 0, c.stream>>>(a, h);
   }
   time_end(c, "build_level");
   time_begin(c, "build_tail");
