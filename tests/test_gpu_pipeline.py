@@ -242,3 +242,43 @@ def test_pipeline_graph_replay_matches_direct(host):
     assert torch.equal(q2, r2)
     g.close()
     d.close()
+
+
+@pytest.mark.parametrize("cut", [15, 18])
+def test_full_size_step_as_benched(cut):
+    """The benchmark's step exactly as bench.py times it: the 2000-shell
+    batch (2,155,957 beads, seed 0), one zq_pipeline call per step in FP32
+    with the double-single build, on a non-default stream, replayed from the
+    library's CUDA graph (ZQ_GRAPH) at the level cut the tuner picks.  The
+    third call is a replay; every output of it is checked per body against
+    the FP64 oracle (1e-5)."""
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=2000, nmin=50, nmax=5000, seed=0)
+    rng = np.random.default_rng(1000)
+    v = rng.standard_normal((3, bt.N))
+    w = rng.standard_normal(bt.n_residues)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        x, y, z = (torch.from_numpy(a.copy()).to(dev) for a in (bt.x, bt.y, bt.z))
+        tv = torch.from_numpy(v).to(dev, torch.float32)
+        tw = torch.from_numpy(w).to(dev, torch.float32)
+        qv = torch.empty(bt.n_residues, device=dev)
+        qtw = torch.empty((3, bt.N), device=dev)
+    stream.synchronize()
+    ctx = zq.Context(0, stream=stream)
+    ctx.set_build_arith("dd")
+    for _ in range(3):  # plan, capture, replay
+        with torch.cuda.stream(stream):  # ordered before the call on its stream
+            qv.fill_(float("nan"))
+            qtw.fill_(float("nan"))
+        ctx.pipeline(bt.off, x, y, z, tv, qv, tw, qtw, level_cut=cut, graph=True)
+    ctx.sync()
+    # the oracle sees the FP32-rounded inputs the kernels saw
+    vr = tv.double().cpu().numpy()
+    wr = tw.double().cpu().numpy()
+    rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*vr), wr)
+    e1 = _per_body(qv.double().cpu().numpy(), rq, bt, "res")
+    e2 = _per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt, "bead")
+    assert max(e1, e2) <= TOL[torch.float32], (e1, e2)
+    ctx.close()
