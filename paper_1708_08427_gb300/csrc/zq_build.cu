@@ -497,6 +497,80 @@ __global__ void __launch_bounds__(kThreads) k_build_tail(BuildArgs a) {
   }
 }
 
+// Nodes above the cut when every body has at most 8192 beads: one warp per
+// body, height by height (__syncwarp orders the lanes' state writes and
+// reads).  Every body's upper chain runs at once instead of one launch per
+// height, and a body's nodes above the cut fit a warp's few passes.  The
+// body's tail slots (contiguous, node-id order) are sorted by height in
+// shared memory when there are at most kWarpTailMax of them; otherwise the
+// warp scans them at every height.
+constexpr int kTailWarps = 4;
+constexpr int kWarpTailMax = 256;
+
+template <class R>
+__global__ void __launch_bounds__(32 * kTailWarps) k_build_tail_warp(BuildArgs a, int32_t m) {
+  __shared__ int32_t ids[kTailWarps][kWarpTailMax];
+  __shared__ int32_t hs[kTailWarps][kMaxHeight + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t j = blockIdx.x * kTailWarps + warp;
+  if (j >= m) return;  // whole warp
+  const int bt = 3 * a.cut;
+  const int32_t t0 = a.bstart[bt], t1 = a.bstart[bt + 1];
+  int32_t lo, hi;
+  id_range(a.sid, t0, t1, a.off[j] - j, a.off[j + 1] - (j + 1), &lo, &hi);
+  const int32_t n = hi - lo;
+  if (n == 0) return;
+  const uint8_t* sh = a.sheight;
+  int hmin = kMaxHeight + 1, hmax = 0;
+  for (int32_t t = lane; t < n; t += 32) {
+    const int h = sh[lo + t];
+    hmin = min(hmin, h);
+    hmax = max(hmax, h);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    hmin = min(hmin, __shfl_xor_sync(0xffffffffu, hmin, d));
+    hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, d));
+  }
+  const bool sorted = n <= kWarpTailMax;
+  if (sorted) {  // counting sort of the slots by height
+    int32_t* H = hs[warp];
+    for (int h = lane; h < kMaxHeight + 2; h += 32) H[h] = 0;
+    __syncwarp();
+    for (int32_t t = lane; t < n; t += 32) atomicAdd(&H[sh[lo + t]], 1);
+    __syncwarp();
+    if (lane == 0) {
+      int32_t run = 0;
+      for (int h = hmin; h <= hmax + 1; ++h) {
+        const int32_t v = H[h];
+        H[h] = run;
+        run += v;
+      }
+    }
+    __syncwarp();
+    for (int32_t t = lane; t < n; t += 32) ids[warp][atomicAdd(&H[sh[lo + t]], 1)] = lo + t;
+    __syncwarp();
+    // H[h] is now the end of height h; the start is the end of the previous
+  }
+  for (int h = hmin; h <= hmax; ++h) {
+    if (sorted) {
+      const int32_t k0 = h == hmin ? 0 : hs[warp][h - 1], k1 = hs[warp][h];
+      for (int32_t k = k0 + lane; k < k1; k += 32) {
+        const int32_t s = ids[warp][k];
+        const int2 cc = a.sc[s];
+        build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
+      }
+    } else {
+      for (int32_t s = lo + lane; s < hi; s += 32) {
+        if (sh[s] != h) continue;
+        const int2 cc = a.sc[s];
+        build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void k_count_table_dd(const double* __restrict__ tab, float2* __restrict__ tab2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * kCountTab) return;
@@ -517,7 +591,11 @@ zq_status run_build(Ctx& c, const BuildArgs& a) {
   }
   time_end(c, "build_level");
   time_begin(c, "build_tail");
-  k_build_tail<R><<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
+  if (c.big_bodies.empty())
+    k_build_tail_warp<R><<<(unsigned)((c.m + kTailWarps - 1) / kTailWarps), 32 * kTailWarps, 0, c.stream>>>(
+        a, (int32_t)c.m);
+  else
+    k_build_tail<R><<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
   time_end(c, "build_tail");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
