@@ -260,8 +260,9 @@ zq_status zq_pipeline(zq_ctx *ctx, zq_prec prec, int64_t m, const int64_t *off, 
  * caller's own capture) records them at every replay.  Names:
  * "small_tree" (the per-body tree kernels), "bead_body", "aabb", "keys",
  * "sort_radix", "sort_radix_count", "lcp", "bottom_up" (bodies over 8192
- * beads), "scan", "segments", "schedule", "build_level" (the Case I kernel
- * and one launch per height up to the level cut), "build_tail",
+ * beads), "scan", "segments", "schedule", "build" (the whole transform
+ * build), "build_level" (the Case I kernel and one launch per height up to
+ * the level cut), "build_tail",
  * "up_seg", "up_top", "down_top", "down_seg", their "_blk" block-form
  * variants, "qgen", "count_table".  When one API call launches the named
  * kernel several times, start is recorded before its first launch and

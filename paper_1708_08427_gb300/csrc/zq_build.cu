@@ -581,8 +581,10 @@ __global__ void k_count_table_dd(const double* __restrict__ tab, float2* __restr
 template <class R>
 zq_status run_build(Ctx& c, const BuildArgs& a) {
   const int grid = c.num_sms * kLevelBlocksPerSM;
-  // one timing bracket around all level launches (few event records in a
+  // timing brackets: "build" around the whole transform build, and
+  // "build_level" around all level launches (few event records in a
   // captured step)
+  time_open(c, "build");
   time_begin(c, "build_level");
   k_build_case1<R><<<c.num_sms * 8, kThreads, 0, c.stream>>>(a);
   for (int h = 2; h <= c.cut; ++h) {
@@ -597,6 +599,7 @@ zq_status run_build(Ctx& c, const BuildArgs& a) {
   else
     k_build_tail<R><<<(unsigned)c.m, kThreads, 0, c.stream>>>(a);
   time_end(c, "build_tail");
+  time_end(c, "build");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }

@@ -184,6 +184,13 @@ inline void time_begin(Ctx& c, const char* name) {
     c.time_started = true;
   }
 }
+// A bracket around several launches (no launch of its own).
+inline void time_open(Ctx& c, const char* name) {
+  if (c.time_ev0 && !c.time_started && __builtin_strcmp(c.time_name, name) == 0) {
+    time_record(c.time_ev0, c.stream);
+    c.time_started = true;
+  }
+}
 inline void time_end(const Ctx& c, const char* name) {
   if (c.time_ev1 && __builtin_strcmp(c.time_name, name) == 0) time_record(c.time_ev1, c.stream);
 }
