@@ -470,13 +470,15 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     char* sw = sqtw + 3 * N * es;
     char* sqv = sw + R * es;
     // coordinates first on the context stream (the tree needs them); the
-    // vectors on a side stream, overlapping the tree and the transforms,
-    // joined before the sweeps
-    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
-    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[3], c.fork_ev, 0));
+    // vectors after them on a side stream, overlapping the tree and the
+    // transforms, joined before the sweeps.  Forking after the coordinate
+    // copies keeps the vectors from sharing the host link with them (the
+    // tree would wait for both).
     ZQ_CUDA_TRY(cudaMemcpyAsync(sx, x, N * 8, cudaMemcpyHostToDevice, c.stream));
     ZQ_CUDA_TRY(cudaMemcpyAsync(sy, y, N * 8, cudaMemcpyHostToDevice, c.stream));
     ZQ_CUDA_TRY(cudaMemcpyAsync(sz, z, N * 8, cudaMemcpyHostToDevice, c.stream));
+    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[3], c.fork_ev, 0));
     if (v) ZQ_CUDA_TRY(cudaMemcpyAsync(sv, v, 3 * N * es, cudaMemcpyHostToDevice, c.side[3]));
     if (w) ZQ_CUDA_TRY(cudaMemcpyAsync(sw, w, R * es, cudaMemcpyHostToDevice, c.side[3]));
     ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[3], c.side[3]));
@@ -493,13 +495,23 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
   c.have64 = prec == ZQ_FP64;
   c.have32 = prec == ZQ_FP32;
   if (host) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[3], 0));  // the vectors are in
-  if (dv && dw) {
-    // Q~v on the context stream, Q~^T w concurrently on a side stream; with
-    // host buffers qv goes back while Q~^T w still runs
+  if (dv && dw && host) {
+    // host buffers: the sweeps one after the other (together they take as
+    // long as run concurrently), so that qv goes back over the host link
+    // while Q~^T w runs instead of both results going back at the end
+    ZQ_TRY(zq::launch_apply_Q(c, prec, dv, 3 * N, dqv));
+    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[3], c.fork_ev, 0));
+    ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.side[3]));
+    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[3], c.side[3]));
+    ZQ_TRY(zq::launch_apply_QT(c, prec, dw, dqtw, 3 * N));
+    ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[3], 0));
+  } else if (dv && dw) {
+    // Q~v on the context stream, Q~^T w concurrently on a side stream
     ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
     ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[0], c.fork_ev, 0));
     ZQ_TRY(zq::launch_apply_Q(c, prec, dv, 3 * N, dqv));
-    if (host) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));
     cudaStream_t main = c.stream;
     std::swap(c.x32, c.x32b);
     std::swap(c.x64, c.x64b);
@@ -511,7 +523,6 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     ZQ_TRY(st);
     ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[0], c.side[0]));
     ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[0], 0));
-    if (host) ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
   } else {
     if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
     if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));
