@@ -137,3 +137,34 @@ def test_large_batch_properties():
     e4 = ((Uv - root[:, 3:]).norm() / root[:, 3:].norm()).item()
     assert max(e1, e2, e3, e4) <= 1e-12, (e1, e2, e3, e4)
     ctx.close()
+
+
+def test_large_body_path_properties():
+    """One body of 20,000 beads (the device-wide tree path, thousands of
+    nodes above the segments) next to small ones: CSR Q~ v equals
+    zq_apply_Q in FP64 and FP32, every row has unit norm."""
+    big = W.ellipsoid_body(n=20000, seed=5)
+    small = W.shell_batch(m=3, nmin=40, nmax=600, seed=6)
+    pts = [np.stack(big.body(0), 1)] + [np.stack(small.body(j), 1) for j in range(small.m)]
+    off = np.zeros(len(pts) + 1, np.int64)
+    off[1:] = np.cumsum([p.shape[0] for p in pts])
+    P = np.concatenate(pts)
+    bt = W.Batch(off, P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy())
+    ctx = _ctx(bt)
+    dev = _dev()
+    N, R = bt.N, bt.n_residues
+    g = torch.Generator(device="cpu").manual_seed(7)
+    v64 = torch.randn((3, N), generator=g, dtype=torch.float64).to(dev)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        rp, col, val, _ = ctx.qgen(dt)
+        rows = torch.repeat_interleave(torch.arange(R, device=dev), rp[1:] - rp[:-1])
+        v = v64.to(dt)
+        vi = v.t().reshape(-1)
+        qv = torch.zeros(R, dtype=dt, device=dev).index_add_(0, rows, val * vi[col.long()])
+        ref = ctx.apply_Q(v)
+        norms = torch.zeros(R, dtype=torch.float64, device=dev).index_add_(0, rows, val.double() ** 2)
+        ctx.sync()
+        e1 = ((qv - ref).double().norm() / ref.double().norm()).item()
+        e2 = (norms - 1).abs().max().item()
+        assert e1 <= tol and e2 <= 10 * tol, (dt, e1, e2)
+    ctx.close()
