@@ -117,6 +117,15 @@ __device__ __forceinline__ void prefetch_l2_inside(const void* base, int64_t lim
   if (hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
 }
 
+// One node's record (at most 80 bytes, 16-byte aligned) into L2: the
+// lines holding its first word and the kRecMax-th (inside the record
+// buffer, which holds kRecMax words per node).
+template <typename T>
+__device__ __forceinline__ void prefetch_l2_line(const T* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p + kRecMax - 1));
+}
+
 // Height boundaries of a segment: hb[h] = first local index of height h,
 // hb[H + 1] = nn (the heights 1..H of a subtree are all present).  Returns H.
 // Stages the segment's per-node data (children, record offset, residue
@@ -261,6 +270,9 @@ __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
   if (n == 0) return;
   const int32_t* list = a.topv + t0;
   const uint8_t* ph = a.ph;
+  // the body's top records into L2 first (they are scattered among the
+  // segments' records), so the height-by-height chain reads them from L2
+  for (int32_t t = threadIdx.x; t < n; t += blockDim.x) prefetch_l2_line(a.rec + 4 * (int64_t)a.prw[list[t]]);
   const bool sorted = sort_by_height(n, [&](int32_t t) { const int32_t p = list[t]; return make_int2(p, ph[p]); }, S);
   for (int h = S.lim[0]; h <= S.lim[1]; ++h) {
     if (sorted) {
@@ -328,6 +340,13 @@ __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
   if (n == 0) return;
   const int32_t* list = a.topv + t0;
   const uint8_t* ph = a.ph;
+  // the body's top records and residue coefficients into L2 first (they
+  // are scattered), so the height-by-height chain reads them from L2
+  for (int32_t t = threadIdx.x; t < n; t += blockDim.x) {
+    const int32_t p = list[t];
+    prefetch_l2_line(a.rec + 4 * (int64_t)a.prw[p]);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.in + a.proff[p]));  // 3 or 6 values
+  }
   const bool sorted = sort_by_height(n, [&](int32_t t) { const int32_t p = list[t]; return make_int2(p, ph[p]); }, S);
   const int hmax = S.lim[1];
   for (int h = hmax; h >= S.lim[0]; --h) {
