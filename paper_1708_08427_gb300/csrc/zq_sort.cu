@@ -22,8 +22,8 @@ namespace {
 // a scan of the per-tile histograms (digit-major).
 constexpr int kRadixThreads = 256;
 constexpr int kWarps = kRadixThreads / 32;
-constexpr int kSlice = 512;                 // keys per warp
-constexpr int kTile = kWarps * kSlice;      // 4096 keys per block
+constexpr int kSlice = 128;                 // keys per warp
+constexpr int kTile = kWarps * kSlice;      // 1024 keys per block
 constexpr int kDigits = 256;
 
 __global__ void __launch_bounds__(kRadixThreads)
