@@ -173,12 +173,27 @@ __device__ __forceinline__ void up_dispatch(const SweepArgs<T>& a, uint32_t rw, 
   else up_node<T, 2>(r, X, Y, true, P, res);
 }
 
+// The blocks of a grid share a bulk L2 prefetch of an array of `bytes`:
+// block k takes the k-th slice.
+__device__ __forceinline__ void prefetch_l2_share(const void* base, int64_t bytes) {
+  const int64_t slice = ((bytes + gridDim.x - 1) / gridDim.x + 15) & ~(int64_t)15;
+  const int64_t lo = (int64_t)blockIdx.x * slice;
+  if (lo < bytes)
+    prefetch_l2_inside(base, bytes, static_cast<const char*>(base) + lo, bytes - lo < slice ? bytes - lo : slice);
+}
+
 template <typename T, bool ROT>
 __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
   __shared__ T info[(kSegMax - 1) * 6];
   __shared__ T bead[kSegMax * 3];
   __shared__ SegMeta M;
   const int ns = *a.nseg;
+  // the bead vectors and the position -> bead map are gathered segment by
+  // segment: bring them into L2 once, all blocks together (a few tens of MB)
+  if (threadIdx.x < 32) {
+    prefetch_l2_share(a.in, 3 * a.N * (int64_t)sizeof(T));
+    prefetch_l2_share(a.perm, a.N * (int64_t)sizeof(int32_t));
+  }
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
     const int4 sg = a.seg[i];
     const int32_t p0 = sg.x, nn = sg.y, f = sg.z;
