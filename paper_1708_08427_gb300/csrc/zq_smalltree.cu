@@ -1,10 +1,12 @@
 // zq_smalltree.cu -- the whole bisection tree of a body of at most 8192
 // beads in one thread block (Sec. 2.1, same readings as zq_tree.cu):
-//   1. bounding box (block min/max on order-preserving integer encodings);
+//   1. bounding box: read from the device-wide pass over all bodies
+//      (k_aabb, order-preserving integer encodings of the doubles);
 //   2. 21-bit quantisation and bisection keys (z, then y, then x per octree
 //      level, most significant first);
 //   3. stable LSD radix sort of (key, body-local index) in shared memory,
-//      8-bit digits, warp-level ranks from ballots: four passes over the high 32 key bits, then each run of
+//      8-bit digits, warp-level ranks from ballots: four passes over the
+//      high 32 key bits, then each run of
 //      equal high halves (rare: beads closer than 2^-10 of the box) sorted
 //      by insertion; bodies with a run of more than 32 such beads take all
 //      eight passes instead.  Equal keys keep index order;
@@ -26,6 +28,8 @@ struct SmallTreeArgs {
   const double* x;
   const double* y;
   const double* z;
+  const unsigned long long* lo;  // bounding boxes (ordered-integer encodings), 3 per body
+  const unsigned long long* hi;
   const int64_t* off;
   const int32_t* bodies;  // body ids of this size class
   int32_t* perm;
@@ -147,7 +151,6 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   uint16_t* idxB = idxA + MAXN;
   int32_t* whist = reinterpret_cast<int32_t*>(idxB + MAXN);  // [NW][256]
   __shared__ int32_t sh[33];
-  __shared__ unsigned long long bb[6];
   __shared__ double lim[9];  // lo[3], hi[3], 2^21 / (hi - lo)[3]
 
   const int32_t j = a.bodies[blockIdx.x];
@@ -155,44 +158,10 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   const int n = (int)(a.off[j + 1] - o);
   const int tid = threadIdx.x;
 
-  // ---- 1. bounding box (order-preserving integer encodings of doubles)
-  if (tid < 3) bb[tid] = ~0ull;
-  if (tid >= 3 && tid < 6) bb[tid] = 0ull;
-  __syncthreads();
-  {
-    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
-    bool bad = false;
-#pragma unroll 4
-    for (int i = tid; i < n; i += THREADS) {
-      const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const unsigned long long e = ord_encode(p[c]);
-        // NaN or infinite: all exponent bits set (integer test, no FP64 op)
-        bad |= ((unsigned long long)__double_as_longlong(p[c]) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
-        mn[c] = e < mn[c] ? e : mn[c];
-        mx[c] = e > mx[c] ? e : mx[c];
-      }
-    }
-    if (bad) atomicOr(a.err, kErrNonFinite);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn[c], d);
-        const unsigned long long omx = __shfl_xor_sync(0xffffffffu, mx[c], d);
-        mn[c] = omn < mn[c] ? omn : mn[c];
-        mx[c] = omx > mx[c] ? omx : mx[c];
-      }
-      if ((tid & 31) == 0) {
-        atomicMin(&bb[c], mn[c]);
-        atomicMax(&bb[3 + c], mx[c]);
-      }
-    }
-  }
-  __syncthreads();
+  // ---- 1. bounding box: from the device-wide pass (k_aabb), which also
+  // checked the coordinates for NaN and infinity
   if (tid < 3) {
-    const double l = ord_decode(bb[tid]), h = ord_decode(bb[3 + tid]);
+    const double l = ord_decode(a.lo[3 * j + tid]), h = ord_decode(a.hi[3 * j + tid]);
     lim[tid] = l;
     lim[3 + tid] = h;
     lim[6 + tid] = h > l ? (double)(1u << kQBits) / (h - l) : 0.0;
@@ -475,6 +444,8 @@ int small_tree_class(int64_t n) { return n <= 1024 ? 0 : (n <= 2048 ? 1 : (n <= 
 zq_status launch_small_trees(Ctx& c, const double* x, const double* y, const double* z) {
   SmallTreeArgs a;
   a.x = x; a.y = y; a.z = z;
+  a.lo = reinterpret_cast<const unsigned long long*>(c.aabb);
+  a.hi = a.lo + 3 * c.m;
   a.off = c.off; a.bodies = nullptr; a.perm = c.perm; a.cl = c.cl; a.cr = c.cr; a.first = c.first;
   a.cnt = c.cnt; a.height = c.height; a.res = c.roff; a.root = c.root; a.err = c.counters + 2;
   a.final_roff = c.big_bodies.empty() ? 1 : 0;

@@ -35,8 +35,7 @@ __global__ void k_aabb(const double* __restrict__ x, const double* __restrict__ 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = i < N;
-  int32_t j = valid ? bead_body[i] : -1;
-  if (j >= 0 && off[j + 1] - off[j] <= kSmallSortMax) j = -1;  // done by the per-body kernel
+  const int32_t j = valid ? bead_body[i] : -1;
   const bool mine = j >= 0;
   double p[3] = {mine ? x[i] : 0.0, mine ? y[i] : 0.0, mine ? z[i] : 0.0};
   if (mine && !(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(err, kErrNonFinite);
@@ -401,16 +400,18 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   unsigned long long* lo = reinterpret_cast<unsigned long long*>(c.aabb);
   unsigned long long* hi = lo + 3 * c.m;
   int32_t* err = c.counters + 2;
+  // every body's bounding box in one pass over the coordinates (coalesced,
+  // and it leaves them in L2 for the key pass of the per-body kernels)
+  ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
+  ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
+  time_begin(c, "aabb");
+  k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.off, c.N, lo, hi, err);
+  time_end(c, "aabb");
   // bodies of at most kSmallSortMax beads: one thread block each
   zq_status st = launch_small_trees(c, x, y, z);
   if (st != ZQ_OK) return st;
   // larger bodies: device-wide kernels (they skip the beads of small bodies)
   if (!c.big_bodies.empty()) {
-    ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
-    ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
-    time_begin(c, "aabb");
-    k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.off, c.N, lo, hi, err);
-    time_end(c, "aabb");
     time_begin(c, "keys");
     k_body_scale<<<blocks(3 * c.m), kThreads, 0, s>>>(c.m, lo, hi, c.body_scale);
     time_end(c, "keys");
