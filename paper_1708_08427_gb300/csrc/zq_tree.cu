@@ -28,72 +28,105 @@ __global__ void k_bead_body(const int64_t* __restrict__ off, int64_t m, int64_t 
   if (i < N) bead_body[i] = body_of_bead(off, m, i);
 }
 
-__global__ void k_aabb(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, const int32_t* __restrict__ bead_body,
-                       const int64_t* __restrict__ off, int64_t N, unsigned long long* __restrict__ lo,
-                       unsigned long long* __restrict__ hi, int32_t* __restrict__ err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const bool valid = i < N;
-  const int32_t j = valid ? bead_body[i] : -1;
-  const bool mine = j >= 0;
-  double p[3] = {mine ? x[i] : 0.0, mine ? y[i] : 0.0, mine ? z[i] : 0.0};
-  if (mine && !(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) atomicOr(err, kErrNonFinite);
-  // a block whose beads all belong to one large body reduces in shared
-  // memory and issues one atomic per axis; otherwise per warp or per bead
-  __shared__ int32_t jb[2];
-  __shared__ unsigned long long wmn[3][32], wmx[3][32];
-  if (threadIdx.x == 0) {
-    jb[0] = 0x7fffffff;
-    jb[1] = -2;
-  }
-  __syncthreads();
-  atomicMin(&jb[0], mine ? j : -1);
-  atomicMax(&jb[1], mine ? j : -1);
-  __syncthreads();
-  const bool block_uniform = jb[0] == jb[1] && jb[0] >= 0;
-  const int32_t j0 = __shfl_sync(0xffffffffu, j, 0);
-  const bool uniform = __all_sync(0xffffffffu, j == j0) && j0 >= 0;
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// Bounding boxes of all bodies (order-preserving integer encodings of the
+// doubles, atomic min / max per body and axis) and the check for NaN and
+// infinity.  A block takes kAabbItems beads per thread, consecutive beads
+// per step (coalesced).  Bodies are contiguous, so a tile whose first and
+// last bead belong to one body is that body's: thread-local min / max,
+// one block reduction, three atomics per bound.  Other tiles go bead by
+// bead, a warp at a time (one atomic per warp when the warp is one body's).
+constexpr int kAabbItems = 4;
+
+__global__ void __launch_bounds__(kThreads) k_aabb(const double* __restrict__ x, const double* __restrict__ y,
+                                                   const double* __restrict__ z,
+                                                   const int32_t* __restrict__ bead_body, int64_t N,
+                                                   unsigned long long* __restrict__ lo,
+                                                   unsigned long long* __restrict__ hi,
+                                                   int32_t* __restrict__ err) {
+  __shared__ unsigned long long wmn[3][kThreads / 32], wmx[3][kThreads / 32];
+  const int64_t t0 = (int64_t)blockIdx.x * kThreads * kAabbItems;
+  if (t0 >= N) return;
+  const int64_t t1 = t0 + kThreads * kAabbItems < N ? t0 + kThreads * kAabbItems : N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t jf = bead_body[t0], jl = bead_body[t1 - 1];
+  bool bad = false;
+  if (jf == jl) {
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    unsigned long long e = mine ? ord_encode(p[a]) : 0ull;
-    if (uniform) {
-      unsigned long long mn = e, mx = e;
+    for (int k = 0; k < kAabbItems; ++k) {
+      const int64_t i = t0 + k * kThreads + threadIdx.x;
+      if (i < t1) {
+        const double p[3] = {x[i], y[i], z[i]};
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn, d);
-        unsigned long long omx = __shfl_xor_sync(0xffffffffu, mx, d);
-        mn = omn < mn ? omn : mn;
-        mx = omx > mx ? omx : mx;
-      }
-      if (block_uniform) {
-        if (lane == 0) {
-          wmn[a][warp] = mn;
-          wmx[a][warp] = mx;
+        for (int a = 0; a < 3; ++a) {
+          bad |= ((unsigned long long)__double_as_longlong(p[a]) & 0x7ff0000000000000ull) ==
+                 0x7ff0000000000000ull;
+          const unsigned long long e = ord_encode(p[a]);
+          mn[a] = e < mn[a] ? e : mn[a];
+          mx[a] = e > mx[a] ? e : mx[a];
         }
-      } else if (lane == 0) {
-        atomicMin(&lo[3 * j0 + a], mn);
-        atomicMax(&hi[3 * j0 + a], mx);
       }
-    } else if (mine) {
-      atomicMin(&lo[3 * j + a], e);
-      atomicMax(&hi[3 * j + a], e);
     }
-  }
-  if (block_uniform) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {  // min and max separately: the neutral values differ
+        const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn[a], d);
+        const unsigned long long omx = __shfl_xor_sync(0xffffffffu, mx[a], d);
+        mn[a] = omn < mn[a] ? omn : mn[a];
+        mx[a] = omx > mx[a] ? omx : mx[a];
+      }
+      if (lane == 0) {
+        wmn[a][warp] = mn[a];
+        wmx[a][warp] = mx[a];
+      }
+    }
     __syncthreads();
     if (threadIdx.x < 3) {
       const int a = threadIdx.x;
-      unsigned long long mn = wmn[a][0], mx = wmx[a][0];
-      for (int w = 1; w < nwarps; ++w) {
-        mn = wmn[a][w] < mn ? wmn[a][w] : mn;
-        mx = wmx[a][w] > mx ? wmx[a][w] : mx;
+      unsigned long long m0 = wmn[a][0], m1 = wmx[a][0];
+      for (int w = 1; w < kThreads / 32; ++w) {
+        m0 = wmn[a][w] < m0 ? wmn[a][w] : m0;
+        m1 = wmx[a][w] > m1 ? wmx[a][w] : m1;
       }
-      atomicMin(&lo[3 * jb[0] + a], mn);
-      atomicMax(&hi[3 * jb[0] + a], mx);
+      atomicMin(&lo[3 * jf + a], m0);
+      atomicMax(&hi[3 * jf + a], m1);
+    }
+  } else {
+    for (int k = 0; k < kAabbItems; ++k) {
+      const int64_t i = t0 + k * kThreads + threadIdx.x;
+      const bool mine = i < t1;
+      const int32_t j = mine ? bead_body[i] : -1;
+      const double p[3] = {mine ? x[i] : 0.0, mine ? y[i] : 0.0, mine ? z[i] : 0.0};
+      const int32_t j0 = __shfl_sync(0xffffffffu, j, 0);
+      const bool uniform = __all_sync(0xffffffffu, j == j0) && j0 >= 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (mine)
+          bad |= ((unsigned long long)__double_as_longlong(p[a]) & 0x7ff0000000000000ull) ==
+                 0x7ff0000000000000ull;
+        const unsigned long long e = mine ? ord_encode(p[a]) : 0ull;
+        if (uniform) {
+          unsigned long long mn = e, mx = e;
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn, d);
+            const unsigned long long omx = __shfl_xor_sync(0xffffffffu, mx, d);
+            mn = omn < mn ? omn : mn;
+            mx = omx > mx ? omx : mx;
+          }
+          if (lane == 0) {
+            atomicMin(&lo[3 * j0 + a], mn);
+            atomicMax(&hi[3 * j0 + a], mx);
+          }
+        } else if (mine) {
+          atomicMin(&lo[3 * j + a], e);
+          atomicMax(&hi[3 * j + a], e);
+        }
+      }
     }
   }
+  if (bad) atomicOr(err, kErrNonFinite);
 }
 
 // Spread the 21 low bits of v to every third bit (bit b -> bit 3b).
@@ -405,7 +438,8 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
   ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
   time_begin(c, "aabb");
-  k_aabb<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.off, c.N, lo, hi, err);
+  k_aabb<<<(unsigned)((c.N + kThreads * kAabbItems - 1) / (kThreads * kAabbItems)), kThreads, 0, s>>>(
+      x, y, z, c.bead_body, c.N, lo, hi, err);
   time_end(c, "aabb");
   // bodies of at most kSmallSortMax beads: one thread block each
   zq_status st = launch_small_trees(c, x, y, z);
