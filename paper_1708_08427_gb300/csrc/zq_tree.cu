@@ -378,14 +378,14 @@ __global__ void k_bucket_starts(const int32_t* __restrict__ hist, int64_t nblk, 
   if (b == nb) bstart[nb] = (int32_t)nodes;
 }
 
+// Per-slot data that depends on the tree and the slots only (it runs while
+// the segment schedule is still being made on its side stream).
 __global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
                             const int32_t* __restrict__ slot_of, const int32_t* __restrict__ cl,
                             const int32_t* __restrict__ cr, const int32_t* __restrict__ roff,
                             const int32_t* __restrict__ cnt, const uint8_t* __restrict__ height,
-                            const int32_t* __restrict__ pos_of, const int32_t* __restrict__ prw,
                             int2* __restrict__ sc, int32_t* __restrict__ sroff,
-                            int32_t* __restrict__ scnt, uint8_t* __restrict__ sheight,
-                            int32_t* __restrict__ srw) {
+                            int32_t* __restrict__ scnt, uint8_t* __restrict__ sheight) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nodes) return;
   const int32_t q = sid[s];
@@ -394,7 +394,15 @@ __global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
   sroff[s] = roff[q];
   scnt[s] = cnt[q];
   sheight[s] = height[q];
-  srw[s] = prw[pos_of[q]];
+}
+
+// Record offset of each slot's node (position order, from the segment
+// schedule): the one part of the slot data that waits for it.
+__global__ void k_slot_records(int64_t nodes, const int32_t* __restrict__ sid, const int32_t* __restrict__ pos_of,
+                               const int32_t* __restrict__ prw, int32_t* __restrict__ srw) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nodes) return;
+  srw[s] = prw[pos_of[sid[s]]];
 }
 
 __global__ void k_root_slots(int64_t m, const int32_t* __restrict__ root,
@@ -496,14 +504,16 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   time_begin(c, "schedule");
   k_bucket_starts<<<1, 128, 0, s>>>(hist, nblk, nb, c.nodes, c.bstart);
   time_end(c, "schedule");
-  ZQ_CUDA_TRY(cudaStreamWaitEvent(s, c.join_ev[1], 0));
   time_begin(c, "schedule");
   k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.roff, c.cnt,
-                                                   c.height, c.pos_of, c.prw, c.sc, c.sroff, c.scnt,
-                                                   c.sheight, c.srw);
+                                                   c.height, c.sc, c.sroff, c.scnt, c.sheight);
   time_end(c, "schedule");
   time_begin(c, "schedule");
   k_root_slots<<<blocks(c.m), kThreads, 0, s>>>(c.m, c.root, c.slot_of, c.root_slot);
+  time_end(c, "schedule");
+  ZQ_CUDA_TRY(cudaStreamWaitEvent(s, c.join_ev[1], 0));  // the segment schedule (positions, prw)
+  time_begin(c, "schedule");
+  k_slot_records<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.pos_of, c.prw, c.srw);
   time_end(c, "schedule");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
