@@ -1,0 +1,39 @@
+"""The benchmark's output contract, checked on the CPU through the reference
+arm (the oracle on host cores): one JSON line with the required keys, the
+reference arm's own cpu_baseline and e2e objects, and the workload named in
+config.  The GPU arm prints the same line with roofline, clocks and
+gpu_launches; it needs a GPU and is run by the benchmark itself."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--bodies", "30", "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    return json.loads(lines[0])
+
+
+def test_reference_line_has_the_contract_keys(line):
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["unit"] == "beads/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 1
+    assert "workload" in line["config"]
+
+
+def test_reference_cpu_baseline_and_e2e(line):
+    cb, e2e = line["cpu_baseline"], line["e2e"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
