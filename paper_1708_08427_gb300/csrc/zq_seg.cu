@@ -127,8 +127,11 @@ __global__ void k_top_scatter(int64_t nodes, const int32_t* __restrict__ cnt, co
   topv[top_off[j] + atomicAdd(&fill[j], 1)] = (int32_t)q;
 }
 
-// One block per segment: range, height order, positions, per-position data.
-__global__ void __launch_bounds__(kThreads)
+// One block per segment: range, height order, positions, per-position data
+// (blocks of 128: a segment averages a few hundred nodes).
+constexpr int kOrderThreads = 128;
+
+__global__ void __launch_bounds__(kOrderThreads)
 k_seg_order(const int32_t* __restrict__ nseg, const int4* __restrict__ seg, const int32_t* __restrict__ cl,
             const int32_t* __restrict__ cr,
             const int32_t* __restrict__ roff, const uint8_t* __restrict__ height, int32_t* __restrict__ pos_of,
@@ -203,7 +206,7 @@ zq_status launch_segments(Ctx& c) {
   ZQ_TRY_STATUS(launch_exclusive_scan(c, top_cnt, c.top_off, m, c.scan_tmp, c.top_off + m));
   time_begin(c, "segments");
   k_top_scatter<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.first, c.bead_body, c.top_off, top_cnt + m, c.topv);
-  k_seg_order<<<c.num_sms * 8, kThreads, 0, s>>>(c.nseg, c.seg, c.cl, c.cr, c.roff, c.height, c.pos_of,
+  k_seg_order<<<c.num_sms * 16, kOrderThreads, 0, s>>>(c.nseg, c.seg, c.cl, c.cr, c.roff, c.height, c.pos_of,
                                                  c.pnode, c.pc, c.proff, c.ph, c.prw);
   time_end(c, "segments");
   ZQ_TRY_STATUS(launch_exclusive_scan(c, c.prw, c.prw, n, c.scan_tmp, c.prw + n));
