@@ -280,6 +280,20 @@ zq_status zq_time_kernel(zq_ctx *ctx, const char *name, void *start_event, void 
 typedef enum { ZQ_BUILD_DD = 0, ZQ_BUILD_FP64 = 1 } zq_build_arith;
 zq_status zq_set_build_arith(zq_ctx *ctx, zq_build_arith arith);
 
+/* Order of the bead vectors of every product call that follows (inputs of
+ * Q~, outputs of Q~^T, in every precision and form, and of zq_pipeline).
+ * ZQ_ORDER_CALLER (default): bead i is the caller's bead i.  ZQ_ORDER_TREE:
+ * entry s of each plane is the bead at sorted position s of the context's
+ * current tree, i.e. the caller's bead perm[s] (perm from zq_get_tree);
+ * the sweeps then read and write the planes without the gather through
+ * perm.  The results are the same numbers, permuted.  Residue vectors are
+ * not affected.  In zq_pipeline the order is that of the tree the call
+ * builds (or keeps, with ZQ_KEEP_TREE); the tree is a deterministic function
+ * of off and the coordinates, so a rebuild from unchanged coordinates gives
+ * the same perm.  zq_qgen's columns stay in the caller's order. */
+typedef enum { ZQ_ORDER_CALLER = 0, ZQ_ORDER_TREE = 1 } zq_vector_order;
+zq_status zq_set_vector_order(zq_ctx *ctx, zq_vector_order order);
+
 /* Number of kernels this context has launched since it was created (for
  * launch accounting in measurements). */
 zq_status zq_launch_count(const zq_ctx *ctx, int64_t *launches);

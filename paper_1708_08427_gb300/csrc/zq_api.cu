@@ -549,6 +549,12 @@ zq_status zq_time_kernel(zq_ctx* ctx, const char* name, void* start_event, void*
   return ZQ_OK;
 }
 
+zq_status zq_set_vector_order(zq_ctx* ctx, zq_vector_order order) {
+  if (!ctx || (order != ZQ_ORDER_CALLER && order != ZQ_ORDER_TREE)) return ZQ_EINVAL;
+  ctx->c.tree_order = order == ZQ_ORDER_TREE;
+  return ZQ_OK;
+}
+
 zq_status zq_set_build_arith(zq_ctx* ctx, zq_build_arith arith) {
   if (!ctx || (arith != ZQ_BUILD_DD && arith != ZQ_BUILD_FP64)) return ZQ_EINVAL;
   ctx->c.build_dd = arith == ZQ_BUILD_DD;
@@ -699,7 +705,8 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
   if (!c.stream || !off || m < 1) return pipeline_body(ctx, prec, m, off, x, y, z, v, qv, w, qtw, level_cut, flags);
   const int32_t cut = level_cut == 0 ? zq::kDefaultCut : level_cut;
   std::vector<uintptr_t> key = {(uintptr_t)prec, (uintptr_t)m, (uintptr_t)cut, (uintptr_t)flags,
-                                (uintptr_t)c.build_dd, (uintptr_t)x, (uintptr_t)y, (uintptr_t)z, (uintptr_t)v,
+                                (uintptr_t)c.build_dd, (uintptr_t)c.tree_order, (uintptr_t)x, (uintptr_t)y,
+                                (uintptr_t)z, (uintptr_t)v,
                                 (uintptr_t)qv, (uintptr_t)w, (uintptr_t)qtw};
   key.insert(key.end(), off, off + m + 1);
   // the kernel-timing hook is part of the captured step

@@ -31,7 +31,7 @@ constexpr int kTopThreads = 256;
 template <typename T>
 struct SweepArgs {
   int64_t N;
-  const int32_t* perm;     // sorted position -> bead
+  const int32_t* perm;     // sorted position -> bead (null: vectors in tree order)
   const int2* pc;          // by position: children (positions or leaves)
   const int32_t* proff;    // residue offsets
   const uint8_t* ph;       // heights
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
     }
     const Rot<T> R = body_rot<ROT>(a, ROT ? a.bead_body[f] : 0);
     for (int32_t t = threadIdx.x; t <= nn; t += blockDim.x) {
-      const int32_t b = a.perm[f + t];
+      const int32_t b = a.perm ? a.perm[f + t] : f + t;
       T v[3] = {a.in[b], a.in[a.N + b], a.in[2 * a.N + b]};
       rot_in(R, v);
       bead[3 * t] = v[0];
@@ -250,7 +250,7 @@ __device__ __forceinline__ bool top_range(const int32_t* __restrict__ topv, cons
 
 template <typename T>
 __device__ __forceinline__ void load_bead(const SweepArgs<T>& a, int32_t code, T* v, const Rot<T>& R) {
-  const int32_t b = a.perm[leaf_pos(code)];
+  const int32_t b = a.perm ? a.perm[leaf_pos(code)] : leaf_pos(code);
   v[0] = a.in[b];
   v[1] = a.in[a.N + b];
   v[2] = a.in[2 * a.N + b];
@@ -315,7 +315,7 @@ __device__ __forceinline__ void down_dispatch(const SweepArgs<T>& a, uint32_t rw
 
 template <typename T>
 __device__ __forceinline__ void store_bead(const SweepArgs<T>& a, int32_t code, const T* L, const Rot<T>& R) {
-  const int32_t b = a.perm[leaf_pos(code)];
+  const int32_t b = a.perm ? a.perm[leaf_pos(code)] : leaf_pos(code);
   T u[3] = {L[0], L[1], L[2]};
   rot_out(R, u);
   a.out[b] = u[0];
@@ -464,7 +464,7 @@ __device__ __forceinline__ void blk_child_up(const BlockArgs<TS, TC>& a, int32_t
 #pragma unroll
     for (int e = 0; e < 6; ++e) X[e] = p[(int64_t)e * a.k];
   } else {
-    const int64_t b = a.perm[leaf_pos(code)];
+    const int64_t b = a.perm ? a.perm[leaf_pos(code)] : leaf_pos(code);
 #pragma unroll
     for (int e = 0; e < 3; ++e) X[e] = to_c(a.in[((int64_t)e * a.N + b) * a.k + col]);
   }
@@ -509,7 +509,7 @@ __device__ __forceinline__ void blk_down_one(const BlockArgs<TS, TC>& a, int64_t
 #pragma unroll
       for (int e = 0; e < 6; ++e) d[(int64_t)e * a.k] = L[s2][e];
     } else {
-      const int64_t b = a.perm[leaf_pos(ch[s2])];
+      const int64_t b = a.perm ? a.perm[leaf_pos(ch[s2])] : leaf_pos(ch[s2]);
 #pragma unroll
       for (int e = 0; e < 3; ++e) a.out[((int64_t)e * a.N + b) * a.k + col] = from_c<TS>(L[s2][e]);
     }
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kTopThreads) k_down_top_blk(BlockArgs<TS, TC> 
 template <typename TS, typename TC>
 BlockArgs<TS, TC> make_block_args(const Ctx& c, int32_t k, const TC* rec, const TS* in, TS* out) {
   BlockArgs<TS, TC> a;
-  a.N = c.N; a.k = k; a.perm = c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
+  a.N = c.N; a.k = k; a.perm = c.tree_order ? nullptr : c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
   a.prw = reinterpret_cast<const uint32_t*>(c.prw);
   a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
   a.rec = rec; a.xk = static_cast<TC*>(c.xblk); a.in = in; a.out = out;
@@ -646,7 +646,7 @@ zq_status run_block(Ctx& c, bool up, int32_t k, const TC* rec, const void* in, v
 template <typename T>
 SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   SweepArgs<T> a;
-  a.N = c.N; a.perm = c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
+  a.N = c.N; a.perm = c.tree_order ? nullptr : c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
   a.prw = reinterpret_cast<const uint32_t*>(c.prw);
   a.seg = c.seg; a.seg_r = c.seg_r; a.R = c.R; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;

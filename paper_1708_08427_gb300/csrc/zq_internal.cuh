@@ -76,6 +76,7 @@ struct Ctx {
   int cut = kDefaultCut;
   bool have_tree = false, have_xform = false, have64 = false, have32 = false;
   bool build_dd = true;    // build the transforms in double-single (else native FP64)
+  bool tree_order = false; // bead vectors of the products are in tree (sorted-position) order
   bool st_is_dd = false;   // representation of st64 written by the last build
   std::vector<int64_t> off_h;
   std::vector<int32_t> small_bodies;  // n_j <= kSmallSortMax, grouped by size class

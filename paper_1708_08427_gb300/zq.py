@@ -78,6 +78,8 @@ def _lib() -> ctypes.CDLL:
         L.zq_time_kernel.argtypes = [_vp, ctypes.c_char_p, _vp, _vp]
         L.zq_set_build_arith.restype = ctypes.c_int
         L.zq_set_build_arith.argtypes = [_vp, ctypes.c_int]
+        L.zq_set_vector_order.restype = ctypes.c_int
+        L.zq_set_vector_order.argtypes = [_vp, ctypes.c_int]
         L.zq_launch_count.restype = ctypes.c_int
         L.zq_launch_count.argtypes = [_vp, _i64p]
         L.zq_apply_Q_full.restype = ctypes.c_int
@@ -360,6 +362,11 @@ class Context:
             return
         _check(_lib().zq_time_kernel(self._h, name.encode(), _vp(start.cuda_event), _vp(stop.cuda_event)),
                "zq_time_kernel")
+
+    def set_vector_order(self, order: str):
+        """'caller' (default) or 'tree': bead vectors of the products in the
+        tree's sorted-position order (entry s = caller's bead perm[s])."""
+        _check(_lib().zq_set_vector_order(self._h, {"caller": 0, "tree": 1}[order]), "zq_set_vector_order")
 
     def set_build_arith(self, arith: str):
         """'dd' (double-single on the FP32 pipes, default) or 'fp64'."""
