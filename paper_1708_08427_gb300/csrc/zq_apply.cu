@@ -189,10 +189,11 @@ __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
   __shared__ SegMeta M;
   const int ns = *a.nseg;
   // the bead vectors and the position -> bead map are gathered segment by
-  // segment: bring them into L2 once, all blocks together (a few tens of MB)
+  // segment: bring them into L2 once, all blocks together (a few tens of MB;
+  // tree-ordered vectors have no map)
   if (threadIdx.x < 32) {
     prefetch_l2_share(a.in, 3 * a.N * (int64_t)sizeof(T));
-    prefetch_l2_share(a.perm, a.N * (int64_t)sizeof(int32_t));
+    if (a.perm) prefetch_l2_share(a.perm, a.N * (int64_t)sizeof(int32_t));
   }
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
     const int4 sg = a.seg[i];
