@@ -223,16 +223,17 @@ def build_flops(k: int) -> int:
 RECORD_FLOATS = {3: 11, 6: 13, 9: 19}
 
 
-def sweep_bytes(census, N, R, es=4) -> int:
+def sweep_bytes(census, N, R, es=4, gather=True) -> int:
     """Algorithmic DRAM bytes of one sweep (up or down): the bead-vector
     planes (3N) and residues (R) once, each node record once (by k), the
-    node structure (two child codes and the residue offset, 12 B) and the
-    sorted-position -> bead map (4 B per bead).  The Info-/Velocity-sets
-    that the implementation passes between heights through global memory
-    are not counted (the method needs them only on chip)."""
+    node structure (two child codes and the residue offset, 12 B) and, for
+    vectors in the caller's order (gather), the sorted-position -> bead map
+    (4 B per bead).  The Info-/Velocity-sets that the implementation passes
+    between heights through global memory are not counted (the method needs
+    them only on chip)."""
     rec = sum(census[k] * RECORD_FLOATS[k] * es for k in census)
     nodes = sum(census.values())
-    return es * (3 * N + R) + rec + 12 * nodes + 4 * N
+    return es * (3 * N + R) + rec + 12 * nodes + (4 * N if gather else 0)
 
 
 def kernel_work(name, census, N, R, m, es):
@@ -524,8 +525,9 @@ def timed(args, fn, stream, flush, world, dev, N, graph=True, steps=None):
 
 def apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev):
     """Q~v + Q~^T w with the transforms already built (as inside a Krylov
-    solve), FP32 and FP64, through zq_apply_pair (the two sweeps run
-    concurrently), with the sweep bytes achieved against HBM."""
+    solve), FP32 and FP64, and FP32 with the bead vectors in the tree's
+    order, through zq_apply_pair (the two sweeps run concurrently), with the
+    sweep bytes achieved against HBM."""
     import torch
 
     N, R, m = bt.N, bt.n_residues, bt.m
@@ -551,6 +553,25 @@ def apply_only(args, ctx, bt, stream, flush, census, v, w, qv, qtw, world, dev):
         r["hbm_frac"] = r["hbm_achieved_gbs"] / hbm
         r["algorithmic_bytes_per_step"] = byt
         res[name] = r
+    # bead vectors kept in the tree's sorted-position order (zq_set_vector_order):
+    # the sweeps read and write the planes without the gather through perm
+    perm = torch.from_numpy(ctx.get_tree()["perm"].astype(np.int64)).to(dev)
+    vv, ww = v.to(torch.float32)[:, perm].contiguous(), w.to(torch.float32)
+    oq = torch.empty(R, dtype=torch.float32, device=dev)
+    oqt = torch.empty((3, N), dtype=torch.float32, device=dev)
+    ctx.set_vector_order("tree")
+    stream.synchronize()
+
+    def fn_tree():
+        ctx.apply_pair(vv, ww, oq, oqt)
+
+    r = timed(args, fn_tree, stream, flush, world, dev, N, graph=not args.no_graph)
+    ctx.set_vector_order("caller")
+    byt = 2 * sweep_bytes(census, N, R, 4, gather=False)
+    r["hbm_achieved_gbs"] = byt / (r["ms_per_step"] / 1e3) / 1e9
+    r["hbm_frac"] = r["hbm_achieved_gbs"] / hbm
+    r["algorithmic_bytes_per_step"] = byt
+    res["fp32_tree_order"] = r
     return res
 
 
