@@ -29,7 +29,7 @@ void free_all(Ctx& c) {
   void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
-                c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage,
+                c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage, c.ord,
                 c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.seg_r, c.topv,
                 c.top_off, c.nseg, c.srw, c.xblk};
   for (void* p : ps)
@@ -432,6 +432,22 @@ zq_status zq_apply_rotated(zq_ctx* ctx, zq_prec prec, const double* R, const voi
   return apply_two(ctx, prec, R, v, qv, w, qtw);
 }
 
+// zq_pipeline with both products and the vectors in the caller's order:
+// 0 = the sweeps gather v and scatter Q~^T w through perm themselves;
+// 1 = v is gathered into the tree's order on a side stream next to the
+// transform build, so the upward sweep reads contiguous planes;
+// 2 = as 1, and the downward sweep also writes in tree order, scattered by a
+// separate pass after it.
+constexpr int kPipeOrder = 2;
+
+static int64_t pipe_order_bytes(int64_t N, size_t es) {
+  return (kPipeOrder == 2 ? 2 : 1) * 3 * N * (int64_t)es;
+}
+
+static bool pipe_reorders(const Ctx& c, const void* v, const void* w) {
+  return kPipeOrder > 0 && v && w && !c.tree_order;
+}
+
 static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
                                const double* y, const double* z, const void* v, void* qv, const void* w,
                                void* qtw, int32_t level_cut, int32_t flags) {
@@ -447,6 +463,15 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     return ZQ_ESTATE;
   const int64_t N = off[m], R = 3 * N - 6 * m;
   const size_t es = prec == ZQ_FP64 ? sizeof(double) : sizeof(float);
+  const bool reorder = pipe_reorders(c, v, w);
+  if (reorder && pipe_order_bytes(N, es) > c.ord_cap) {
+    ++c.plan_gen;
+    if (c.ord) cudaFree(c.ord);
+    c.ord = nullptr;
+    c.ord_cap = 0;
+    if (cudaMalloc(&c.ord, (size_t)pipe_order_bytes(N, es)) != cudaSuccess) return ZQ_ENOMEM;
+    c.ord_cap = pipe_order_bytes(N, es);
+  }
   const double *dx = x, *dy = y, *dz = z;
   const void *dv = v, *dw = w;
   void *dqv = qv, *dqtw = qtw;
@@ -489,6 +514,38 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     dqtw = qtw ? sqtw : nullptr;
   }
   if (!keep) ZQ_TRY(zq_build_tree_batched(ctx, m, off, dx, dy, dz, level_cut));
+  // v into the tree's order on a side stream, next to the transform build
+  // (it needs the tree's perm and, from host buffers, the copied v)
+  char* vt = reorder ? static_cast<char*>(c.ord) : nullptr;
+  char* qtt = reorder && kPipeOrder == 2 ? vt + 3 * N * es : nullptr;
+  if (reorder) {
+    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[2], c.fork_ev, 0));
+    if (host) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[2], c.join_ev[3], 0));
+    cudaStream_t main = c.stream;
+    c.stream = c.side[2];
+    const zq_status st = zq::launch_to_tree(c, prec, dv, vt);
+    c.stream = main;
+    ZQ_TRY(st);
+    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[2], c.side[2]));
+  }
+  // the two sweeps of the step, each on the stream current at its call
+  auto sweep_up = [&]() -> zq_status {
+    if (reorder) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[2], 0));
+    const bool saved = c.tree_order;
+    c.tree_order = saved || reorder;
+    const zq_status st = zq::launch_apply_Q(c, prec, reorder ? vt : dv, 3 * N, dqv);
+    c.tree_order = saved;
+    return st;
+  };
+  auto sweep_down = [&]() -> zq_status {
+    const bool saved = c.tree_order;
+    c.tree_order = saved || qtt != nullptr;
+    zq_status st = zq::launch_apply_QT(c, prec, dw, qtt ? qtt : dqtw, 3 * N);
+    c.tree_order = saved;
+    if (st == ZQ_OK && qtt) st = zq::launch_from_tree(c, prec, qtt, dqtw);
+    return st;
+  };
   // only the records of the precision the sweeps use
   ZQ_TRY(zq::launch_build(c, dx, dy, dz, prec == ZQ_FP64 ? 1 : 2));
   c.have_xform = true;
@@ -499,24 +556,24 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     // host buffers: the sweeps one after the other (together they take as
     // long as run concurrently), so that qv goes back over the host link
     // while Q~^T w runs instead of both results going back at the end
-    ZQ_TRY(zq::launch_apply_Q(c, prec, dv, 3 * N, dqv));
+    ZQ_TRY(sweep_up());
     ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
     ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[3], c.fork_ev, 0));
     ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.side[3]));
     ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[3], c.side[3]));
-    ZQ_TRY(zq::launch_apply_QT(c, prec, dw, dqtw, 3 * N));
+    ZQ_TRY(sweep_down());
     ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
     ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[3], 0));
   } else if (dv && dw) {
     // Q~v on the context stream, Q~^T w concurrently on a side stream
     ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
     ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[0], c.fork_ev, 0));
-    ZQ_TRY(zq::launch_apply_Q(c, prec, dv, 3 * N, dqv));
+    ZQ_TRY(sweep_up());
     cudaStream_t main = c.stream;
     std::swap(c.x32, c.x32b);
     std::swap(c.x64, c.x64b);
     c.stream = c.side[0];
-    const zq_status st = zq::launch_apply_QT(c, prec, dw, dqtw, 3 * N);
+    const zq_status st = sweep_down();
     c.stream = main;
     std::swap(c.x32, c.x32b);
     std::swap(c.x64, c.x64b);
@@ -717,7 +774,8 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
   const bool warm = c.have_tree && m == c.m && cut == c.cut && std::equal(off, off + m + 1, c.off_h.begin());
   const int64_t N = off[m], R = 3 * N - 6 * m;
   const int64_t stage_bytes = 3 * N * 8 + (int64_t)(prec == ZQ_FP64 ? 8 : 4) * (6 * N + 2 * R);
-  const bool staged = !(flags & ZQ_HOST_BUFFERS) || stage_bytes <= c.stage_cap;
+  const bool staged = (!(flags & ZQ_HOST_BUFFERS) || stage_bytes <= c.stage_cap) &&
+                      (!pipe_reorders(c, v, w) || pipe_order_bytes(N, prec == ZQ_FP64 ? 8 : 4) <= c.ord_cap);
   key.push_back((uintptr_t)c.plan_gen);
   if (c.gexec && warm && staged && key == c.gkey) {
     c.time_started = false;

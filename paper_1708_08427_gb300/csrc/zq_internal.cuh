@@ -155,6 +155,10 @@ struct Ctx {
   // staging for host-buffer calls (bytes)
   void* stage = nullptr;
   int64_t stage_cap = 0;
+  // zq_pipeline's bead planes in tree order: v gathered for the upward
+  // sweep, then Q~^T w before its scatter (bytes)
+  void* ord = nullptr;
+  int64_t ord_cap = 0;
   // a step captured as a CUDA graph (zq_pipeline with ZQ_GRAPH): replayed
   // while every argument and the plan generation are unchanged
   uint64_t plan_gen = 0;         // bumped whenever the launch plan or a buffer changes
@@ -344,6 +348,10 @@ zq_status launch_segments(Ctx& c);
 // zq_build.cu
 // which: bit 0 = FP64 records, bit 1 = FP32 records
 zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which);
+// zq_order.cu: bead planes (3 x N) to and from the tree's sorted-position
+// order (entry s = bead perm[s]), on c.stream
+zq_status launch_to_tree(Ctx& c, zq_prec prec, const void* v, void* vt);
+zq_status launch_from_tree(Ctx& c, zq_prec prec, const void* ut, void* u);
 // zq_apply.cu
 // root_out / root_in (6 m values, may be null): the root Info-set Q_Z v of
 // every body / the root Velocity-set fed to Q~^T (null: zero).  rot (9 m
