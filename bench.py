@@ -240,8 +240,8 @@ def kernel_work(name, census, N, R, m, es):
     """(bound, algorithmic amount per launch, unit)."""
     if name == "build":  # every node's transform
         return "alu", sum(census[k] * build_flops(k) for k in census), "flop"
-    if name in ("up_seg", "down_seg"):
-        return "hbm", sweep_bytes(census, N, R, es), "B"
+    if name in ("up_seg", "down_seg"):  # the step's sweeps see tree-ordered planes (no gather)
+        return "hbm", sweep_bytes(census, N, R, es, gather=False), "B"
     if name == "sort_small":
         return "hbm", 8 * N + 8 * N + 4 * N, "B"
     if name == "bottom_up":
@@ -316,7 +316,8 @@ def run_ours(args, world, rank, local):
 
     # --- per-kernel time of one step (measurement hook), picks the dominant kernel
     names = ["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "segments",
-             "schedule", "build", "build_level", "build_tail", "up_seg", "up_top", "down_top", "down_seg"]
+             "schedule", "build", "build_level", "build_tail", "to_tree", "up_seg", "up_top", "down_top",
+             "down_seg", "from_tree"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e1.record(stream)

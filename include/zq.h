@@ -262,7 +262,8 @@ zq_status zq_pipeline(zq_ctx *ctx, zq_prec prec, int64_t m, const int64_t *off, 
  * "sort_radix", "sort_radix_count", "lcp", "bottom_up" (bodies over 8192
  * beads), "scan", "segments", "schedule", "build" (the whole transform
  * build), "build_level" (the Case I kernel and one launch per height up to
- * the level cut), "build_tail",
+ * the level cut), "build_tail", "to_tree" / "from_tree" (zq_pipeline's
+ * bead planes into and out of the tree's order around its sweeps),
  * "up_seg", "up_top", "down_top", "down_seg", their "_blk" block-form
  * variants, "qgen", "count_table".  When one API call launches the named
  * kernel several times, start is recorded before its first launch and
