@@ -51,6 +51,9 @@ def test_null_arguments_rejected_without_gpu(lib):
     lib.zq_qgen_nnz.restype = ctypes.c_int
     assert lib.zq_qgen(None, 0, None, None, None, None) == 1
     assert lib.zq_qgen_nnz(None, None) == 1
+    lib.zq_set_vector_order.restype = ctypes.c_int
+    assert lib.zq_set_vector_order(None, 0) == 1
+    assert lib.zq_set_vector_order(None, 1) == 1
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
