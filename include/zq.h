@@ -322,6 +322,36 @@ zq_status zq_sizes(const zq_ctx *ctx, int64_t *N, int64_t *m, int64_t *R, int64_
 zq_status zq_get_tree(zq_ctx *ctx, int32_t *perm, int32_t *left, int32_t *right, int32_t *first,
                       int32_t *count, int32_t *height, int32_t *roff);
 
+/* Row orders of Q~ (Sec. 3).  ZQ_ROWS_INORDER: the order of every
+ * product's residue vector: internal nodes by id (split position within a
+ * body), each node's rows in the order of G's rows 4..k, bodies
+ * concatenated.  ZQ_ROWS_PREORDER: the recursive layout of Sec. 3,
+ * Q~_p = [Residue_p; diag(Q~_x, Q~_y)]: a node's rows, then those of its
+ * left (x) subtree, then those of its right (y) subtree; bodies
+ * concatenated.  A node has 3 rows per internal child (0, 3 or 6) in
+ * either order, so a residue vector converts row block by row block:
+ * y_pre[pre[q] + i] = y_in[in[q] + i]. */
+typedef enum { ZQ_ROWS_INORDER = 0, ZQ_ROWS_PREORDER = 1 } zq_row_order;
+
+/* Residue offsets of every internal node in the chosen row order, on the
+ * HOST from a tree in zq_get_tree's form (no context, no device work):
+ *   m bodies with bead offsets off[m + 1] (off[0] = 0, n_j >= 3);
+ *   left[q], right[q] child codes of the N - m internal nodes (N = off[m]);
+ *   node_off[N - m] (int64) receives the offsets;
+ *   body_off[m + 1] (int64, may be NULL) the residue offset of each body,
+ *   3 off[j] - 6 j, the same in both orders.
+ * ZQ_EINVAL for a NULL array, m < 1, an unknown order, bad offsets, or
+ * arrays that are not one binary tree per body (a child outside its body,
+ * a node that is the child of two nodes, nodes not reached from the
+ * body's root). */
+zq_status zq_residue_offsets(int64_t m, const int64_t *off, const int32_t *left, const int32_t *right,
+                             zq_row_order order, int64_t *node_off, int64_t *body_off);
+
+/* zq_residue_offsets for the context's current tree (synchronous; HOST
+ * arrays node_off[N - m], body_off[m + 1] or NULL).  ZQ_ESTATE before a
+ * tree is built. */
+zq_status zq_get_residue_offsets(zq_ctx *ctx, zq_row_order order, int64_t *node_off, int64_t *body_off);
+
 /* FP64 node data export (synchronous; HOST arrays, N - m rows each, NULL
  * skips): centroid[3*q + a]; T22[6*q + i] packed lower triangle
  * (L00, L10, L11, L20, L21, L22). */

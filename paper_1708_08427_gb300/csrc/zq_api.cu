@@ -202,7 +202,7 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
     if (n > zq::kSmallSortMax && n > max_big) max_big = n;
   }
   const int64_t N = off[m];
-  if (N > 700000000LL) return ZQ_EINVAL;
+  if (N > zq::kMaxBeads) return ZQ_EINVAL;
   Ctx& c = ctx->c;
   c.time_started = false;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
@@ -670,6 +670,82 @@ zq_status zq_get_tree(zq_ctx* ctx, int32_t* perm, int32_t* left, int32_t* right,
     for (int64_t i = 0; i < c.nodes; ++i) height[i] = h[(size_t)i];
   }
   return ZQ_OK;
+}
+
+// Row offsets of the two layouts of Q~ (Sec. 3).  In-order: a running sum
+// of the node sizes by id.  Pre-order, the recursive [Residue_p;
+// diag(Q~_x, Q~_y)]: a depth-first walk from each body's root that numbers
+// a node before its left subtree and the left subtree before the right one.
+zq_status zq_residue_offsets(int64_t m, const int64_t* off, const int32_t* left, const int32_t* right,
+                             zq_row_order order, int64_t* node_off, int64_t* body_off) {
+  if (m < 1 || !off || !left || !right || !node_off) return ZQ_EINVAL;
+  if (order != ZQ_ROWS_INORDER && order != ZQ_ROWS_PREORDER) return ZQ_EINVAL;
+  if (off[0] != 0) return ZQ_EINVAL;
+  for (int64_t j = 0; j < m; ++j)
+    if (off[j + 1] - off[j] < 3 || off[j + 1] > zq::kMaxBeads) return ZQ_EINVAL;
+  auto rows = [&](int64_t q) -> int64_t { return 3 * ((left[q] >= 0) + (right[q] >= 0)); };
+  // every child inside its body, every internal node the child of at most one node
+  std::vector<uint8_t> is_child((size_t)(off[m] - m), 0);
+  for (int64_t j = 0; j < m; ++j) {
+    const int64_t nb = off[j] - j, ne = off[j + 1] - j - 1;
+    for (int64_t q = nb; q < ne; ++q) {
+      for (const int32_t code : {left[q], right[q]}) {
+        if (code >= 0) {
+          if (code < nb || code >= ne || code == q || is_child[(size_t)code]) return ZQ_EINVAL;
+          is_child[(size_t)code] = 1;
+        } else {
+          const int64_t pos = -1 - (int64_t)code;
+          if (pos < off[j] || pos >= off[j + 1]) return ZQ_EINVAL;
+        }
+      }
+    }
+  }
+  // one tree per body: a single root from which every node is reached (the
+  // walk visits each node once: no node has two parents); the walk is the
+  // pre-order numbering, the in-order one is by id
+  std::vector<int32_t> stack;
+  for (int64_t j = 0; j < m; ++j) {
+    const int64_t nb = off[j] - j, ne = off[j + 1] - j - 1;
+    const int64_t base = 3 * off[j] - 6 * j;
+    int64_t root = -1;
+    for (int64_t q = nb; q < ne; ++q) {
+      if (is_child[(size_t)q]) continue;
+      if (root >= 0) return ZQ_EINVAL;  // two roots
+      root = q;
+    }
+    if (root < 0) return ZQ_EINVAL;
+    int64_t acc = base, reached = 0;
+    stack.assign(1, (int32_t)root);
+    while (!stack.empty()) {
+      const int32_t q = stack.back();
+      stack.pop_back();
+      if (order == ZQ_ROWS_PREORDER) node_off[q] = acc;
+      acc += rows(q);
+      ++reached;
+      if (right[q] >= 0) stack.push_back(right[q]);
+      if (left[q] >= 0) stack.push_back(left[q]);  // the left subtree first
+    }
+    if (reached != ne - nb) return ZQ_EINVAL;
+    if (order == ZQ_ROWS_INORDER) {
+      acc = base;
+      for (int64_t q = nb; q < ne; ++q) {
+        node_off[q] = acc;
+        acc += rows(q);
+      }
+    }
+  }
+  if (body_off)
+    for (int64_t j = 0; j <= m; ++j) body_off[j] = 3 * off[j] - 6 * j;
+  return ZQ_OK;
+}
+
+zq_status zq_get_residue_offsets(zq_ctx* ctx, zq_row_order order, int64_t* node_off, int64_t* body_off) {
+  if (!ctx || !node_off) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.have_tree) return ZQ_ESTATE;
+  std::vector<int32_t> l((size_t)c.nodes), r((size_t)c.nodes);
+  ZQ_TRY(zq_get_tree(ctx, nullptr, l.data(), r.data(), nullptr, nullptr, nullptr, nullptr));
+  return zq_residue_offsets(c.m, c.off_h.data(), l.data(), r.data(), order, node_off, body_off);
 }
 
 zq_status zq_get_nodes(zq_ctx* ctx, double* centroid, double* T22) {

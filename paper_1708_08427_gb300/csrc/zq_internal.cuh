@@ -15,6 +15,7 @@ namespace zq {
 constexpr int kQBits = 21;            // bits per coordinate (Sec. 2.1 quantisation)
 constexpr int kMaxHeight = 96;        // 63 coordinate + 32 index bisection levels + 1
 constexpr int kSmallSortMax = 8192;   // bodies sorted inside one thread block
+constexpr int64_t kMaxBeads = 700000000;  // N cap: node ids, positions and residue offsets fit int32
 // Schedule: nodes of height 1..cut are processed level by level over all
 // bodies at once, sorted by (height, type) into 3 * cut buckets (type 0:
 // two leaf children, k = 3; 1: one, k = 6; 2: none, k = 9); the nodes

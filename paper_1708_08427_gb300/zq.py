@@ -100,6 +100,10 @@ def _lib() -> ctypes.CDLL:
             f = getattr(L, name)
             f.restype = ctypes.c_int
             f.argtypes = [_vp, ctypes.c_int, _i64, _vp, _vp]
+        L.zq_residue_offsets.restype = ctypes.c_int
+        L.zq_residue_offsets.argtypes = [_i64, _i64p, _i32p, _i32p, ctypes.c_int, _i64p, _i64p]
+        L.zq_get_residue_offsets.restype = ctypes.c_int
+        L.zq_get_residue_offsets.argtypes = [_vp, ctypes.c_int, _i64p, _i64p]
         L.zq_apply_Q_noalloc.restype = ctypes.c_int
         L.zq_apply_Q_noalloc.argtypes = [ctypes.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
         _L = L
@@ -392,6 +396,17 @@ class Context:
                                   _np_i32(arrs["roff"])), "zq_get_tree")
         return dict(perm=perm, **arrs)
 
+    def residue_offsets(self, order: str = "preorder"):
+        """Per-node residue offsets of the current tree in row order
+        'inorder' (the products' order) or 'preorder' (the recursive layout
+        [Residue_p; diag(Q~_x, Q~_y)]); returns (node_off, body_off), int64."""
+        N, m, R, nodes = self.sizes()
+        node_off = np.empty(nodes, np.int64)
+        body_off = np.empty(m + 1, np.int64)
+        _check(_lib().zq_get_residue_offsets(self._h, _ROW_ORDER[order], node_off.ctypes.data_as(_i64p),
+                                             body_off.ctypes.data_as(_i64p)), "zq_get_residue_offsets")
+        return node_off, body_off
+
     def get_nodes(self):
         N, m, R, nodes = self.sizes()
         c = np.empty((nodes, 3))
@@ -428,6 +443,26 @@ class Context:
 
 
 ZQ_NOALLOC_MAX_BEADS = 2048
+
+
+_ROW_ORDER = {"inorder": 0, "preorder": 1}
+
+
+def residue_offsets(off, left, right, order: str = "preorder"):
+    """zq_residue_offsets on host arrays in zq_get_tree's form: off (m + 1)
+    bead offsets, left / right child codes of the N - m internal nodes.
+    Returns (node_off, body_off), int64."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    left = np.ascontiguousarray(left, dtype=np.int32)
+    right = np.ascontiguousarray(right, dtype=np.int32)
+    m = off.shape[0] - 1
+    node_off = np.empty(left.shape[0], np.int64)
+    body_off = np.empty(m + 1, np.int64)
+    assert right.shape == left.shape and m >= 1 and left.shape[0] == int(off[-1]) - m
+    _check(_lib().zq_residue_offsets(m, off.ctypes.data_as(_i64p), _np_i32(left), _np_i32(right),
+                                     _ROW_ORDER[order], node_off.ctypes.data_as(_i64p),
+                                     body_off.ctypes.data_as(_i64p)), "zq_residue_offsets")
+    return node_off, body_off
 
 
 def apply_Q_noalloc(x, y, z, v, out, stream=None):
