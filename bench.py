@@ -420,7 +420,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": desc, "m": m, "N": N, "residues": R, "level_cut": args.cut,
                    "level_cut_tuning_ms": tuned,
                    "graph": not args.no_graph, "prec": "fp32", "build": args.build,
-                   "step": "tree + FP64 transforms + Q~v + Q~^T w (one C-ABI call, zq_pipeline)",
+                   "step": ("tree + transforms (" + ("double-single" if args.build == "dd" else "FP64")
+                            + ") + Q~v + Q~^T w, one C-ABI call (zq_pipeline)"),
                    "l2": "512 MB buffer written before every step, outside the step events",
                    "wall_s_timed_region": wall},
         "roofline": roofline, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
