@@ -22,6 +22,8 @@ ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE 
 ZQ_FP64, ZQ_FP32, ZQ_BF16 = 0, 1, 2
 ZQ_HOST_BUFFERS, ZQ_KEEP_TREE, ZQ_GRAPH = 1, 2, 4
 ZQ_BUILD_DD, ZQ_BUILD_FP64 = 0, 1
+ZQ_ORDER_CALLER, ZQ_ORDER_TREE = 0, 1
+ZQ_ROWS_INORDER, ZQ_ROWS_PREORDER = 0, 1
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -370,7 +372,7 @@ class Context:
     def set_vector_order(self, order: str):
         """'caller' (default) or 'tree': bead vectors of the products in the
         tree's sorted-position order (entry s = caller's bead perm[s])."""
-        _check(_lib().zq_set_vector_order(self._h, {"caller": 0, "tree": 1}[order]), "zq_set_vector_order")
+        _check(_lib().zq_set_vector_order(self._h, {"caller": ZQ_ORDER_CALLER, "tree": ZQ_ORDER_TREE}[order]), "zq_set_vector_order")
 
     def set_build_arith(self, arith: str):
         """'dd' (double-single on the FP32 pipes, default) or 'fp64'."""
@@ -445,7 +447,7 @@ class Context:
 ZQ_NOALLOC_MAX_BEADS = 2048
 
 
-_ROW_ORDER = {"inorder": 0, "preorder": 1}
+_ROW_ORDER = {"inorder": ZQ_ROWS_INORDER, "preorder": ZQ_ROWS_PREORDER}
 
 
 def residue_offsets(off, left, right, order: str = "preorder"):

@@ -56,6 +56,23 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.zq_set_vector_order(None, 1) == 1
 
 
+def test_binding_constants_match_the_header():
+    """Every enum value and integer #define of include/zq.h has the same
+    value in the binding."""
+    from paper_1708_08427_gb300 import zq
+
+    text = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "zq.h").read_text(), flags=re.S)
+    values = {}
+    for body in re.findall(r"typedef enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"\b(ZQ_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+            values[name] = int(val)
+    for name, val in re.findall(r"#define\s+(ZQ_[A-Z0-9_]+)\s+(\d+)\b", text):
+        values[name] = int(val)
+    assert len(values) >= 20
+    for name, val in values.items():
+        assert getattr(zq, name) == val, name
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_1708_08427_gb300 import zq
 
