@@ -240,12 +240,18 @@ zq_status zq_apply_QT_block(zq_ctx *ctx, zq_prec prec, int64_t k, const void *W,
  *                    asynchronous call.  The zq_time_kernel events are
  *                    recorded in every replay.  Ignored on the legacy
  *                    default stream.
+ * With both products and the vectors in the caller's order (the default
+ * of zq_set_vector_order), the step moves the bead planes into the tree's
+ * order around its sweeps: v is gathered through perm next to the
+ * transform build and Q~^T w is scattered back after its sweep, through
+ * two 3N-value planes the context owns (allocated on first use and when N
+ * or the precision grows).  The results are the same numbers.
  * Only the transform copy of the requested precision is refreshed, so a
  * later zq_apply_Q / zq_apply_QT must use the same precision (else
  * ZQ_ESTATE).  Asynchronous; the results are ready after zq_sync.  When m,
- * off and level_cut equal the previous call's, no host synchronisation
- * happens and the call can be captured into a CUDA graph (device buffers
- * only). */
+ * off, level_cut and prec equal the previous call's, no host
+ * synchronisation or allocation happens and the call can be captured into
+ * a CUDA graph (device buffers only). */
 #define ZQ_HOST_BUFFERS 1
 #define ZQ_KEEP_TREE 2
 #define ZQ_GRAPH 4
