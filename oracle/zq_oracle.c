@@ -44,11 +44,12 @@
  *     made nonnegative by flipping the signs of rows of R and of Q^T
  *     together: T22 = R(1:3,1:3)^T lower triangular with a nonnegative
  *     diagonal (the layout of Eq. 3.6), G = Q^T; a column whose part below
- *     the diagonal is exactly zero gets no reflection.  Before each reflection,
- *     entries of the column whose binary exponent is more than 40 below
- *     that of the largest entry of M are set to 0 (rounding noise of an
- *     exact zero when M is rank-deficient; LAPACK would reflect on the
- *     noise).
+ *     the diagonal is exactly zero gets no reflection.  Before each
+ *     reflection, a column whose entries (from the diagonal down) all have
+ *     binary exponents more than 40 below that of the largest entry of M is
+ *     set to 0 (rounding noise of an exact zero when M is rank-deficient;
+ *     LAPACK would reflect on the noise); any other column is reduced
+ *     exactly as LAPACK reduces it.
  *   - A node whose T22 comes out (numerically) singular is flagged
  *     degenerate: a diagonal entry of T22 zero or more than 33 binary
  *     orders below M's largest entry; coincident beads in Case I (d = 0)
@@ -193,14 +194,19 @@ static void lq(const double *M, int k, double *L, double *G) {
       A[i][j] = M[j * k + i];
       if (A[i][j] != 0.0 && ilogb(A[i][j]) > emax) emax = ilogb(A[i][j]);
     }
-  /* An entry whose binary exponent is more than 40 below that of the
-   * largest entry of M is rounding noise of an exact zero (rank-deficient
-   * M: collinear or coincident beads below the node); such entries are set
-   * to zero before each reflection, so that the reflection is a
-   * deterministic function of the geometry. */
+  /* Numerical rank decision: when every entry of the column to be
+   * reduced (rows j..k-1) has a binary exponent more than 40 below that of
+   * the largest entry of M, the column is rounding noise of an exact zero
+   * (rank-deficient M: collinear or coincident beads below the node) and
+   * is set to zero, so that the factorisation is a deterministic function
+   * of the geometry.  A column with any entry above that level is reduced
+   * exactly as LAPACK does, small entries included. */
   for (int j = 0; j < 3; ++j) {
+    int noise = 1;
     for (int i = j; i < k; ++i)
-      if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;
+      if (A[i][j] != 0.0 && ilogb(A[i][j]) >= emax - 40) noise = 0;
+    if (noise)
+      for (int i = j; i < k; ++i) A[i][j] = 0.0;
     for (int i = 0; i < k; ++i) v[j][i] = 0.0;
     v[j][j] = 1.0;
     double xn2 = 0.0;

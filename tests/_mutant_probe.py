@@ -24,6 +24,7 @@ CHECKS = [
     lambda: P.test_table1_orthogonality(500),
     lambda: [P.test_node_assembly_eq_3_5(s) for s in range(3)],
     lambda: P.test_lq_rank_deficient_is_exact_and_valid(),
+    lambda: [P.test_lq_badly_scaled_full_rank_matches_lapack(e) for e in (33, 39)],
     lambda: [P.test_singular_T22_flag_marks_exactly_the_collinear_nodes(n) for n in (12, 27)],
 ]
 

@@ -42,7 +42,9 @@ MUTANTS = [
     ("sign_flip_R_only", "for (int c = 0; c < k; ++c) G[j * k + c] = -G[j * k + c];", ";"),
     ("rank_flag_last_pivot_only", "for (int j = 0; j < 3; ++j)\n    if (L[4 * j] == 0.0", "for (int j = 2; j < 3; ++j)\n    if (L[4 * j] == 0.0"),
     ("rank_flag_never", "p->degenerate = rank_deficient(M, k, p->L);", "p->degenerate = 0;"),
-    ("no_numerical_zero_rule", "if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;", ";"),
+    ("no_numerical_zero_rule", "    if (noise)\n      for (int i = j; i < k; ++i) A[i][j] = 0.0;", ";"),
+    ("zero_rule_per_entry", "if (noise)\n      for (int i = j; i < k; ++i) A[i][j] = 0.0;",
+     "for (int i = j; i < k; ++i)\n      if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;"),
 ]
 
 

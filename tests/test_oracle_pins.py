@@ -483,6 +483,61 @@ def test_lq_rank_deficient_is_exact_and_valid():
             np.testing.assert_allclose(M @ G[3:].T, 0.0, atol=1e-14)
 
 
+def _scaled_full_rank_M(rng, k, e):
+    """M = [s T22_x | (T22_y) | K] with the child block s T22_x lower
+    triangular, entries of magnitude [1/2, 1) s, s = 2^-e, beside an O(1)
+    skew block K = [d]x (rank two) and, for k = 9, an O(1) lower-triangular
+    T22_y: a full-rank M whose third singular value is about s |M| (a tight
+    child cluster next to a far sibling)."""
+    sgn = lambda shape: rng.choice([-1.0, 1.0], shape)
+    d = rng.uniform(0.5, 1.0, 3) * sgn(3)
+    T = np.tril(rng.uniform(0.5, 1.0, (3, 3)) * sgn((3, 3))) * 2.0 ** -e
+    if k == 6:
+        return np.hstack([T, _cross(d)])
+    T2 = np.tril(rng.uniform(0.5, 1.0, (3, 3)) * sgn((3, 3)))
+    return np.hstack([T, T2, _cross(d)])
+
+
+@pytest.mark.parametrize("e", [10, 20, 30, 33, 36, 38, 39, 40])
+def test_lq_badly_scaled_full_rank_matches_lapack(e):
+    """Full-rank M whose child block is 2^-e of the rest (e <= 40): the
+    numerical rank decision must not fire, so the oracle's G equals LAPACK's
+    Householder QR (Matlab qr) of M^T up to the forward error of a
+    backward-stable QR, 8 cond(M) 2^-53, and T22 likewise.  A rule that
+    zeroed small entries one by one (rather than whole noise columns)
+    perturbs the third pivot column by up to 2^-40 |M| against a column
+    norm of about 2^-e |M| and fails this bound by orders of magnitude."""
+    rng = np.random.default_rng(500 + e)
+    u = 2.0 ** -53
+    for _ in range(60):
+        for k in (6, 9):
+            M = _scaled_full_rank_M(rng, k, e)
+            L, G = oracle.lq(M)
+            Q, R = qr_nonneg(M.T)
+            kap = np.linalg.cond(M)
+            assert np.abs(G - Q.T).max() <= 8.0 * kap * u, (k, e, np.abs(G - Q.T).max() / (kap * u))
+            assert np.abs(L - R[:3, :3].T).max() <= 8.0 * kap * u * np.abs(M).max()
+            assert np.all(np.diag(L) > 0.0)
+
+
+@pytest.mark.parametrize("e", [41, 42, 45, 50, 60])
+def test_lq_below_rank_threshold_is_a_small_backward_perturbation(e):
+    """Below the threshold (child block 2^-e of |M|, e > 40) the third
+    column is rounding-level relative to M: the oracle treats M as rank two,
+    and its factorisation is then the exact LQ of a matrix within
+    2^-40 sqrt(k) max|M| of M: G orthogonal, [T22 0] G = M to that bound,
+    T22 lower triangular with a nonnegative diagonal."""
+    rng = np.random.default_rng(600 + e)
+    for _ in range(60):
+        for k in (6, 9):
+            M = _scaled_full_rank_M(rng, k, e)
+            L, G = oracle.lq(M)
+            np.testing.assert_allclose(G @ G.T, np.eye(k), atol=1e-14)
+            back = np.abs(np.hstack([L, np.zeros((3, k - 3))]) @ G - M).max()
+            assert back <= 2.0 ** -40 * np.sqrt(k) * np.abs(M).max(), (k, e, back)
+            assert np.all(np.triu(L, 1) == 0.0) and np.all(np.diag(L) >= 0.0)
+
+
 @pytest.mark.parametrize("n", [6, 13, 30])
 def test_collinear_and_lattice_bodies(n):
     """Exactly collinear beads (rank Z = 5) and a lattice (many collinear
