@@ -377,8 +377,8 @@ zq_status zq_get_records(zq_ctx *ctx, double *rec);
  * Q~ v for one small body without allocating device memory.
  *
  * The paper has no counterpart to this entry point: it computes the same
- * product as zq_build_tree + zq_build_transforms + zq_apply_Q (Algorithm 2,
- * Eqs. 4.2-4.3, FP64) for ONE body, for callers that cannot allocate device
+ * product as zq_build_tree + zq_build_transforms + zq_apply_Q in FP64 for
+ * ONE body, for callers that cannot allocate device
  * memory where they call it -- code inside a host framework that owns all
  * device memory through its own allocator, or a loop that runs on a fixed
  * memory budget -- and so cannot hold a zq_ctx, whose workspace grows with
@@ -405,6 +405,12 @@ zq_status zq_get_records(zq_ctx *ctx, double *rec);
  * (cudaGetSymbolAddress, with that device made current for the lookup, then
  * the caller's current device restored); make that first call before any
  * stream capture starts on the device.  Later calls only launch one kernel.
+ * The address is kept for the life of the process: after cudaDeviceReset on
+ * that device the library's module is reloaded and the kept address is no
+ * longer valid, so do not call this entry point again after a reset.  The
+ * kernel keeps everything per thread in registers (no local-memory stack
+ * frame), so its first launch does not make the driver enlarge the
+ * context's local-memory reservation.
  *
  * All calls on a device share the one array: two calls whose kernels can
  * run at the same time (different streams, or different host threads,

@@ -10,10 +10,11 @@
 //       dgeqrf convention: beta_j = -sign(alpha_j) ||x||, no reflection when
 //       the part below the diagonal is exactly zero; then R's diagonal made
 //       nonnegative; T22_p = R^T, G = Q^T);
-//       before each reflection, column entries whose binary exponent is
-//       more than 40 below that of M's largest entry are set to zero, so
-//       rank-deficient M (collinear or coincident beads) give a transform
-//       that does not depend on rounding noise.
+//       before each reflection, a column whose entries (diagonal down) all
+//       have binary exponents more than 40 below that of M's largest entry
+//       is set to zero (numerical rank decision), so rank-deficient M
+//       (collinear or coincident beads) give a transform that does not
+//       depend on rounding noise; other columns are reduced as they are.
 // Case I (two leaves, Eqs. 3.9-3.10): G rows g1 = (e_x x d)/|e_x x d|
 // (e_y x d when d has no y, z part), g2 = dhat x g1, g3 = -dhat, and
 // T22_p = sqrt(n_x n_y / n) |d| [g2, -g1, 0]; d = 0 gives G = I, T22 = 0
@@ -283,10 +284,17 @@ __device__ __forceinline__ R reflector(R& al, R (&x)[M]) {
   return tau;
 }
 
-// The zero rule: entries whose exponent is more than 40 below the largest.
-template <class R>
-__device__ __forceinline__ void flush(R& v, int lim) {
-  if (Real<R>::bexp(v) < lim) v = Real<R>::from_float(0.0f);
+// The numerical rank decision: the column to be reduced (its entries from
+// the diagonal down) is set to zero when every entry's exponent is more
+// than 40 below M's largest (lim); otherwise it is left as it is.
+template <class R, class... Rs>
+__device__ __forceinline__ void flush_col(int lim, R& a, Rs&... rest) {
+  using RT = Real<R>;
+  const bool noise = (RT::bexp(a) < lim) && ((RT::bexp(rest) < lim) && ...);
+  if (noise) {
+    a = RT::from_float(0.0f);
+    ((rest = RT::from_float(0.0f)), ...);
+  }
 }
 
 // After the three reflections: the rank test, then T22's diagonal made
@@ -336,7 +344,7 @@ __device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   rec[1] = g.be;
   rec[13] = rec[14] = rec[15] = zero;
   // H1: column 0, rows 4, 5 below the diagonal
-  flush(A00, lim); flush(A40, lim); flush(A50, lim);
+  flush_col(lim, A00, A40, A50);
   {
     R x[2] = {A40, A50};
     const R tau = reflector<R, 2>(A00, x);
@@ -348,7 +356,7 @@ __device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
     rec[2] = tau; rec[5] = v4; rec[6] = v5;
   }
   // H2: column 1, rows 3, 4, 5
-  flush(A11, lim); flush(A31, lim); flush(A41, lim); flush(A51, lim);
+  flush_col(lim, A11, A31, A41, A51);
   {
     R x[3] = {A31, A41, A51};
     const R tau = reflector<R, 3>(A11, x);
@@ -358,7 +366,7 @@ __device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
     rec[3] = tau; rec[7] = v3; rec[8] = v4; rec[9] = v5;
   }
   // H3: column 2, rows 3, 4, 5
-  flush(A22, lim); flush(A32, lim); flush(A42, lim); flush(A52, lim);
+  flush_col(lim, A22, A32, A42, A52);
   {
     R x[3] = {A32, A42, A52};
     const R tau = reflector<R, 3>(A22, x);
@@ -399,7 +407,7 @@ __device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   rec[1] = g.be;
   rec[19] = zero;
   // H1: column 0, rows 3, 7, 8
-  flush(A00, lim); flush(A30, lim); flush(A70, lim); flush(A80, lim);
+  flush_col(lim, A00, A30, A70, A80);
   {
     R x[3] = {A30, A70, A80};
     const R tau = reflector<R, 3>(A00, x);
@@ -411,7 +419,7 @@ __device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
     rec[2] = tau; rec[5] = v3; rec[6] = v7; rec[7] = v8;
   }
   // H2: column 1, rows 3, 4, 6, 7, 8
-  flush(A11, lim); flush(A31, lim); flush(A41, lim); flush(A61, lim); flush(A71, lim); flush(A81, lim);
+  flush_col(lim, A11, A31, A41, A61, A71, A81);
   {
     R x[5] = {A31, A41, A61, A71, A81};
     const R tau = reflector<R, 5>(A11, x);
@@ -421,8 +429,7 @@ __device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
     rec[3] = tau; rec[8] = v3; rec[9] = v4; rec[10] = v6; rec[11] = v7; rec[12] = v8;
   }
   // H3: column 2, rows 3..8
-  flush(A22, lim); flush(A32, lim); flush(A42, lim); flush(A52, lim); flush(A62, lim);
-  flush(A72, lim); flush(A82, lim);
+  flush_col(lim, A22, A32, A42, A52, A62, A72, A82);
   {
     R x[6] = {A32, A42, A52, A62, A72, A82};
     const R tau = reflector<R, 6>(A22, x);

@@ -15,8 +15,9 @@
 // 21-bit keys, z/y/x bisection, ties by index), then, height by height, each
 // node's FP64 transform (Case I closed form, or the Householder LQ of
 // [T22_x | T22_y | K] with the LAPACK reflector convention, T22's diagonal
-// made nonnegative and the numerical-zero rule) immediately applied to the node's Info-set, writing the Residues to
-// the output in the same order as zq_apply_Q.
+// made nonnegative and the numerical rank decision) immediately applied to
+// the node's Info-set, writing the Residues to the output in the same order
+// as zq_apply_Q.
 #include <mutex>
 
 #include "zq_internal.cuh"
@@ -25,7 +26,13 @@ namespace zq {
 namespace {
 
 constexpr int kNA = ZQ_NOALLOC_MAX_BEADS;  // beads
-constexpr int kNAThreads = 512;
+constexpr int kNAThreads = 256;
+// The bitonic sort pads n to a power of two P <= kNA; bead indices are
+// uint16 with 0xffff as padding, and the arrival slots carry a 16-bit range
+// end; the static shared arrays (19 bytes per bead) must fit in 48 KB.
+static_assert((kNA & (kNA - 1)) == 0, "ZQ_NOALLOC_MAX_BEADS must be a power of two");
+static_assert(kNA < 65535, "bead indices and range ends are 16-bit");
+static_assert(kNA <= 2048, "static shared memory of k_noalloc_apply_q is sized for at most 2048 beads");
 
 // Scratch layout (per body of at most kNA beads; node arrays indexed by
 // split position g in [0, n - 2]):
@@ -59,58 +66,105 @@ __device__ __forceinline__ uint32_t na_quantise(double p, double lo, double hi) 
   return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
 }
 
-// Householder LQ of the 3 x k matrix M = A^T (A given as k x 3), T22's
-// diagonal made nonnegative: fills L (3 x 3 lower, packed) and the dense
-// k x k G = D H3 H2 H1.
-__device__ void na_lq(double (&A)[9][3], int k, double* L, double (&G)[9][9]) {
-  double v[3][9], tau[3];
+// Householder LQ of the 3 x K matrix M = A^T (A given as K x 3), T22's
+// diagonal made nonnegative: fills L (3 x 3 lower, packed) and the
+// reflectors of G = D H3 H2 H1 (v[j] with v[j][j] = 1, tau[j], and the sign
+// flips D as flip[j]); G itself is never formed.  K is a compile-time
+// constant so that every array stays in registers.
+template <int K>
+__device__ __forceinline__ void na_lq(double (&A)[K][3], double* L, double (&v)[3][K], double (&tau)[3],
+                                      bool (&flip)[3]) {
   int emax = -100000;
-  for (int i = 0; i < k; ++i)
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
     for (int c = 0; c < 3; ++c)
       if (A[i][c] != 0.0 && ilogb(A[i][c]) > emax) emax = ilogb(A[i][c]);
+#pragma unroll
   for (int j = 0; j < 3; ++j) {
-    for (int i = j; i < k; ++i)
-      if (A[i][j] != 0.0 && ilogb(A[i][j]) < emax - 40) A[i][j] = 0.0;
-    for (int i = 0; i < k; ++i) v[j][i] = 0.0;
+    // numerical rank decision: a column whose entries (diagonal down) are
+    // all more than 40 binary orders below M's largest is rounding noise
+    bool noise = true;
+#pragma unroll
+    for (int i = j; i < K; ++i)
+      if (A[i][j] != 0.0 && ilogb(A[i][j]) >= emax - 40) noise = false;
+    if (noise) {
+#pragma unroll
+      for (int i = j; i < K; ++i) A[i][j] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[j][i] = 0.0;
     v[j][j] = 1.0;
     double xn2 = 0.0;
-    for (int i = j + 1; i < k; ++i) xn2 += A[i][j] * A[i][j];
-    if (xn2 == 0.0) {
-      tau[j] = 0.0;
-      continue;
-    }
-    const double al = A[j][j];
-    const double norm = sqrt(al * al + xn2);
-    const double be = (al >= 0.0) ? -norm : norm;
-    tau[j] = (be - al) / be;
-    for (int i = j + 1; i < k; ++i) v[j][i] = A[i][j] / (al - be);
-    A[j][j] = be;
-    for (int i = j + 1; i < k; ++i) A[i][j] = 0.0;
-    for (int c = j + 1; c < 3; ++c) {
-      double w = 0.0;
-      for (int i = j; i < k; ++i) w += v[j][i] * A[i][c];
-      for (int i = j; i < k; ++i) A[i][c] -= tau[j] * w * v[j][i];
+#pragma unroll
+    for (int i = j + 1; i < K; ++i) xn2 += A[i][j] * A[i][j];
+    tau[j] = 0.0;
+    if (xn2 != 0.0) {
+      const double al = A[j][j];
+      const double norm = sqrt(al * al + xn2);
+      const double be = (al >= 0.0) ? -norm : norm;
+      tau[j] = (be - al) / be;
+#pragma unroll
+      for (int i = j + 1; i < K; ++i) v[j][i] = A[i][j] / (al - be);
+      A[j][j] = be;
+#pragma unroll
+      for (int i = j + 1; i < K; ++i) A[i][j] = 0.0;
+#pragma unroll
+      for (int c = j + 1; c < 3; ++c) {
+        double w = 0.0;
+#pragma unroll
+        for (int i = j; i < K; ++i) w += v[j][i] * A[i][c];
+#pragma unroll
+        for (int i = j; i < K; ++i) A[i][c] -= tau[j] * w * v[j][i];
+      }
     }
   }
   // nonnegative diagonal of R: rows of R and of G flip together
-  bool flip[3];
+#pragma unroll
   for (int j = 0; j < 3; ++j) {
     flip[j] = A[j][j] < 0.0;
-    if (flip[j])
+    if (flip[j]) {
+#pragma unroll
       for (int c = j; c < 3; ++c) A[j][c] = -A[j][c];
+    }
   }
   L[0] = A[0][0]; L[1] = A[0][1]; L[2] = A[1][1]; L[3] = A[0][2]; L[4] = A[1][2]; L[5] = A[2][2];
-  for (int r = 0; r < k; ++r)
-    for (int c = 0; c < k; ++c) G[r][c] = (r == c) ? 1.0 : 0.0;
+}
+
+// One node of Eq. 3.5 with K = 6 (one internal child, block L1) or K = 9
+// (blocks L1 = T22_x, L2 = T22_y): M = [L1 | L2 | K], K = sk [d]x, factorised
+// into L, then u <- G u = D H3 H2 H1 u.
+template <int K>
+__device__ __forceinline__ void na_node(const double* L1, const double* L2, double sk, const double* d,
+                                        double* L, double (&u)[K]) {
+  double A[K][3];
+  const double* Ls[2] = {L1, L2};
+#pragma unroll
+  for (int b = 0; b < K / 3 - 1; ++b) {
+    const double* Lc = Ls[b];
+    A[3 * b][0] = Lc[0]; A[3 * b][1] = Lc[1]; A[3 * b][2] = Lc[3];
+    A[3 * b + 1][0] = 0.0; A[3 * b + 1][1] = Lc[2]; A[3 * b + 1][2] = Lc[4];
+    A[3 * b + 2][0] = 0.0; A[3 * b + 2][1] = 0.0; A[3 * b + 2][2] = Lc[5];
+  }
+  constexpr int k0 = K - 3;
+  A[k0][0] = sk * 0.0; A[k0][1] = sk * d[2]; A[k0][2] = sk * (-d[1]);
+  A[k0 + 1][0] = sk * (-d[2]); A[k0 + 1][1] = sk * 0.0; A[k0 + 1][2] = sk * d[0];
+  A[k0 + 2][0] = sk * d[1]; A[k0 + 2][1] = sk * (-d[0]); A[k0 + 2][2] = sk * 0.0;
+  double v[3][K], tau[3];
+  bool flip[3];
+  na_lq<K>(A, L, v, tau, flip);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    double w = 0.0;
+#pragma unroll
+    for (int i = j; i < K; ++i) w += v[j][i] * u[i];
+    w *= tau[j];
+#pragma unroll
+    for (int i = j; i < K; ++i) u[i] -= w * v[j][i];
+  }
+#pragma unroll
   for (int j = 0; j < 3; ++j)
-    for (int c = 0; c < k; ++c) {
-      double w = 0.0;
-      for (int i = 0; i < k; ++i) w += v[j][i] * G[i][c];
-      for (int i = 0; i < k; ++i) G[i][c] -= tau[j] * w * v[j][i];
-    }
-  for (int j = 0; j < 3; ++j)
-    if (flip[j])
-      for (int c = 0; c < k; ++c) G[j][c] = -G[j][c];
+    if (flip[j]) u[j] = -u[j];
 }
 
 __global__ void __launch_bounds__(kNAThreads)
@@ -290,77 +344,57 @@ k_noalloc_apply_q(NAScratch* __restrict__ S, int n, const double* __restrict__ x
       const double dn = (double)(nx + ny);
       const double al = sqrt((double)nx / dn), be = sqrt((double)ny / dn);
       const double sk = sqrt((double)nx * (double)ny / dn);
-      double d[3], cp[3], L[6], G[9][9];
+      double d[3], cp[3], L[6], t[3], s3[3];
       for (int i = 0; i < 3; ++i) {
         d[i] = cX[i] - cY[i];
         cp[i] = ((double)nx * cX[i] + (double)ny * cY[i]) / dn;
+        // upward step (Eq. 4.2): t = alpha t_x + beta t_y, s = beta t_x - alpha t_y
+        t[i] = al * tX[i] + be * tY[i];
+        s3[i] = be * tX[i] - al * tY[i];
       }
-      int k;
-      if (cx < 0 && cy < 0) {  // Case I, Eqs. 3.9-3.10
-        k = 3;
+      double r[3];  // the node's rotational Info-set: first three rows of G u
+      const int32_t ro = S->roff[g];
+      if (cx < 0 && cy < 0) {  // Case I, Eqs. 3.9-3.10: G u with the explicit 3 x 3 G
         const double dd2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         for (int i = 0; i < 6; ++i) L[i] = 0.0;
         if (dd2 == 0.0) {
-          for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) G[r][c] = (r == c) ? 1.0 : 0.0;
+          for (int i = 0; i < 3; ++i) r[i] = s3[i];
         } else {
           const double dnorm = sqrt(dd2);
           const double hd[3] = {d[0] / dnorm, d[1] / dnorm, d[2] / dnorm};
           double g1[3];
           if (d[1] != 0.0 || d[2] != 0.0) {
-            const double s = sqrt(d[1] * d[1] + d[2] * d[2]);
-            g1[0] = 0.0; g1[1] = -d[2] / s; g1[2] = d[1] / s;
+            const double sq = sqrt(d[1] * d[1] + d[2] * d[2]);
+            g1[0] = 0.0; g1[1] = -d[2] / sq; g1[2] = d[1] / sq;
           } else {
             g1[0] = 0.0; g1[1] = 0.0; g1[2] = d[0] > 0.0 ? -1.0 : 1.0;
           }
           const double g2[3] = {hd[1] * g1[2] - hd[2] * g1[1], hd[2] * g1[0] - hd[0] * g1[2],
                                 hd[0] * g1[1] - hd[1] * g1[0]};
-          for (int c = 0; c < 3; ++c) {
-            G[0][c] = g1[c];
-            G[1][c] = g2[c];
-            G[2][c] = -hd[c];
-          }
+          r[0] = g1[0] * s3[0] + g1[1] * s3[1] + g1[2] * s3[2];
+          r[1] = g2[0] * s3[0] + g2[1] * s3[1] + g2[2] * s3[2];
+          r[2] = -(hd[0] * s3[0] + hd[1] * s3[1] + hd[2] * s3[2]);
           const double sl = sk * dnorm;
           L[0] = sl * g2[0]; L[1] = sl * g2[1]; L[2] = -sl * g1[1];
           L[3] = sl * g2[2]; L[4] = -sl * g1[2]; L[5] = 0.0;
         }
-      } else {                 // Eq. 3.5 / Case II
-        double A[9][3];
-        k = 0;
-        const double* Ls[2] = {cx >= 0 ? LX : nullptr, cy >= 0 ? LY : nullptr};
-        for (int c = 0; c < 2; ++c) {
-          const double* Lc = Ls[c];
-          if (!Lc) continue;
-          A[k][0] = Lc[0]; A[k][1] = Lc[1]; A[k][2] = Lc[3];
-          A[k + 1][0] = 0.0; A[k + 1][1] = Lc[2]; A[k + 1][2] = Lc[4];
-          A[k + 2][0] = 0.0; A[k + 2][1] = 0.0; A[k + 2][2] = Lc[5];
-          k += 3;
-        }
-        A[k][0] = sk * 0.0; A[k][1] = sk * d[2]; A[k][2] = sk * (-d[1]);
-        A[k + 1][0] = sk * (-d[2]); A[k + 1][1] = sk * 0.0; A[k + 1][2] = sk * d[0];
-        A[k + 2][0] = sk * d[1]; A[k + 2][1] = sk * (-d[0]); A[k + 2][2] = sk * 0.0;
-        k += 3;
-        na_lq(A, k, L, G);
+      } else if (cx >= 0 && cy >= 0) {  // Eq. 3.5, k = 9: u = [r_x; r_y; s]
+        double u[9] = {rX[0], rX[1], rX[2], rY[0], rY[1], rY[2], s3[0], s3[1], s3[2]};
+        na_node<9>(LX, LY, sk, d, L, u);
+        for (int i = 0; i < 3; ++i) r[i] = u[i];
+        for (int i = 3; i < 9; ++i) out[ro + i - 3] = u[i];
+      } else {                 // Case II, k = 6: u = [r_c; s] of the internal child c
+        const double* Lc = cx >= 0 ? LX : LY;
+        const double* rc = cx >= 0 ? rX : rY;
+        double u[6] = {rc[0], rc[1], rc[2], s3[0], s3[1], s3[2]};
+        na_node<6>(Lc, nullptr, sk, d, L, u);
+        for (int i = 0; i < 3; ++i) r[i] = u[i];
+        for (int i = 3; i < 6; ++i) out[ro + i - 3] = u[i];
       }
-      // upward step: [r; eps] = G [r_x?; r_y?; s], t = alpha t_x + beta t_y
-      double u[9], t[3];
-      int m = 0;
-      if (cx >= 0) for (int i = 0; i < 3; ++i) u[m++] = rX[i];
-      if (cy >= 0) for (int i = 0; i < 3; ++i) u[m++] = rY[i];
-      for (int i = 0; i < 3; ++i) {
-        t[i] = al * tX[i] + be * tY[i];
-        u[m++] = be * tX[i] - al * tY[i];
-      }
-      double yv[9];
-      for (int i = 0; i < k; ++i) {
-        yv[i] = 0.0;
-        for (int c = 0; c < k; ++c) yv[i] += G[i][c] * u[c];
-      }
-      for (int i = 3; i < k; ++i) out[S->roff[g] + i - 3] = yv[i];
       for (int i = 0; i < 3; ++i) {
         S->st[g][i] = cp[i];
         S->info[g][i] = t[i];
-        S->info[g][3 + i] = yv[i];
+        S->info[g][3 + i] = r[i];
       }
       for (int i = 0; i < 6; ++i) S->st[g][3 + i] = L[i];
     }
