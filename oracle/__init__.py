@@ -79,6 +79,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.orc_body_node.argtypes = [ctypes.c_void_p, ctypes.c_int64, _c_int32_p, _c_int32_p,
                                   _c_int32_p, _c_double_p, _c_double_p, _c_double_p,
                                   _c_double_p]
+    lib.orc_body_nodes_all.restype = None
+    lib.orc_body_nodes_all.argtypes = [ctypes.c_void_p, _c_double_p, _c_double_p]
     lib.orc_lq.restype = None
     lib.orc_lq.argtypes = [_c_double_p, ctypes.c_int32, _c_double_p, _c_double_p]
     lib.orc_case_one.restype = None
@@ -159,6 +161,14 @@ class Body:
         kk = int(k.value)
         return dict(k=kk, cnt=int(cnt.value), degenerate=bool(dg.value), alpha=ab[0],
                     beta=ab[1], c=c, L=L.reshape(3, 3), G=G[:kk * kk].reshape(kk, kk))
+
+    def nodes_all(self):
+        """(T22, centroid) of every node by split position: (n-1, 3, 3) lower
+        triangular and (n-1, 3)."""
+        L = np.empty((self.n - 1) * 9)
+        c = np.empty((self.n - 1) * 3)
+        self._lib.orc_body_nodes_all(self._h, _dp(L), _dp(c))
+        return L.reshape(self.n - 1, 3, 3), c.reshape(self.n - 1, 3)
 
     def apply_Q(self, f, with_root: bool = False):
         f = _f64(f)

@@ -460,6 +460,15 @@ void orc_body_node(const orc_body *b, int64_t g, int32_t *k, int32_t *cnt, int32
   memcpy(G, p->G, (size_t)(p->k * p->k) * sizeof(double));
 }
 
+/* T22 (row-major 3 x 3) and centroid of every node, by split position:
+ * the tests take the conditioning of each node's factorisation from them. */
+void orc_body_nodes_all(const orc_body *b, double *L, double *c) {
+  for (int64_t g = 0; g < b->n - 1; ++g) {
+    memcpy(L + 9 * g, b->node[g].L, 9 * sizeof(double));
+    memcpy(c + 3 * g, b->node[g].c, 3 * sizeof(double));
+  }
+}
+
 /* Node-level entry points, used by the tests to pin single steps. */
 void orc_lq(const double *M, int32_t k, double *L, double *G) { lq(M, k, L, G); }
 

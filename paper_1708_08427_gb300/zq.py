@@ -424,25 +424,6 @@ class Context:
         _check(_lib().zq_get_records(self._h, rec.ctypes.data_as(_f64p)), "zq_get_records")
         return rec
 
-    @staticmethod
-    def record_to_G(rec: np.ndarray, k: int) -> np.ndarray:
-        """Dense k x k transform G from one FP64 record (host-side, for
-        inspection and tests only)."""
-        if k == 3:
-            return rec[5:14].reshape(3, 3).copy()
-        G = np.eye(k)
-        tail = 5
-        for j in range(3):
-            v = np.zeros(k)
-            v[j] = 1.0
-            v[j + 1:] = rec[tail:tail + k - 1 - j]
-            tail += k - 1 - j
-            G = G - abs(rec[2 + j]) * np.outer(v, v @ G)
-        for j in range(3):
-            if np.signbit(rec[2 + j]):
-                G[j] = -G[j]
-        return G
-
 
 ZQ_NOALLOC_MAX_BEADS = 2048
 

@@ -2,24 +2,27 @@
 
 Every column of the block must equal the oracle's Q~v / Q~^T w of that
 column: FP64 within 1e-12 and FP32 within 1e-5 relative per body and column
-(the single-vector tolerances).  BF16 stores inputs and outputs in bfloat16
+(the single-vector tolerances), by the body's 2-norm and element by element
+(every element within tol * the body's largest |element|).  BF16 stores inputs and outputs in bfloat16
 (8 significant bits) and computes in FP32: the reference is the oracle
 applied to the bfloat16-rounded inputs, and the only other error is the
-rounding of each output element to bfloat16 (relative error at most 2^-9)
-plus FP32 arithmetic (~1e-6), so the per-body relative 2-norm error is held
-to 2^-9 + 1e-5.  Bodies span several segments and nodes above them
+rounding of each output element to bfloat16 (8-bit significand, round to
+nearest: relative error at most 2^-8)
+plus FP32 arithmetic (~1e-6), so both per-body errors are held to
+2^-8 + 1e-5.  Bodies span several segments and nodes above them
 (n > 512), k is ragged (not a multiple of the warp width).
 """
 import numpy as np
 import pytest
 
 import oracle
+from _parity import compare_per_body
 from paper_1708_08427_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {torch.float64: 1e-12, torch.float32: 1e-5, torch.bfloat16: 2.0 ** -9 + 1e-5}
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5, torch.bfloat16: 2.0 ** -8 + 1e-5}
 
 
 def _dev():
@@ -39,20 +42,6 @@ def _ctx(bt):
     return ctx
 
 
-def _per_body(got, ref, bt, kind):
-    errs = []
-    ro = 0
-    for j in range(bt.m):
-        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
-        if kind == "res":
-            a, b = got[ro:ro + 3 * n - 6], ref[ro:ro + 3 * n - 6]
-        else:
-            a, b = got[3 * o:3 * (o + n)], ref[3 * o:3 * (o + n)]
-        ro += 3 * n - 6
-        errs.append(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    return max(errs)
-
-
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("k", [1, 7, 64])
 def test_block_form_matches_oracle(dtype, k):
@@ -68,12 +57,11 @@ def test_block_form_matches_oracle(dtype, k):
     ctx.sync()
     Vd = V.double().cpu().numpy()   # the (rounded) inputs the kernel saw
     Wd = Wr.double().cpu().numpy()
-    worst = 0.0
     for c in range(k):
         rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*Vd[:, c].reshape(3, bt.N)), Wd[:, c])
-        worst = max(worst, _per_body(QV[:, c], rq, bt, "res"))
-        worst = max(worst, _per_body(W.interleave(*QTW[:, c].reshape(3, bt.N)), rqt, bt, "bead"))
-    assert worst <= TOL[dtype], (dtype, k, worst)
+        compare_per_body(QV[:, c], rq, bt.off, "res", TOL[dtype], f"{dtype} k={k} Q~V column {c}")
+        compare_per_body(W.interleave(*QTW[:, c].reshape(3, bt.N)), rqt, bt.off, "bead", TOL[dtype],
+                         f"{dtype} k={k} Q~^T W column {c}")
     ctx.close()
 
 

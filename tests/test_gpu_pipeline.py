@@ -3,7 +3,8 @@ both products (Q~v on the context stream, Q~^T w concurrently on a side
 stream with its own scratch), from device or pinned host buffers, with the
 tree rebuilt or kept.
 
-Against the FP64 oracle per body (1e-12 FP64, 1e-5 FP32).  With the tree
+Against the FP64 oracle per body (1e-12 FP64, 1e-5 FP32), by each body's
+relative 2-norm and element by element.  With the tree
 kept, the oracle's own tree (built from the moved coordinates) is not the
 kept one, so the result is checked against the separate calls on a context
 that built its tree from the original coordinates (bitwise), and against
@@ -13,6 +14,8 @@ import numpy as np
 import pytest
 
 import oracle
+from _parity import compare_per_body
+from paper_1708_08427_gb300 import tune
 from paper_1708_08427_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -31,19 +34,6 @@ def _zq():
     from paper_1708_08427_gb300 import zq
 
     return zq
-
-
-def _per_body(got, ref, bt, kind):
-    errs, ro = [], 0
-    for j in range(bt.m):
-        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
-        if kind == "res":
-            a, b = got[ro:ro + 3 * n - 6], ref[ro:ro + 3 * n - 6]
-        else:
-            a, b = got[3 * o:3 * (o + n)], ref[3 * o:3 * (o + n)]
-        ro += 3 * n - 6
-        errs.append(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    return max(errs)
 
 
 @pytest.mark.parametrize("dtype,host", [(torch.float32, False), (torch.float64, False), (torch.float32, True)])
@@ -71,9 +61,8 @@ def test_pipeline_matches_oracle(dtype, host):
         ctx.pipeline(bt.off, x, y, z, tv, qv, tw, qtw, host=host)
         ctx.sync()
         rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*v), w)
-        e1 = _per_body(qv.double().cpu().numpy(), rq, bt, "res")
-        e2 = _per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt, "bead")
-        assert max(e1, e2) <= TOL[dtype], (e1, e2)
+        compare_per_body(qv.double().cpu().numpy(), rq, bt.off, "res", TOL[dtype], "Q~v")
+        compare_per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt.off, "bead", TOL[dtype], "Q~^T w")
     ctx.close()
 
 
@@ -244,14 +233,14 @@ def test_pipeline_graph_replay_matches_direct(host):
     d.close()
 
 
-@pytest.mark.parametrize("cut", [15, 18])
+@pytest.mark.parametrize("cut", tune.CUTS)
 def test_full_size_step_as_benched(cut):
     """The benchmark's step exactly as bench.py times it: the 2000-shell
     batch (2,155,957 beads, seed 0), one zq_pipeline call per step in FP32
     with the double-single build, on a non-default stream, replayed from the
-    library's CUDA graph (ZQ_GRAPH) at the level cut the tuner picks.  The
-    third call is a replay; every output of it is checked per body against
-    the FP64 oracle (1e-5)."""
+    library's CUDA graph (ZQ_GRAPH), at every level cut the tuner can pick.
+    The third call is a replay; every output of it is checked per body
+    against the FP64 oracle (1e-5), by norm and element by element."""
     zq = _zq()
     dev = _dev()
     bt = W.shell_batch(m=2000, nmin=50, nmax=5000, seed=0)
@@ -278,7 +267,7 @@ def test_full_size_step_as_benched(cut):
     vr = tv.double().cpu().numpy()
     wr = tw.double().cpu().numpy()
     rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*vr), wr)
-    e1 = _per_body(qv.double().cpu().numpy(), rq, bt, "res")
-    e2 = _per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt, "bead")
-    assert max(e1, e2) <= TOL[torch.float32], (e1, e2)
+    compare_per_body(qv.double().cpu().numpy(), rq, bt.off, "res", TOL[torch.float32], f"Q~v cut {cut}")
+    compare_per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt.off, "bead", TOL[torch.float32],
+                     f"Q~^T w cut {cut}")
     ctx.close()

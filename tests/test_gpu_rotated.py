@@ -9,11 +9,13 @@ per-body top-node kernels), and the smallest body (3 beads, Case I at the
 root).  R = I gives the plain products bit for bit, one product alone gives
 the same bits as both at once, and Q~^T Q~ f on the moved bodies is the
 moved bodies' projector f - Z^T (Z Z^T)^-1 Z f (basis-free, FP64 1e-12).
+Products are compared per body by norm and element by element.
 """
 import numpy as np
 import pytest
 
 import oracle
+from _parity import compare_per_body
 from paper_1708_08427_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -65,19 +67,6 @@ def setup():
     ctx.close()
 
 
-def _per_body(got, ref, bt, kind):
-    errs, ro = [], 0
-    for j in range(bt.m):
-        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
-        if kind == "res":
-            a, b = got[ro:ro + 3 * n - 6], ref[ro:ro + 3 * n - 6]
-        else:
-            a, b = got[3 * o:3 * (o + n)], ref[3 * o:3 * (o + n)]
-        ro += 3 * n - 6
-        errs.append(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    return max(errs)
-
-
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_rotated_products_match_oracle(setup, dtype):
     zq, ctx, bt, Rm, dev = setup
@@ -88,9 +77,8 @@ def test_rotated_products_match_oracle(setup, dtype):
     qv, qtw = ctx.apply_rotated(R_d, torch.from_numpy(v).to(dev, dtype), torch.from_numpy(w).to(dev, dtype))
     ctx.sync()
     rq, rqt = oracle.batch_apply_rotated(bt.off, bt.x, bt.y, bt.z, Rm, W.interleave(*v), w)
-    e1 = _per_body(qv.double().cpu().numpy(), rq, bt, "res")
-    e2 = _per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt, "bead")
-    assert max(e1, e2) <= TOL[dtype], (e1, e2)
+    compare_per_body(qv.double().cpu().numpy(), rq, bt.off, "res", TOL[dtype], "rotated Q~v")
+    compare_per_body(W.interleave(*qtw.double().cpu().numpy()), rqt, bt.off, "bead", TOL[dtype], "rotated Q~^T w")
 
 
 def test_identity_rotation_and_single_products(setup):

@@ -2,7 +2,8 @@
 library's static device array, no allocation in the call.
 
 Checked against the context path (zq_build_tree + zq_build_transforms +
-zq_apply_Q, FP64) within the FP64 parity tolerance, on consecutive calls
+zq_apply_Q, FP64) and against the FP64 oracle directly, within the FP64
+parity tolerance (by norm and element by element), on consecutive calls
 that reuse the one static array with different body sizes.  The argument
 checks run without a GPU.
 """
@@ -11,6 +12,8 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
+from _parity import compare_elementwise
 from paper_1708_08427_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -73,9 +76,13 @@ def test_noalloc_matches_context_path_on_consecutive_calls():
         outs.append(out)
     torch.cuda.synchronize()
     for i, out in zip(order, outs):
-        n, _, _, _, _, ref = cases[i]
+        n, x, y, z, v, ref = cases[i]
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got)), n
         err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
         assert err <= TOL, (n, err)
+        # and against the oracle itself, element by element
+        B = oracle.Body(x.cpu().numpy(), y.cpu().numpy(), z.cpu().numpy())
+        want = B.apply_Q(W.interleave(*v.cpu().numpy()))
+        compare_elementwise(got, want, TOL, f"n = {n}")
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[5])
