@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / apply-only / e2e / CPU legs")
     ap.add_argument("--extras", default="all",
-                    help="comma-separated subset of the extra legs: build_other, fp64_step, apply, qgen, e2e, "
-                         "multirhs, bd_loop, cpu (default all)")
+                    help="comma-separated subset of the extra legs: error, build_other, fp64_step, apply, qgen, "
+                         "e2e, multirhs, bd_loop, cpu (default all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the per-kernel timing pass (the dominant kernel is then build_level)")
@@ -250,6 +250,15 @@ def kernel_work(name, census, N, R, m, es):
     return "hbm", 24 * N, "B"
 
 
+def sources_sha256(paths) -> str:
+    """sha256 over the concatenated contents of the files a kernel is built
+    from (paths relative to the repository root)."""
+    h = hashlib.sha256()
+    for rel in paths:
+        h.update((ROOT / rel).read_bytes())
+    return h.hexdigest()
+
+
 def traffic_for(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current source of the kernel (else None)."""
@@ -261,9 +270,7 @@ def traffic_for(kernel: str):
         e = d.get(kernel)
         if not e:
             return None
-        src = ROOT / e["source"]
-        h = hashlib.sha256(src.read_bytes()).hexdigest()
-        if h != e["sha256"]:
+        if sources_sha256(e.get("sources") or [e["source"]]) != e["sha256"]:
             return None
         return float(e["dram_bytes_per_launch"]) * float(e.get("scale", 1.0))
     except Exception:
@@ -428,15 +435,32 @@ def run_ours(args, world, rank, local):
         "phases_ms": phases,
     }
 
+    # the outputs of the last timed step against the FP64 oracle (rank 0):
+    # the error the metric is stated at
+    legs = set() if args.no_extras else (
+        {"error", "build_other", "fp64_step", "apply", "qgen", "e2e", "multirhs", "bd_loop", "cpu"}
+        if args.extras == "all" else set(args.extras.split(",")))
+    if rank == 0 and "error" in legs:
+        stream.synchronize()
+        out["config"]["stated_error"] = step_error(bt, v, w, qv, qtw)
+
+    # each sweep of the step against HBM (per-kernel events, algorithmic bytes)
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sweeps = {}
+    for nm in ("up_seg", "down_seg"):
+        if phases.get(nm):
+            byt = sweep_bytes(census, N, R, 4, gather=False)
+            sweeps[nm] = {"ms": phases[nm], "algorithmic_bytes": byt,
+                          "hbm_frac": byt / (phases[nm] / 1e3) / 1e9 / hbm_peak}
+    roofline["sweeps_in_step"] = sweeps
+
     if not args.no_graph:
         # the same step without the library's graph, captured by torch instead
         out["graph_replay"] = timed(args, step_direct, stream, flush, world, dev, N, graph=True)
         out["direct_launches"] = timed(args, step_direct, stream, flush, world, dev, N, graph=False)
         # the library's graph without the kernel-timing event nodes of the timed steps
         out["library_graph_untimed"] = timed(args, step, stream, flush, world, dev, N, graph=False)
-    legs = set() if args.no_extras else (
-        {"build_other", "fp64_step", "apply", "qgen", "e2e", "multirhs", "bd_loop", "cpu"}
-        if args.extras == "all" else set(args.extras.split(",")))
     if "build_other" in legs:
         other = "fp64" if args.build == "dd" else "dd"
         ctx.set_build_arith(other)
@@ -459,7 +483,60 @@ def run_ours(args, world, rank, local):
     if rank == 0 and "cpu" in legs:
         out["cpu_baseline"] = cpu_baseline(bt, args.cpu_seconds)
     ctx.close()
+    # FP32 against the plain FP64 GPU form, in the kept part of the line
+    cmp = {"fp32_step_ms": ms_per_step}
+    if "fp64_step" in out:
+        cmp["fp64_sweeps_step_ms"] = out["fp64_step"]["ms_per_step"]
+        cmp["speedup_vs_fp64_sweeps"] = out["fp64_step"]["ms_per_step"] / ms_per_step
+    other = "fp64" if args.build == "dd" else "dd"
+    if f"build_{other}_step" in out:
+        cmp[f"build_{other}_step_ms"] = out[f"build_{other}_step"]["ms_per_step"]
+    if "apply" in out:
+        for nm in ("fp32", "fp32_tree_order", "fp64"):
+            cmp[f"apply_pair_{nm}_ms"] = out["apply"][nm]["ms_per_step"]
+            cmp[f"apply_pair_{nm}_hbm_frac"] = out["apply"][nm]["hbm_frac"]
+    out["config"]["fp32_vs_fp64_gpu"] = cmp
+    # a short summary as the line's last key (the end of the line is what
+    # log tails keep)
+    se = out["config"].get("stated_error", {})
+    out["summary"] = {"ms": round(ms_per_step, 4), "err_elem": se.get("worst_element"),
+                      "err_norm": se.get("worst_norm"),
+                      "fp64_ms": round(cmp["fp64_sweeps_step_ms"], 4) if "fp64_sweeps_step_ms" in cmp else None,
+                      "up_frac": round(sweeps["up_seg"]["hbm_frac"], 3) if "up_seg" in sweeps else None,
+                      "down_frac": round(sweeps["down_seg"]["hbm_frac"], 3) if "down_seg" in sweeps else None,
+                      "pair_tree_frac": round(cmp["apply_pair_fp32_tree_order_hbm_frac"], 3)
+                      if "apply_pair_fp32_tree_order_hbm_frac" in cmp else None}
     return out
+
+
+def step_error(bt, v, w, qv, qtw):
+    """Every output of the timed step (FP32 Q~v and Q~^T w of the whole
+    batch) against the FP64 oracle on the same (FP32-rounded) inputs: per
+    body the relative 2-norm error and the worst element error relative to
+    the body's largest |element|; the worst of each over all bodies."""
+    import oracle
+    from paper_1708_08427_gb300 import workloads as W
+
+    vr = v.double().cpu().numpy()
+    wr = w.double().cpu().numpy()
+    got_q = qv.double().cpu().numpy()
+    got_qt = W.interleave(*qtw.double().cpu().numpy())
+    t0 = time.perf_counter()
+    rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*vr), wr)
+    dt = time.perf_counter() - t0
+    worst = {"qv_norm": 0.0, "qv_element": 0.0, "qtw_norm": 0.0, "qtw_element": 0.0}
+    ro = 0
+    for j in range(bt.m):
+        o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
+        for key, g, r in (("qv", got_q[ro:ro + 3 * n - 6], rq[ro:ro + 3 * n - 6]),
+                          ("qtw", got_qt[3 * o:3 * (o + n)], rqt[3 * o:3 * (o + n)])):
+            worst[key + "_norm"] = max(worst[key + "_norm"], float(np.linalg.norm(g - r) / np.linalg.norm(r)))
+            worst[key + "_element"] = max(worst[key + "_element"], float(np.abs(g - r).max() / np.abs(r).max()))
+        ro += 3 * n - 6
+    return {"against": "FP64 oracle, every body of the timed batch (last timed step's outputs)",
+            "bodies": bt.m, "tolerance": 1e-5, **worst,
+            "worst_norm": max(worst["qv_norm"], worst["qtw_norm"]),
+            "worst_element": max(worst["qv_element"], worst["qtw_element"]), "oracle_s": dt}
 
 
 def fp64_step(args, ctx, bt, stream, flush, rng, world, dev):
@@ -802,40 +879,77 @@ def bd_loop(args, stream, flush, world, dev, rank, steps_in_graph=10, reuse=Fals
             for _ in range(steps_in_graph):
                 one_step()
         stream.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 3
-    ms = []
-    for _ in range(reps):
-        s0.record(stream)
+    def run_replay():
         with torch.cuda.stream(stream):
             if g is not None:
                 g.replay()
             else:
                 for _ in range(steps_in_graph):
                     one_step()
-        s1.record(stream)
-        stream.synchronize()
-        ms.append(s0.elapsed_time(s1))
+
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20  # 200 steps
+    s0.record(stream)
+    for _ in range(reps):
+        run_replay()
+    s1.record(stream)
+    stream.synchronize()
     ctx.sync()
-    t_step = max_over_ranks(world, sum(ms) / 1e3, dev) / (reps * steps_in_graph)
-    # projector error of the last step, in FP64
-    Pc = P - (torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, P) / n)[body]
-    fd = f.double().t()                                            # (N, 3)
-    Fsum = torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, fd)
-    Tsum = torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, torch.cross(Pc, fd, dim=1))
-    r2 = (Pc * Pc).sum(1)
-    J = torch.zeros((m, 3, 3), device=dev, dtype=torch.float64).index_add_(
-        0, body, r2[:, None, None] * torch.eye(3, device=dev, dtype=torch.float64) - Pc[:, :, None] * Pc[:, None, :])
-    om = torch.linalg.solve(J, Tsum)
-    Pf = (Fsum / n)[body] + torch.cross(om[body], Pc, dim=1)
-    err = float(((out.double().t() - (fd - Pf)).norm() / fd.norm()).item())
+    t_step = max_over_ranks(world, s0.elapsed_time(s1) / 1e3, dev) / (reps * steps_in_graph)
+
+    def projector_err():
+        """|Q~^T Q~ f - (f - Z^T (Z Z^T)^-1 Z f)| / |f| of the last step, FP64."""
+        Pc = P - (torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, P) / n)[body]
+        fd = f.double().t()                                            # (N, 3)
+        Fsum = torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, fd)
+        Tsum = torch.zeros((m, 3), device=dev, dtype=torch.float64).index_add_(0, body, torch.cross(Pc, fd, dim=1))
+        r2 = (Pc * Pc).sum(1)
+        J = torch.zeros((m, 3, 3), device=dev, dtype=torch.float64).index_add_(
+            0, body, r2[:, None, None] * torch.eye(3, device=dev, dtype=torch.float64)
+            - Pc[:, :, None] * Pc[:, None, :])
+        om = torch.linalg.solve(J, Tsum)
+        Pf = (Fsum / n)[body] + torch.cross(om[body], Pc, dim=1)
+        return float(((out.double().t() - (fd - Pf)).norm() / fd.norm()).item())
+
+    def oracle_spot(bodies):
+        """The same projector from the FP64 oracle's own tree and transforms
+        on the moved positions (Q~^T Q~ does not depend on the basis), for a
+        few bodies: worst relative error of the GPU's FP32 result."""
+        import oracle
+        from paper_1708_08427_gb300 import workloads as W
+
+        Ph = P.cpu().numpy()
+        fh = f.double().cpu().numpy()
+        oh = out.double().cpu().numpy()
+        worst = 0.0
+        for j in bodies:
+            a, b = j * n, (j + 1) * n
+            B = oracle.Body(Ph[a:b, 0].copy(), Ph[a:b, 1].copy(), Ph[a:b, 2].copy())
+            fj = W.interleave(*fh[:, a:b])
+            want = B.apply_QT(B.apply_Q(fj))
+            got = W.interleave(*oh[:, a:b])
+            worst = max(worst, float(np.linalg.norm(got - want) / np.linalg.norm(fj)))
+        return worst
+
+    # sampled steps after the timed ones: the last step of each of three
+    # more replays, checked in full (FP64 torch) and by the oracle on 8 bodies
+    errs, spots = [], []
+    rs = np.random.default_rng(77)
+    for _ in range(3):
+        run_replay()
+        stream.synchronize()
+        errs.append(projector_err())
+        if rank == 0:
+            spots.append(oracle_spot(sorted(rs.choice(m, 8, replace=False).tolist())))
     ctx.close()
     what = ("transforms kept, accumulated rotation applied to the bead vectors" if reuse
             else "transforms rebuilt")
     return {"workload": f"m=1000 shells x 1000 beads, tree kept, per step: rigid motion, {what}, "
                         "Q~^T(Q~ f) FP32", "steps_per_s": 1.0 / t_step, "ms_per_step": 1e3 * t_step,
             "beads_per_s": N / t_step, "graph": g is not None, "steps_timed": reps * steps_in_graph,
-            "projector_rel_err_fp32": err}
+            "projector_rel_err_fp32": max(errs), "projector_rel_err_sampled_steps": errs,
+            "oracle_spot_check_rel_err": spots,
+            "oracle_spot_check": "8 bodies per sampled step, the oracle's own Q~^T Q~ f on the moved positions"}
 
 
 # ------------------------------------------------------------ CPU oracle
