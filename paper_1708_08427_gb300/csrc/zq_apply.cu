@@ -27,6 +27,9 @@ namespace {
 
 constexpr int kSegThreads = 128;
 constexpr int kTopThreads = 256;
+// Bodies with at most this many top nodes: one warp each (k_*_top_warp);
+// more: one thread block each (k_*_top).
+constexpr int kWarpTop = 64;
 
 template <typename T>
 struct SweepArgs {
@@ -259,20 +262,20 @@ __device__ __forceinline__ void load_bead(const SweepArgs<T>& a, int32_t code, T
 }
 
 template <bool ROT, typename T>
-__device__ __forceinline__ void up_top_node(const SweepArgs<T>& a, int32_t p, bool root) {
+__device__ __forceinline__ void up_top_node(const SweepArgs<T>& a, int32_t p, bool root, int32_t j) {
   const int2 cc = a.pc[p];
   T X[6], Y[6], P[6];
   if (cc.x >= 0 && cc.y >= 0) {
     load6(a.xs + 6 * (int64_t)cc.x, X);
     load6(a.xs + 6 * (int64_t)cc.y, Y);
   } else {
-    const Rot<T> R = body_rot<ROT>(a, blockIdx.x);
+    const Rot<T> R = body_rot<ROT>(a, j);
     if (cc.x >= 0) load6(a.xs + 6 * (int64_t)cc.x, X); else load_bead(a, cc.x, X, R);
     if (cc.y >= 0) load6(a.xs + 6 * (int64_t)cc.y, Y); else load_bead(a, cc.y, Y, R);
   }
   up_dispatch(a, a.prw[p], a.proff[p], cc, X, Y, P);
   store6(a.xs + 6 * (int64_t)p, P);
-  if (root && a.root_out) store6(a.root_out + 6 * (int64_t)blockIdx.x, P);  // Q_Z v of body blockIdx.x
+  if (root && a.root_out) store6(a.root_out + 6 * (int64_t)j, P);  // Q_Z v of body j
 }
 
 // Body blockIdx.x's top nodes, height by height (sorted by height in
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
   __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
   const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
-  if (n == 0) return;
+  if (n <= kWarpTop) return;  // none, or few: k_up_top_warp
   const int32_t* list = a.topv + t0;
   const uint8_t* ph = a.ph;
   // the body's top records into L2 first (they are scattered among the
@@ -293,12 +296,59 @@ __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
   for (int h = S.lim[0]; h <= S.lim[1]; ++h) {
     if (sorted) {
       for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x)
-        up_top_node<ROT>(a, S.ids[k], h == S.lim[1]);
+        up_top_node<ROT>(a, S.ids[k], h == S.lim[1], j);
     } else {
       for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
-        if (ph[list[t]] == h) up_top_node<ROT>(a, list[t], h == S.lim[1]);
+        if (ph[list[t]] == h) up_top_node<ROT>(a, list[t], h == S.lim[1], j);
     }
     __syncthreads();
+  }
+}
+
+// Bodies with at most kWarpTop top nodes: one warp per body, lane l taking
+// the body's top nodes l and l + 32, height by height with a warp barrier
+// in between (a node's children are finished at lower heights; __syncwarp
+// orders the warp's global writes before the reads of the next height).
+// The records and the children's Info-sets are fetched into L2 first.
+template <typename T>
+struct TopPair {
+  int32_t p[2];
+  int h[2];
+  int hmin, hmax;
+};
+
+template <typename T>
+__device__ __forceinline__ bool warp_top_setup(const SweepArgs<T>& a, int32_t j, TopPair<T>& tp, bool down) {
+  const int lane = threadIdx.x & 31;
+  const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
+  if (n == 0 || n > kWarpTop) return false;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int32_t t = lane + 32 * e;
+    tp.p[e] = t < n ? a.topv[t0 + t] : -1;
+    tp.h[e] = tp.p[e] >= 0 ? (int)a.ph[tp.p[e]] : -1;
+    if (tp.p[e] >= 0) {
+      prefetch_l2_line(a.rec + 4 * (int64_t)a.prw[tp.p[e]]);
+      if (down) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.in + a.proff[tp.p[e]]));
+    }
+  }
+  const int lo = min(tp.h[0] >= 0 ? tp.h[0] : kMaxHeight + 1, tp.h[1] >= 0 ? tp.h[1] : kMaxHeight + 1);
+  tp.hmin = __reduce_min_sync(0xffffffffu, lo);
+  tp.hmax = __reduce_max_sync(0xffffffffu, max(tp.h[0], tp.h[1]));
+  return true;
+}
+
+template <typename T, bool ROT>
+__global__ void __launch_bounds__(kTopThreads) k_up_top_warp(SweepArgs<T> a, int32_t m) {
+  const int32_t j = blockIdx.x * (kTopThreads / 32) + (threadIdx.x >> 5);
+  if (j >= m) return;
+  TopPair<T> tp;
+  if (!warp_top_setup(a, j, tp, false)) return;
+  for (int h = tp.hmin; h <= tp.hmax; ++h) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      if (tp.h[e] == h) up_top_node<ROT>(a, tp.p[e], h == tp.hmax, j);
+    __syncwarp();
   }
 }
 
@@ -325,12 +375,12 @@ __device__ __forceinline__ void store_bead(const SweepArgs<T>& a, int32_t code, 
 }
 
 template <bool ROT, typename T>
-__device__ __forceinline__ void down_top_node(const SweepArgs<T>& a, int32_t p, bool root) {
+__device__ __forceinline__ void down_top_node(const SweepArgs<T>& a, int32_t p, bool root, int32_t j) {
   const int2 cc = a.pc[p];
   T Lp[6], Lx[6], Ly[6];
   if (root) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) Lp[k] = a.root_in ? a.root_in[6 * (int64_t)blockIdx.x + k] : T(0);
+    for (int k = 0; k < 6; ++k) Lp[k] = a.root_in ? a.root_in[6 * (int64_t)j + k] : T(0);
   } else {
     load6(a.xs + 6 * (int64_t)p, Lp);
   }
@@ -339,7 +389,7 @@ __device__ __forceinline__ void down_top_node(const SweepArgs<T>& a, int32_t p, 
     store6(a.xs + 6 * (int64_t)cc.x, Lx);
     store6(a.xs + 6 * (int64_t)cc.y, Ly);
   } else {
-    const Rot<T> R = body_rot<ROT>(a, blockIdx.x);
+    const Rot<T> R = body_rot<ROT>(a, j);
     if (cc.x >= 0) store6(a.xs + 6 * (int64_t)cc.x, Lx); else store_bead(a, cc.x, Lx, R);
     if (cc.y >= 0) store6(a.xs + 6 * (int64_t)cc.y, Ly); else store_bead(a, cc.y, Ly, R);
   }
@@ -353,7 +403,7 @@ __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
   __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
   const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
-  if (n == 0) return;
+  if (n <= kWarpTop) return;  // none, or few: k_down_top_warp
   const int32_t* list = a.topv + t0;
   const uint8_t* ph = a.ph;
   // the body's top records and residue coefficients into L2 first (they
@@ -368,12 +418,26 @@ __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
   for (int h = hmax; h >= S.lim[0]; --h) {
     if (sorted) {
       for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x)
-        down_top_node<ROT>(a, S.ids[k], h == hmax);
+        down_top_node<ROT>(a, S.ids[k], h == hmax, j);
     } else {
       for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
-        if (ph[list[t]] == h) down_top_node<ROT>(a, list[t], h == hmax);
+        if (ph[list[t]] == h) down_top_node<ROT>(a, list[t], h == hmax, j);
     }
     __syncthreads();
+  }
+}
+
+template <typename T, bool ROT>
+__global__ void __launch_bounds__(kTopThreads) k_down_top_warp(SweepArgs<T> a, int32_t m) {
+  const int32_t j = blockIdx.x * (kTopThreads / 32) + (threadIdx.x >> 5);
+  if (j >= m) return;
+  TopPair<T> tp;
+  if (!warp_top_setup(a, j, tp, true)) return;
+  for (int h = tp.hmax; h >= tp.hmin; --h) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      if (tp.h[e] == h) down_top_node<ROT>(a, tp.p[e], h == tp.hmax, j);
+    __syncwarp();
   }
 }
 
@@ -664,9 +728,14 @@ zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out, T* root_out, c
   if (rot) k_up_seg<T, true><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
   else k_up_seg<T, false><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
   time_end(c, "up_seg");
+  const unsigned wblocks = (unsigned)((c.m + kTopThreads / 32 - 1) / (kTopThreads / 32));
   time_begin(c, "up_top");
+  if (rot) k_up_top_warp<T, true><<<wblocks, kTopThreads, 0, c.stream>>>(a, (int32_t)c.m);
+  else k_up_top_warp<T, false><<<wblocks, kTopThreads, 0, c.stream>>>(a, (int32_t)c.m);
+  time_begin(c, "up_top_block");
   if (rot) k_up_top<T, true><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
   else k_up_top<T, false><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  time_end(c, "up_top_block");
   time_end(c, "up_top");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
@@ -677,9 +746,14 @@ zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out, const T* roo
   SweepArgs<T> a = make_args<T>(c, rec, xs, w, out);
   a.root_in = root_in;
   a.rot = rot;
+  const unsigned wblocks = (unsigned)((c.m + kTopThreads / 32 - 1) / (kTopThreads / 32));
   time_begin(c, "down_top");
+  if (rot) k_down_top_warp<T, true><<<wblocks, kTopThreads, 0, c.stream>>>(a, (int32_t)c.m);
+  else k_down_top_warp<T, false><<<wblocks, kTopThreads, 0, c.stream>>>(a, (int32_t)c.m);
+  time_begin(c, "down_top_block");
   if (rot) k_down_top<T, true><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
   else k_down_top<T, false><<<(unsigned)c.m, kTopThreads, 0, c.stream>>>(a);
+  time_end(c, "down_top_block");
   time_end(c, "down_top");
   time_begin(c, "down_seg");
   if (rot) k_down_seg<T, true><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
