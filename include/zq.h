@@ -287,6 +287,25 @@ zq_status zq_time_kernel(zq_ctx *ctx, const char *name, void *start_event, void 
 typedef enum { ZQ_BUILD_DD = 0, ZQ_BUILD_FP64 = 1 } zq_build_arith;
 zq_status zq_set_build_arith(zq_ctx *ctx, zq_build_arith arith);
 
+/* Schedule of zq_pipeline's step after the tree.  Bodies are independent
+ * (Q~ is block diagonal over the bodies, Sec. 1), so the node transforms
+ * (Sec. 3) and both sweeps (Algorithms 2 and 3) of one body need nothing
+ * from any other body.
+ *   ZQ_STEP_LEVELS (default): the transforms level by level over all bodies
+ *     (one launch per height up to the level cut, then one block or warp
+ *     per body), then the sweeps on segments of at most 512 beads.
+ *   ZQ_STEP_FUSED: one persistent launch; a thread block takes the next
+ *     body from a queue ordered by bead count (largest first) and runs its
+ *     transforms with Q~ v, then Q~^T w, height by height.  Used when every
+ *     body has at most 8192 beads (else the step falls back to
+ *     ZQ_STEP_LEVELS).  The transform arithmetic and the node steps are the
+ *     same, so both schedules give the same bits.  The records are stored
+ *     in another layout: after a fused step the separate products
+ *     (zq_apply_Q, ...) return ZQ_ESTATE until zq_build_transforms runs.
+ * Performance only; takes effect at the next zq_pipeline call. */
+typedef enum { ZQ_STEP_LEVELS = 0, ZQ_STEP_FUSED = 1 } zq_step_schedule;
+zq_status zq_set_step_schedule(zq_ctx *ctx, zq_step_schedule schedule);
+
 /* Order of the bead vectors of every product call that follows (inputs of
  * Q~, outputs of Q~^T, in every precision and form, and of zq_pipeline).
  * ZQ_ORDER_CALLER (default): bead i is the caller's bead i.  ZQ_ORDER_TREE:

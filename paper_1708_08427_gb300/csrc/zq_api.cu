@@ -26,7 +26,7 @@ zq_status grow(T** p, int64_t count) {
 }
 
 void free_all(Ctx& c) {
-  void* ps[] = {c.off, c.small_d, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
+  void* ps[] = {c.off, c.small_d, c.lpt, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
                 c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage, c.ord,
@@ -67,6 +67,7 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     const int64_t nodes = N;  // >= N - m
     ZQ_TRY(grow(&c.off, m + 1));
     ZQ_TRY(grow(&c.small_d, m));
+    ZQ_TRY(grow(&c.lpt, m));
     ZQ_TRY(grow(&c.bead_body, N));
     ZQ_TRY(grow(&c.aabb, 6 * m));
     ZQ_TRY(grow(&c.body_scale, 3 * m));
@@ -189,8 +190,11 @@ zq_status zq_destroy(zq_ctx* ctx) {
   return ZQ_OK;
 }
 
-zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, const double* x,
-                                const double* y, const double* z, int32_t level_cut) {
+// The tree of m bodies; with schedules, also the segment and bucket
+// schedules of the level build and the separate sweeps (the fused step of
+// zq_pipeline needs neither; zq_build_transforms makes them when missing).
+static zq_status build_tree_impl(zq_ctx* ctx, int64_t m, const int64_t* off, const double* x, const double* y,
+                                 const double* z, int32_t level_cut, bool schedules) {
   if (!ctx || !off || !x || !y || !z || m < 1) return ZQ_EINVAL;
   if (level_cut == 0) level_cut = zq::kDefaultCut;
   if (level_cut < 1 || level_cut > zq::kMaxCut) return ZQ_EINVAL;
@@ -211,7 +215,7 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
   if (c.have_tree && m == c.m && level_cut == c.cut &&
       std::equal(off, off + m + 1, c.off_h.begin())) {
     c.have_xform = false;
-    ZQ_TRY(zq::launch_tree(c, x, y, z));
+    ZQ_TRY(zq::launch_tree(c, x, y, z, schedules));
     return ZQ_OK;
   }
   const int64_t hist_words = zq::sort_hist_words(max_big);
@@ -244,17 +248,28 @@ zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, cons
       c.small_bodies.insert(c.small_bodies.end(), cls[k].begin(), cls[k].end());
     }
     c.small_class_start[4] = (int)c.small_bodies.size();
+    // the fused step's queue: largest bodies first (ties by id)
+    c.lpt_h.resize((size_t)m);
+    for (int64_t j = 0; j < m; ++j) c.lpt_h[(size_t)j] = (int32_t)j;
+    std::stable_sort(c.lpt_h.begin(), c.lpt_h.end(),
+                     [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
   }
   ZQ_CUDA_TRY(cudaMemcpyAsync(c.off, off, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
   if (!c.small_bodies.empty())
     ZQ_CUDA_TRY(cudaMemcpyAsync(c.small_d, c.small_bodies.data(), c.small_bodies.size() * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, c.stream));
+  ZQ_CUDA_TRY(cudaMemcpyAsync(c.lpt, c.lpt_h.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
   // the host vectors are read by the copies above: keep them alive until then
   ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
   ZQ_TRY(zq::launch_bead_body(c));
-  ZQ_TRY(zq::launch_tree(c, x, y, z));
+  ZQ_TRY(zq::launch_tree(c, x, y, z, schedules));
   c.have_tree = true;
   return ZQ_OK;
+}
+
+zq_status zq_build_tree_batched(zq_ctx* ctx, int64_t m, const int64_t* off, const double* x,
+                                const double* y, const double* z, int32_t level_cut) {
+  return build_tree_impl(ctx, m, off, x, y, z, level_cut, true);
 }
 
 zq_status zq_build_tree(zq_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
@@ -269,6 +284,7 @@ zq_status zq_build_transforms(zq_ctx* ctx, const double* x, const double* y, con
   c.time_started = false;
   if (!c.have_tree) return ZQ_ESTATE;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
+  if (!c.have_sched) ZQ_TRY(zq::launch_schedules(c));  // the tree came from a fused step
   ZQ_TRY(zq::launch_build(c, x, y, z, 3));
   c.have_xform = true;
   c.have64 = c.have32 = true;
@@ -445,7 +461,14 @@ static int64_t pipe_order_bytes(int64_t N, size_t es) {
 }
 
 static bool pipe_reorders(const Ctx& c, const void* v, const void* w) {
-  return kPipeOrder > 0 && v && w && !c.tree_order;
+  return kPipeOrder > 0 && v && w && !c.tree_order && !c.fused_step;
+}
+
+// Every body small enough for the fused step (one thread block per body).
+static bool bodies_fit_fused(int64_t m, const int64_t* off) {
+  for (int64_t j = 0; j < m; ++j)
+    if (off[j + 1] - off[j] > zq::kSmallSortMax) return false;
+  return true;
 }
 
 static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, const double* x,
@@ -513,7 +536,21 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     dqv = qv ? sqv : nullptr;
     dqtw = qtw ? sqtw : nullptr;
   }
-  if (!keep) ZQ_TRY(zq_build_tree_batched(ctx, m, off, dx, dy, dz, level_cut));
+  const bool fused = c.fused_step && bodies_fit_fused(m, off);
+  if (!keep) ZQ_TRY(build_tree_impl(ctx, m, off, dx, dy, dz, level_cut, !fused));
+  if (fused) {
+    // transforms and both products of every body in one launch; the
+    // separate products need zq_build_transforms afterwards (other layout)
+    if (host) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[3], 0));  // the vectors are in
+    ZQ_TRY(zq::launch_fused_step(c, prec, dx, dy, dz, dv, dqv, dw, dqtw));
+    c.have_xform = false;
+    c.have64 = c.have32 = false;
+    if (host) {
+      if (qv) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));
+      if (qtw) ZQ_CUDA_TRY(cudaMemcpyAsync(qtw, dqtw, 3 * N * es, cudaMemcpyDeviceToHost, c.stream));
+    }
+    return ZQ_OK;
+  }
   // v into the tree's order on a side stream, next to the transform build
   // (it needs the tree's perm and, from host buffers, the copied v)
   char* vt = reorder ? static_cast<char*>(c.ord) : nullptr;
@@ -609,6 +646,14 @@ zq_status zq_time_kernel(zq_ctx* ctx, const char* name, void* start_event, void*
 zq_status zq_set_vector_order(zq_ctx* ctx, zq_vector_order order) {
   if (!ctx || (order != ZQ_ORDER_CALLER && order != ZQ_ORDER_TREE)) return ZQ_EINVAL;
   ctx->c.tree_order = order == ZQ_ORDER_TREE;
+  return ZQ_OK;
+}
+
+zq_status zq_set_step_schedule(zq_ctx* ctx, zq_step_schedule schedule) {
+  if (!ctx || (schedule != ZQ_STEP_LEVELS && schedule != ZQ_STEP_FUSED)) return ZQ_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.fused_step != (schedule == ZQ_STEP_FUSED)) ++c.plan_gen;  // a captured step is stale
+  c.fused_step = schedule == ZQ_STEP_FUSED;
   return ZQ_OK;
 }
 
@@ -838,7 +883,8 @@ zq_status zq_pipeline(zq_ctx* ctx, zq_prec prec, int64_t m, const int64_t* off, 
   if (!c.stream || !off || m < 1) return pipeline_body(ctx, prec, m, off, x, y, z, v, qv, w, qtw, level_cut, flags);
   const int32_t cut = level_cut == 0 ? zq::kDefaultCut : level_cut;
   std::vector<uintptr_t> key = {(uintptr_t)prec, (uintptr_t)m, (uintptr_t)cut, (uintptr_t)flags,
-                                (uintptr_t)c.build_dd, (uintptr_t)c.tree_order, (uintptr_t)x, (uintptr_t)y,
+                                (uintptr_t)c.build_dd, (uintptr_t)c.tree_order, (uintptr_t)c.fused_step,
+                                (uintptr_t)x, (uintptr_t)y,
                                 (uintptr_t)z, (uintptr_t)v,
                                 (uintptr_t)qv, (uintptr_t)w, (uintptr_t)qtw};
   key.insert(key.end(), off, off + m + 1);

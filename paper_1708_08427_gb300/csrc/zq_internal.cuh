@@ -78,8 +78,11 @@ struct Ctx {
   bool have_tree = false, have_xform = false, have64 = false, have32 = false;
   bool build_dd = true;    // build the transforms in double-single (else native FP64)
   bool tree_order = false; // bead vectors of the products are in tree (sorted-position) order
+  bool fused_step = false; // zq_pipeline runs the step after the tree as one per-body launch
+  bool have_sched = false; // the segment and bucket schedules of the current tree exist
   bool st_is_dd = false;   // representation of st64 written by the last build
   std::vector<int64_t> off_h;
+  std::vector<int32_t> lpt_h;         // host copy of lpt (kept alive for its upload)
   std::vector<int32_t> small_bodies;  // n_j <= kSmallSortMax, grouped by size class
   std::vector<int32_t> big_bodies;    // n_j > kSmallSortMax (device-wide tree kernels)
   int small_class_start[5] = {0, 0, 0, 0, 0};
@@ -87,6 +90,7 @@ struct Ctx {
   // device buffers (bodies)
   int64_t* off = nullptr;        // [m+1]
   int32_t* small_d = nullptr;    // [m] ids of small bodies
+  int32_t* lpt = nullptr;        // [m] body ids by bead count, largest first (fused step queue)
   int32_t* bead_body = nullptr;  // [N] body of each bead / sorted position
   uint64_t* aabb = nullptr;      // [m * 6] ordered-int encoded lo[3], hi[3]
   double* body_scale = nullptr;  // [m * 3] 1 / (hi - lo) per axis (0 if hi == lo)
@@ -324,7 +328,10 @@ __device__ inline double ord_decode(unsigned long long u) {
 
 // ---------------------------------------------------- launchers (per TU)
 // zq_tree.cu
-zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z);
+// the tree; with schedules, also the segment and bucket schedules that the
+// level build and the separate sweeps need (launch_schedules)
+zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z, bool schedules = true);
+zq_status launch_schedules(Ctx& c);
 zq_status launch_bead_body(Ctx& c);
 // zq_smalltree.cu
 int small_tree_class(int64_t n);
@@ -349,6 +356,11 @@ zq_status launch_segments(Ctx& c);
 // zq_build.cu
 // which: bit 0 = FP64 records, bit 1 = FP32 records
 zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which);
+// zq_fused.cu: transforms, Q~ v and Q~^T w of every body in one launch
+// (bodies of at most kSmallSortMax beads; records in the fused layout)
+bool fused_step_possible(const Ctx& c);
+zq_status launch_fused_step(Ctx& c, zq_prec prec, const double* x, const double* y, const double* z,
+                            const void* v, void* qv, const void* w, void* qtw);
 // zq_order.cu: bead planes (3 x N) to and from the tree's sorted-position
 // order (entry s = bead perm[s]), on c.stream
 zq_status launch_to_tree(Ctx& c, zq_prec prec, const void* v, void* vt);

@@ -436,7 +436,7 @@ zq_status launch_bead_body(Ctx& c) {
   return ZQ_OK;
 }
 
-zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z) {
+zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z, bool schedules) {
   cudaStream_t s = c.stream;
   unsigned long long* lo = reinterpret_cast<unsigned long long*>(c.aabb);
   unsigned long long* hi = lo + 3 * c.m;
@@ -477,6 +477,14 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
     st = launch_exclusive_scan(c, c.roff, c.roff, c.nodes, c.scan_tmp, nullptr);
     if (st != ZQ_OK) return st;
   }
+  c.have_sched = false;
+  if (!schedules) return ZQ_OK;
+  return launch_schedules(c);
+}
+
+zq_status launch_schedules(Ctx& c) {
+  cudaStream_t s = c.stream;
+  zq_status st = ZQ_OK;
   // The sweep schedule (segments) and the build schedule (buckets) only
   // read the tree: the former runs on a side stream next to the latter,
   // joined before the slot data, which needs both.
@@ -516,6 +524,7 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z)
   k_slot_records<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.pos_of, c.prw, c.srw);
   time_end(c, "schedule");
   ZQ_CUDA_TRY(cudaGetLastError());
+  c.have_sched = true;
   return ZQ_OK;
 }
 

@@ -22,6 +22,7 @@ ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE 
 ZQ_FP64, ZQ_FP32, ZQ_BF16 = 0, 1, 2
 ZQ_HOST_BUFFERS, ZQ_KEEP_TREE, ZQ_GRAPH = 1, 2, 4
 ZQ_BUILD_DD, ZQ_BUILD_FP64 = 0, 1
+ZQ_STEP_LEVELS, ZQ_STEP_FUSED = 0, 1
 ZQ_ORDER_CALLER, ZQ_ORDER_TREE = 0, 1
 ZQ_ROWS_INORDER, ZQ_ROWS_PREORDER = 0, 1
 
@@ -80,6 +81,8 @@ def _lib() -> ctypes.CDLL:
         L.zq_time_kernel.argtypes = [_vp, ctypes.c_char_p, _vp, _vp]
         L.zq_set_build_arith.restype = ctypes.c_int
         L.zq_set_build_arith.argtypes = [_vp, ctypes.c_int]
+        L.zq_set_step_schedule.restype = ctypes.c_int
+        L.zq_set_step_schedule.argtypes = [_vp, ctypes.c_int]
         L.zq_set_vector_order.restype = ctypes.c_int
         L.zq_set_vector_order.argtypes = [_vp, ctypes.c_int]
         L.zq_launch_count.restype = ctypes.c_int
@@ -373,6 +376,11 @@ class Context:
         """'caller' (default) or 'tree': bead vectors of the products in the
         tree's sorted-position order (entry s = caller's bead perm[s])."""
         _check(_lib().zq_set_vector_order(self._h, {"caller": ZQ_ORDER_CALLER, "tree": ZQ_ORDER_TREE}[order]), "zq_set_vector_order")
+
+    def set_step_schedule(self, schedule: str):
+        """zq_set_step_schedule: "levels" or "fused" (include/zq.h)."""
+        code = {"levels": ZQ_STEP_LEVELS, "fused": ZQ_STEP_FUSED}[schedule]
+        _check(_lib().zq_set_step_schedule(self._h, code), "zq_set_step_schedule")
 
     def set_build_arith(self, arith: str):
         """'dd' (double-single on the FP32 pipes, default) or 'fp64'."""
