@@ -57,6 +57,11 @@ def parse():
                     help="bodies of the shell workload (smaller values: profiling captures)")
     ap.add_argument("--cut", type=int, default=0,
                     help="level cut (performance only); 0: chosen by the autotuner on this workload")
+    ap.add_argument("--schedule", choices=["auto", "levels", "fused"], default="auto",
+                    help="step schedule after the tree (performance only): level launches, the fused per-body "
+                         "launch, or auto (the autotuner times both, with every level cut)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of the autotuner's picks per workload shape (read and updated)")
     ap.add_argument("--build", choices=["dd", "fp64"], default="dd",
                     help="node-transform arithmetic: double-single on FP32 pipes or native FP64")
     ap.add_argument("--no-graph", action="store_true")
@@ -238,7 +243,7 @@ def sweep_bytes(census, N, R, es=4, gather=True) -> int:
 
 def kernel_work(name, census, N, R, m, es):
     """(bound, algorithmic amount per launch, unit)."""
-    if name == "build":  # every node's transform
+    if name in ("build", "fused"):  # every node's transform (the fused step also runs both sweeps)
         return "alu", sum(census[k] * build_flops(k) for k in census), "flop"
     if name in ("up_seg", "down_seg"):  # the step's sweeps see tree-ordered planes (no gather)
         return "hbm", sweep_bytes(census, N, R, es, gather=False), "B"
@@ -302,11 +307,21 @@ def run_ours(args, world, rank, local):
     _XYZ[id(bt)] = (x, y, z)
     ctx = zq.Context(local, stream=stream)
     ctx.set_build_arith(args.build)
-    tuned = None
-    if args.cut == 0:  # the level schedule chosen by timing the step itself
-        from paper_1708_08427_gb300.tune import tune_level_cut
+    tuned, from_cache = None, False
+    if args.schedule == "auto" or args.cut == 0:  # chosen by timing the step itself
+        from paper_1708_08427_gb300.tune import CANDIDATES, tune_level_cut, tune_step
 
-        args.cut, tuned = tune_level_cut(ctx, bt.off, x, y, z, v, qv, w, qtw, graph=not args.no_graph)
+        if args.schedule == "levels":
+            args.cut, tuned = tune_level_cut(ctx, bt.off, x, y, z, v, qv, w, qtw, graph=not args.no_graph)
+        elif args.schedule == "fused":
+            args.cut = args.cut or 15
+        else:
+            cands = CANDIDATES if args.cut == 0 else (("levels", args.cut), ("fused", 0))
+            (args.schedule, cut), tuned, from_cache = tune_step(
+                ctx, bt.off, x, y, z, v, qv, w, qtw, candidates=cands, graph=not args.no_graph,
+                cache=args.tune_cache, key_extra={"arith": args.build})
+            args.cut = cut or args.cut or 15
+    ctx.set_step_schedule(args.schedule)
 
     # the step is one zq_pipeline call; with graphs on, the library captures
     # it once and replays it (ZQ_GRAPH), the timing events included
@@ -322,9 +337,11 @@ def run_ours(args, world, rank, local):
     census = node_census(ctx)
 
     # --- per-kernel time of one step (measurement hook), picks the dominant kernel
-    names = ["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "segments",
-             "schedule", "build", "build_level", "build_tail", "to_tree", "up_seg", "up_top", "down_top",
-             "down_seg", "from_tree"]
+    names = (["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "fused"]
+             if args.schedule == "fused" else
+             ["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "segments",
+              "schedule", "build", "build_level", "build_tail", "to_tree", "up_seg", "up_top", "down_top",
+              "down_seg", "from_tree"])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e1.record(stream)
@@ -346,8 +363,8 @@ def run_ours(args, world, rank, local):
         phases[nm] = tot / reps
     # candidates: the transform build as a whole (Case I kernel, level
     # launches and the part above the cut), each sweep, the tree, the schedules
-    dominant = max(("build", "up_seg", "down_seg", "small_tree", "schedule", "segments"),
-                   key=lambda k: phases.get(k, 0.0)) if phases else "build"
+    dominant = max(("build", "up_seg", "down_seg", "small_tree", "schedule", "segments", "fused"),
+                   key=lambda k: phases.get(k, 0.0)) if phases else ("fused" if args.schedule == "fused" else "build")
 
     # --- the dominant kernel is bracketed by events in every timed step
     # (external event records: in a replayed step they are graph nodes)
@@ -424,8 +441,8 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 sweeps; transforms " + ("double-single (2 x f32, ~48-bit)" if args.build == "dd" else "f64"),
         "data": "synthetic (seeded numpy generators; no dataset)",
-        "config": {"workload": desc, "m": m, "N": N, "residues": R, "level_cut": args.cut,
-                   "level_cut_tuning_ms": tuned,
+        "config": {"workload": desc, "m": m, "N": N, "residues": R, "schedule": args.schedule,
+                   "level_cut": args.cut, "schedule_tuning_ms": tuned, "tuning_from_cache": from_cache,
                    "graph": not args.no_graph, "prec": "fp32", "build": args.build,
                    "step": ("tree + transforms (" + ("double-single" if args.build == "dd" else "FP64")
                             + ") + Q~v + Q~^T w, one C-ABI call (zq_pipeline)"),

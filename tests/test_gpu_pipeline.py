@@ -179,6 +179,32 @@ def test_level_cut_tuner_picks_a_candidate():
     ctx.close()
 
 
+def test_step_tuner_picks_a_candidate_and_caches_it(tmp_path):
+    """tune_step times the level schedule at two cuts and the fused step,
+    leaves the context on the fastest schedule, writes the pick to the cache
+    and takes it from there on the next call."""
+    from paper_1708_08427_gb300.tune import tune_step
+
+    zq = _zq()
+    dev = _dev()
+    bt = W.shell_batch(m=16, nmin=30, nmax=2000, seed=23)
+    x, y, z = (torch.from_numpy(a.copy()).to(dev) for a in (bt.x, bt.y, bt.z))
+    v = torch.zeros((3, bt.N), device=dev)
+    w = torch.zeros(bt.n_residues, device=dev)
+    qv = torch.empty(bt.n_residues, device=dev)
+    qtw = torch.empty((3, bt.N), device=dev)
+    ctx = zq.Context(0)
+    cands = (("levels", 4), ("levels", 15), ("fused", 0))
+    cache = tmp_path / "picks.json"
+    pick, times, cached = tune_step(ctx, bt.off, x, y, z, v, qv, w, qtw, candidates=cands, reps=2, warmup=1,
+                                    cache=cache)
+    assert not cached and pick in [(s, c) for s, c in cands] and len(times) == 3
+    assert cache.exists()
+    pick2, times2, cached2 = tune_step(ctx, bt.off, x, y, z, v, qv, w, qtw, candidates=cands, cache=cache)
+    assert cached2 and pick2 == pick and times2 == times
+    ctx.close()
+
+
 @pytest.mark.parametrize("host", [False, True])
 def test_pipeline_graph_replay_matches_direct(host):
     """ZQ_GRAPH: the first call plans and runs directly, the second captures,
