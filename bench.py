@@ -752,9 +752,11 @@ def e2e(args, ctx, bt, stream, world, dev):
 def multirhs(args, stream, flush, world, dev, rank, k=64):
     """Block form on 500 shells with n_j uniform in [500, 2000] and k = 64
     right-hand sides: Q~V + Q~^T W with the transforms built, in FP32, BF16
-    (bfloat16 storage, FP32 arithmetic) and FP64, each with its error against
-    the FP64 oracle on sampled columns (rank 0), and FP32 column by column
-    through the single-vector path for comparison.  Unit: bead-columns/s."""
+    (bfloat16 storage, FP32 arithmetic), FP64, and on the tensor cores (TF32
+    and bfloat16 operands, FP32 accumulation, one warp-level mma per node
+    and 8-column tile), each with its error against the FP64 oracle on
+    sampled columns (rank 0), and FP32 column by column through the
+    single-vector path for comparison.  Unit: bead-columns/s."""
     import torch
 
     import oracle
@@ -775,8 +777,9 @@ def multirhs(args, stream, flush, world, dev, rank, k=64):
     W64 = torch.from_numpy(rng.standard_normal((R, k))).to(dev)
     res = {"workload": f"m=500 shells, n_j uniform [500,2000], N={N}, k={k}", "unit": "bead-columns/s"}
     cols = [0, k - 1]
-    for name, dt, es, rs in (("fp32", torch.float32, 4, 4), ("bf16", torch.bfloat16, 2, 4),
-                             ("fp64", torch.float64, 8, 8)):
+    for name, dt, es, rs, tc in (("fp32", torch.float32, 4, 4, False), ("bf16", torch.bfloat16, 2, 4, False),
+                                 ("fp64", torch.float64, 8, 8, False), ("tf32_tensor_core", torch.float32, 4, 4, True),
+                                 ("bf16_tensor_core", torch.bfloat16, 2, 4, True)):
         ctx.reserve_block(k, dt)
         V, Wr = V64.to(dt), W64.to(dt)
         oq = torch.empty((R, k), dtype=dt, device=dev)
@@ -784,8 +787,8 @@ def multirhs(args, stream, flush, world, dev, rank, k=64):
         stream.synchronize()
 
         def fn():
-            ctx.apply_Q_block(V, oq)
-            ctx.apply_QT_block(Wr, oqt)
+            ctx.apply_Q_block(V, oq, tensor_cores=tc)
+            ctx.apply_QT_block(Wr, oqt, tensor_cores=tc)
 
         r = timed(args, fn, stream, flush, world, dev, N * k, graph=not args.no_graph)
         r["unit"] = "bead-columns/s"

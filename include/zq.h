@@ -76,7 +76,14 @@ typedef enum {
 
 /* Arithmetic and storage of an apply.  ZQ_BF16: bfloat16 vectors with
  * FP32 arithmetic and the FP32 transforms (block form only). */
-typedef enum { ZQ_FP64 = 0, ZQ_FP32 = 1, ZQ_BF16 = 2 } zq_prec;
+/* Arithmetic of a product.  ZQ_FP64, ZQ_FP32: the vectors and the
+ * arithmetic in that type.  The block form (k right-hand sides) also takes
+ * ZQ_BF16 (bfloat16 storage, FP32 arithmetic), and two tensor-core forms in
+ * which each node's transform is applied to the k columns as a small
+ * matrix product on the tensor cores with FP32 accumulation: ZQ_TF32 (float
+ * storage, product operands rounded to TF32, a 10-bit significand) and
+ * ZQ_BF16_TC (bfloat16 storage, operands in bfloat16). */
+typedef enum { ZQ_FP64 = 0, ZQ_FP32 = 1, ZQ_BF16 = 2, ZQ_TF32 = 3, ZQ_BF16_TC = 4 } zq_prec;
 
 /* Human-readable name of a status code (static storage). */
 const char *zq_status_string(zq_status s);
@@ -209,8 +216,16 @@ zq_status zq_apply_rotated(zq_ctx *ctx, zq_prec prec, const double *R, const voi
  * out[r*k + c] (r in the residue order above).  DEVICE memory.
  * prec: ZQ_FP32 (float), ZQ_BF16 (__nv_bfloat16 storage, FP32 arithmetic
  * and FP32 transforms; inputs and outputs rounded to bfloat16), ZQ_FP64
- * (double).  The transforms of the matching precision must have been built
- * (zq_build_transforms builds both), else ZQ_ESTATE.
+ * (double), ZQ_TF32 (float storage; per node, G (k_p x k_p, k_p <= 9) zero
+ * padded to 16 x 16 times the node's k_p x k block in tiles of 8 columns by
+ * warp-level mma.sync m16n8k8 with TF32 operands and FP32 accumulation),
+ * ZQ_BF16_TC (bfloat16 storage; the same with m16n8k16 bfloat16 operands).
+ * Each node's operands are rounded once (relative 2^-11 for TF32, 2^-8 for
+ * bfloat16); the rounding errors of the heights add up through the tree
+ * (orthogonal steps do not amplify them).  The transforms of the matching
+ * precision must have been built (zq_build_transforms builds both; the
+ * FP32 ones serve ZQ_FP32, ZQ_BF16, ZQ_TF32 and ZQ_BF16_TC), else
+ * ZQ_ESTATE.
  *
  * zq_reserve_block allocates the context's block scratch for up to k_max
  * columns (6 values per node and column, 4 or 8 bytes each) and must precede

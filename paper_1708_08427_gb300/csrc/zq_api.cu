@@ -350,7 +350,7 @@ zq_status zq_qgen(zq_ctx* ctx, zq_prec prec, int64_t* row_ptr, int32_t* col, voi
 
 zq_status zq_reserve_block(zq_ctx* ctx, zq_prec prec, int64_t k_max) {
   if (!ctx || k_max < 1) return ZQ_EINVAL;
-  if (prec != ZQ_FP32 && prec != ZQ_FP64 && prec != ZQ_BF16) return ZQ_EINVAL;
+  if (prec < ZQ_FP64 || prec > ZQ_BF16_TC) return ZQ_EINVAL;
   Ctx& c = ctx->c;
   if (!c.have_tree) return ZQ_ESTATE;
   ZQ_CUDA_TRY(cudaSetDevice(c.device));
@@ -371,7 +371,7 @@ zq_status zq_reserve_block(zq_ctx* ctx, zq_prec prec, int64_t k_max) {
 
 static zq_status apply_block(zq_ctx* ctx, bool up, zq_prec prec, int64_t k, const void* in, void* out) {
   if (!ctx || !in || !out || k < 1 || k > (1 << 20)) return ZQ_EINVAL;
-  if (prec != ZQ_FP32 && prec != ZQ_FP64 && prec != ZQ_BF16) return ZQ_EINVAL;
+  if (prec < ZQ_FP64 || prec > ZQ_BF16_TC) return ZQ_EINVAL;
   Ctx& c = ctx->c;
   c.time_started = false;
   if (!c.have_xform || !(prec == ZQ_FP64 ? c.have64 : c.have32)) return ZQ_ESTATE;

@@ -18,6 +18,8 @@
 // starts.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "zq_internal.cuh"
 #include "zq_node.cuh"
 
@@ -686,6 +688,339 @@ BlockArgs<TS, TC> make_block_args(const Ctx& c, int32_t k, const TC* rec, const 
   return a;
 }
 
+// ---------------------------------------- block form on tensor cores
+// The node transform meets a dense block of k columns: per node, the
+// product G U (up: U = [r_x?; r_y?; s], k_p x k) or G^T Z (down: Z =
+// [L_p(4:6); w_p]) is a small matrix product, run on the tensor cores with
+// warp-level mma.sync (one warp per node): G, zero-padded to 16 x 16, is
+// the A operand; U or Z, in tiles of 8 columns, the B operand; FP32
+// accumulation.  MMA = Tf32: operands rounded to TF32 (10-bit significand,
+// m16n8k8, two k-steps); MMA = Bf16: operands rounded to bfloat16 (8-bit
+// significand, m16n8k16).  The elementwise parts of the node step (t_p =
+// alpha t_x + beta t_y, s, and the Velocity-set combination) stay in FP32.
+// Fragment layouts (PTX ISA, mma.sync): g = lane / 4, t = lane % 4;
+// C/D (16 x 8): (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
+struct Tf32 {};
+struct Bf16 {};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// A fragments of the 16 x 16 matrix As (row-major, FP32 in shared memory).
+template <class MMA>
+struct AFrag {
+  uint32_t r[8];
+};
+
+template <class MMA>
+__device__ __forceinline__ void load_a(const float (*As)[16], AFrag<MMA>& f) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  if constexpr (std::is_same_v<MMA, Tf32>) {
+    // m16n8k8: a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4); k-step s adds 8 s
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      f.r[4 * ks + 0] = to_tf32(As[g][8 * ks + t]);
+      f.r[4 * ks + 1] = to_tf32(As[g + 8][8 * ks + t]);
+      f.r[4 * ks + 2] = to_tf32(As[g][8 * ks + t + 4]);
+      f.r[4 * ks + 3] = to_tf32(As[g + 8][8 * ks + t + 4]);
+    }
+  } else {
+    // m16n8k16: a0 (g, 2t..2t+1), a1 (g+8, 2t..), a2 (g, 2t+8..), a3 (g+8, 2t+8..)
+    f.r[0] = pack_bf16(As[g][2 * t], As[g][2 * t + 1]);
+    f.r[1] = pack_bf16(As[g + 8][2 * t], As[g + 8][2 * t + 1]);
+    f.r[2] = pack_bf16(As[g][2 * t + 8], As[g][2 * t + 9]);
+    f.r[3] = pack_bf16(As[g + 8][2 * t + 8], As[g + 8][2 * t + 9]);
+  }
+}
+
+// D = A B for B the 16 x 8 tile Bs (row-major, FP32 in shared memory).
+template <class MMA>
+__device__ __forceinline__ void mma_tile(const AFrag<MMA>& A, const float (*Bs)[8], float (&d)[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  d[0] = d[1] = d[2] = d[3] = 0.0f;
+  if constexpr (std::is_same_v<MMA, Tf32>) {
+    // b0 (t, g), b1 (t+4, g); k-step s adds 8 s to the row
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const uint32_t b0 = to_tf32(Bs[8 * ks + t][g]), b1 = to_tf32(Bs[8 * ks + t + 4][g]);
+      asm volatile(
+          "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};"
+          : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+          : "r"(A.r[4 * ks]), "r"(A.r[4 * ks + 1]), "r"(A.r[4 * ks + 2]), "r"(A.r[4 * ks + 3]), "r"(b0),
+            "r"(b1));
+    }
+  } else {
+    // b0 (2t..2t+1, g), b1 (2t+8..2t+9, g)
+    const uint32_t b0 = pack_bf16(Bs[2 * t][g], Bs[2 * t + 1][g]);
+    const uint32_t b1 = pack_bf16(Bs[2 * t + 8][g], Bs[2 * t + 9][g]);
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(A.r[0]), "r"(A.r[1]), "r"(A.r[2]), "r"(A.r[3]), "r"(b0), "r"(b1));
+  }
+}
+
+// Per-warp shared tiles: the node's G (or G^T), one 8-column tile of the B
+// operand, one of the product.
+struct TcTiles {
+  float A[16][16];
+  float B[16][8];
+  float C[16][8];
+};
+
+// G (transpose: G^T) of node record r (FP32, compact layout) into T.A,
+// zero-padded: lane j < k_p builds column j as G e_j.
+__device__ __forceinline__ void tc_form_g(const float* __restrict__ rec, int type, bool transpose, TcTiles& T) {
+  const int lane = threadIdx.x & 31;
+  const int kp = 3 + 3 * type;
+  if (lane < 16) {
+    float u[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) u[i] = (i == lane) ? 1.0f : 0.0f;
+    if (lane < kp) {
+      if (type == 0) {  // G row-major in words 2..10
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u[i] = __ldg(rec + 2 + 3 * i + lane);
+      } else if (type == 1) {
+        float r[16];
+        load_rec<float, 16>(rec, r);
+        g6(r, u, false);
+      } else {
+        float r[20];
+        load_rec<float, 20>(rec, r);
+        g9(r, u, false);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float gv = (lane < kp && i < kp) ? u[i < 9 ? i : 0] : 0.0f;
+      if (transpose) T.A[lane][i] = gv;  // G^T (lane, i) = G (i, lane)
+      else T.A[i][lane] = gv;
+    }
+  }
+  __syncwarp();
+}
+
+// Value i (0..2) of a child's Info-set part t (rows 0-2, or r: rows 3-5)
+// in column col; a leaf child's t is its bead vector.
+template <typename TS>
+__device__ __forceinline__ float tc_child(const BlockArgs<TS, float>& a, int32_t code, int row, int32_t col) {
+  if (code >= 0) return a.xk[((int64_t)code * 6 + row) * a.k + col];
+  const int64_t b = a.perm ? a.perm[leaf_pos(code)] : leaf_pos(code);
+  return to_c(a.in[((int64_t)row * a.N + b) * a.k + col]);
+}
+
+// Upward step of node p for all k columns, one warp (Algorithm 2 on a block):
+// t_p = alpha t_x + beta t_y, [r_p; eps_p] = G [r_x?; r_y?; beta t_x - alpha t_y].
+template <class MMA, typename TS>
+__device__ void tc_up_node(const BlockArgs<TS, float>& a, int64_t p, int2 cc, uint32_t rw, int32_t ro, TcTiles& T) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int type = (cc.x >= 0) + (cc.y >= 0), kp = 3 + 3 * type;
+  const float* rec = a.rec + 4 * (int64_t)rw;
+  tc_form_g(rec, type, false, T);
+  AFrag<MMA> A;
+  load_a<MMA>(T.A, A);
+  const float al = __ldg(rec), be = __ldg(rec + 1);
+  const int32_t ic = cc.x >= 0 ? cc.x : cc.y;  // the internal child of a k = 6 node
+  for (int32_t col0 = 0; col0 < a.k; col0 += 8) {
+    for (int e = lane; e < 128; e += 32) {
+      const int row = e >> 3, cl = e & 7;
+      const int32_t col = col0 + cl;
+      float val = 0.0f;
+      if (row < kp && col < a.k) {
+        const int sr = row - (kp - 3);  // row of s, or < 0
+        if (sr >= 0) val = be * tc_child(a, cc.x, sr, col) - al * tc_child(a, cc.y, sr, col);
+        else if (type == 2) val = tc_child(a, row < 3 ? cc.x : cc.y, 3 + row % 3, col);
+        else val = tc_child(a, ic, 3 + row, col);
+      }
+      T.B[row][cl] = val;
+    }
+    __syncwarp();
+    float d[4];
+    mma_tile<MMA>(A, T.B, d);
+    T.C[g][2 * t] = d[0];
+    T.C[g][2 * t + 1] = d[1];
+    T.C[g + 8][2 * t] = d[2];
+    T.C[g + 8][2 * t + 1] = d[3];
+    __syncwarp();
+    for (int e = lane; e < (kp + 3) * 8; e += 32) {
+      const int row = e >> 3, cl = e & 7;
+      const int32_t col = col0 + cl;
+      if (col >= a.k) continue;
+      if (row < 3) {
+        a.xk[((int64_t)p * 6 + 3 + row) * a.k + col] = T.C[row][cl];
+      } else if (row < kp) {
+        a.out[((int64_t)ro + row - 3) * a.k + col] = from_c<TS>(T.C[row][cl]);
+      } else {
+        const int i = row - kp;
+        a.xk[((int64_t)p * 6 + i) * a.k + col] = al * tc_child(a, cc.x, i, col) + be * tc_child(a, cc.y, i, col);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Downward step of node p for all k columns, one warp (Algorithm 3 on a
+// block): [a_x?; a_y?; sigma] = G^T [L_p(4:6); w_p],
+// L_x = [alpha L_p(1:3) + beta sigma; a_x], L_y = [beta L_p(1:3) - alpha sigma; a_y].
+template <class MMA, typename TS>
+__device__ void tc_down_node(const BlockArgs<TS, float>& a, int64_t p, int2 cc, uint32_t rw, int32_t ro, bool zero,
+                             TcTiles& T) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int type = (cc.x >= 0) + (cc.y >= 0), kp = 3 + 3 * type;
+  const float* rec = a.rec + 4 * (int64_t)rw;
+  tc_form_g(rec, type, true, T);
+  AFrag<MMA> A;
+  load_a<MMA>(T.A, A);
+  const float al = __ldg(rec), be = __ldg(rec + 1);
+  const float* Lp = a.xk + (int64_t)p * 6 * a.k;
+  for (int32_t col0 = 0; col0 < a.k; col0 += 8) {
+    for (int e = lane; e < 128; e += 32) {
+      const int row = e >> 3, cl = e & 7;
+      const int32_t col = col0 + cl;
+      float val = 0.0f;
+      if (row < kp && col < a.k) {
+        if (row < 3) val = zero ? 0.0f : Lp[(int64_t)(3 + row) * a.k + col];
+        else val = to_c(a.in[((int64_t)ro + row - 3) * a.k + col]);
+      }
+      T.B[row][cl] = val;
+    }
+    __syncwarp();
+    float d[4];
+    mma_tile<MMA>(A, T.B, d);
+    T.C[g][2 * t] = d[0];
+    T.C[g][2 * t + 1] = d[1];
+    T.C[g + 8][2 * t] = d[2];
+    T.C[g + 8][2 * t + 1] = d[3];
+    __syncwarp();
+    for (int e = lane; e < 96; e += 32) {  // (child, row, column): 2 x 6 x 8
+      const int side = e / 48, row = (e % 48) >> 3, cl = e & 7;
+      const int32_t col = col0 + cl;
+      const int32_t code = side ? cc.y : cc.x;
+      if (col >= a.k || (code < 0 && row >= 3)) continue;
+      float val;
+      if (row < 3) {
+        const float lp = zero ? 0.0f : Lp[(int64_t)row * a.k + col];
+        const float sg = T.C[kp - 3 + row][cl];
+        val = side ? be * lp - al * sg : al * lp + be * sg;
+      } else {
+        // a_x: rows 0-2 of C; a_y: rows 3-5 (k = 9) or 0-2 (k = 6)
+        val = T.C[(side && type == 2 ? 3 : 0) + row - 3][cl];
+      }
+      if (code >= 0) {
+        a.xk[((int64_t)code * 6 + row) * a.k + col] = val;
+      } else {
+        const int64_t b = a.perm ? a.perm[leaf_pos(code)] : leaf_pos(code);
+        a.out[((int64_t)row * a.N + b) * a.k + col] = from_c<TS>(val);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+constexpr int kTcWarps = 8;
+
+template <class MMA, typename TS>
+__global__ void __launch_bounds__(32 * kTcWarps) k_up_seg_tc(BlockArgs<TS, float> a) {
+  __shared__ SegMeta M;
+  __shared__ TcTiles T[kTcWarps];
+  const int ns = *a.nseg, warp = threadIdx.x >> 5;
+  for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+    const int4 sg = a.seg[i];
+    const int32_t p0 = sg.x, nn = sg.y;
+    const int H = stage_meta_blk(a, p0, nn, M);
+    for (int h = 1; h <= H; ++h) {
+      for (int32_t t = M.hb[h] + warp; t < M.hb[h + 1]; t += kTcWarps)
+        tc_up_node<MMA>(a, p0 + t, M.pc[t], M.rw[t], M.ro[t], T[warp]);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+template <class MMA, typename TS>
+__global__ void __launch_bounds__(32 * kTcWarps) k_down_seg_tc(BlockArgs<TS, float> a) {
+  __shared__ SegMeta M;
+  __shared__ TcTiles T[kTcWarps];
+  const int ns = *a.nseg, warp = threadIdx.x >> 5;
+  for (int i = blockIdx.x; i < ns; i += gridDim.x) {
+    const int4 sg = a.seg[i];
+    const int32_t p0 = sg.x, nn = sg.y;
+    const int H = stage_meta_blk(a, p0, nn, M);
+    for (int h = H; h >= 1; --h) {
+      for (int32_t t = M.hb[h] + warp; t < M.hb[h + 1]; t += kTcWarps)
+        tc_down_node<MMA>(a, p0 + t, M.pc[t], M.rw[t], M.ro[t], h == H && sg.w, T[warp]);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+template <class MMA, typename TS>
+__global__ void __launch_bounds__(32 * kTcWarps) k_up_top_tc(BlockArgs<TS, float> a) {
+  __shared__ int lim[2];
+  __shared__ TcTiles T[kTcWarps];
+  const int32_t j = blockIdx.x, warp = threadIdx.x >> 5;
+  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
+  for (int h = lim[0]; h <= lim[1]; ++h) {
+    for (int32_t t = t0 + warp; t < t1; t += kTcWarps) {
+      const int32_t p = a.topv[t];
+      if (a.ph[p] == h) tc_up_node<MMA>(a, p, a.pc[p], a.prw[p], a.proff[p], T[warp]);
+    }
+    __syncthreads();
+  }
+}
+
+template <class MMA, typename TS>
+__global__ void __launch_bounds__(32 * kTcWarps) k_down_top_tc(BlockArgs<TS, float> a) {
+  __shared__ int lim[2];
+  __shared__ TcTiles T[kTcWarps];
+  const int32_t j = blockIdx.x, warp = threadIdx.x >> 5;
+  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
+  for (int h = lim[1]; h >= lim[0]; --h) {
+    for (int32_t t = t0 + warp; t < t1; t += kTcWarps) {
+      const int32_t p = a.topv[t];
+      if (a.ph[p] == h) tc_down_node<MMA>(a, p, a.pc[p], a.prw[p], a.proff[p], h == lim[1], T[warp]);
+    }
+    __syncthreads();
+  }
+}
+
+template <class MMA, typename TS>
+zq_status run_block_tc(Ctx& c, bool up, int32_t k, const void* in, void* out) {
+  BlockArgs<TS, float> a =
+      make_block_args<TS, float>(c, k, c.rec32, static_cast<const TS*>(in), static_cast<TS*>(out));
+  if (up) {
+    time_begin(c, "up_seg_blk");
+    k_up_seg_tc<MMA, TS><<<c.num_sms * 8, 32 * kTcWarps, 0, c.stream>>>(a);
+    time_end(c, "up_seg_blk");
+    time_begin(c, "up_top_blk");
+    k_up_top_tc<MMA, TS><<<(unsigned)c.m, 32 * kTcWarps, 0, c.stream>>>(a);
+    time_end(c, "up_top_blk");
+  } else {
+    time_begin(c, "down_top_blk");
+    k_down_top_tc<MMA, TS><<<(unsigned)c.m, 32 * kTcWarps, 0, c.stream>>>(a);
+    time_end(c, "down_top_blk");
+    time_begin(c, "down_seg_blk");
+    k_down_seg_tc<MMA, TS><<<c.num_sms * 8, 32 * kTcWarps, 0, c.stream>>>(a);
+    time_end(c, "down_seg_blk");
+  }
+  ZQ_CUDA_TRY(cudaGetLastError());
+  return ZQ_OK;
+}
+
 template <typename TS, typename TC>
 zq_status run_block(Ctx& c, bool up, int32_t k, const TC* rec, const void* in, void* out) {
   BlockArgs<TS, TC> a = make_block_args<TS, TC>(c, k, rec, static_cast<const TS*>(in), static_cast<TS*>(out));
@@ -784,6 +1119,8 @@ zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_
 }
 
 zq_status launch_apply_block(Ctx& c, bool up, zq_prec prec, int64_t k, const void* in, void* out) {
+  if (prec == ZQ_TF32) return run_block_tc<Tf32, float>(c, up, (int32_t)k, in, out);
+  if (prec == ZQ_BF16_TC) return run_block_tc<Bf16, __nv_bfloat16>(c, up, (int32_t)k, in, out);
   if (prec == ZQ_FP64) return run_block<double, double>(c, up, (int32_t)k, c.rec64, in, out);
   if (prec == ZQ_BF16) return run_block<__nv_bfloat16, float>(c, up, (int32_t)k, c.rec32, in, out);
   return run_block<float, float>(c, up, (int32_t)k, c.rec32, in, out);

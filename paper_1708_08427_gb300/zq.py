@@ -19,7 +19,7 @@ import numpy as np
 _LIB_PATH = Path(__file__).resolve().parent / "_build" / "libzq.so"
 
 ZQ_OK, ZQ_EINVAL, ZQ_ENOMEM, ZQ_ECUDA, ZQ_ESTATE, ZQ_ENONFINITE, ZQ_WDEGENERATE = range(7)
-ZQ_FP64, ZQ_FP32, ZQ_BF16 = 0, 1, 2
+ZQ_FP64, ZQ_FP32, ZQ_BF16, ZQ_TF32, ZQ_BF16_TC = 0, 1, 2, 3, 4
 ZQ_HOST_BUFFERS, ZQ_KEEP_TREE, ZQ_GRAPH = 1, 2, 4
 ZQ_BUILD_DD, ZQ_BUILD_FP64 = 0, 1
 ZQ_STEP_LEVELS, ZQ_STEP_FUSED = 0, 1
@@ -299,38 +299,45 @@ class Context:
 
     # ------------------------------------------------------- block form
     @staticmethod
-    def _bprec(t):
+    def _bprec(t, tensor_cores: bool = False):
         import torch
 
+        if tensor_cores:
+            return {torch.float32: ZQ_TF32, torch.bfloat16: ZQ_BF16_TC}[t.dtype]
         return {torch.float64: ZQ_FP64, torch.float32: ZQ_FP32, torch.bfloat16: ZQ_BF16}[t.dtype]
 
     def reserve_block(self, k_max: int, dtype):
-        """Block scratch for up to k_max columns of this dtype."""
+        """Block scratch for up to k_max columns of this dtype (the same
+        scratch serves the tensor-core forms of float32 and bfloat16)."""
         import torch
 
         p = {torch.float64: ZQ_FP64, torch.float32: ZQ_FP32, torch.bfloat16: ZQ_BF16}[dtype]
         _check(_lib().zq_reserve_block(self._h, p, int(k_max)), "zq_reserve_block")
 
-    def apply_Q_block(self, V, out=None):
-        """V: (3N, k) device tensor (rows of k; row a*N + i) -> (R, k)."""
+    def apply_Q_block(self, V, out=None, tensor_cores: bool = False):
+        """V: (3N, k) device tensor (rows of k; row a*N + i) -> (R, k).
+        tensor_cores: the node products on tensor cores (float32: ZQ_TF32,
+        bfloat16: ZQ_BF16_TC)."""
         N, m, R, _ = self.sizes()
         assert V.is_cuda and V.is_contiguous() and V.dim() == 2 and V.shape[0] == 3 * N
         k = V.shape[1]
         if out is None:
             out = self._torch.empty((R, k), dtype=V.dtype, device=V.device)
         assert out.is_contiguous() and tuple(out.shape) == (R, k) and out.dtype == V.dtype
-        _check(_lib().zq_apply_Q_block(self._h, self._bprec(V), k, _ptr(V), _ptr(out)), "zq_apply_Q_block")
+        _check(_lib().zq_apply_Q_block(self._h, self._bprec(V, tensor_cores), k, _ptr(V), _ptr(out)),
+               "zq_apply_Q_block")
         return out
 
-    def apply_QT_block(self, W, out=None):
-        """W: (R, k) device tensor -> (3N, k)."""
+    def apply_QT_block(self, W, out=None, tensor_cores: bool = False):
+        """W: (R, k) device tensor -> (3N, k); tensor_cores as apply_Q_block."""
         N, m, R, _ = self.sizes()
         assert W.is_cuda and W.is_contiguous() and W.dim() == 2 and W.shape[0] == R
         k = W.shape[1]
         if out is None:
             out = self._torch.empty((3 * N, k), dtype=W.dtype, device=W.device)
         assert out.is_contiguous() and tuple(out.shape) == (3 * N, k) and out.dtype == W.dtype
-        _check(_lib().zq_apply_QT_block(self._h, self._bprec(W), k, _ptr(W), _ptr(out)), "zq_apply_QT_block")
+        _check(_lib().zq_apply_QT_block(self._h, self._bprec(W, tensor_cores), k, _ptr(W), _ptr(out)),
+               "zq_apply_QT_block")
         return out
 
     def apply_QT(self, w, out=None):

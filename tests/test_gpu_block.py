@@ -65,6 +65,55 @@ def test_block_form_matches_oracle(dtype, k):
     ctx.close()
 
 
+# unit roundoff of the tensor-core operands: TF32 keeps 11 significant bits,
+# bfloat16 8
+TC_U = {torch.float32: 2.0 ** -11, torch.bfloat16: 2.0 ** -8}
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("k", [1, 7, 64])
+def test_block_form_tensor_cores_within_rounding_bound(dtype, k):
+    """ZQ_TF32 / ZQ_BF16_TC: each node's G and input block are rounded once
+    to the tensor-core type (relative u), so one node step errs by at most
+    (|dG| + |du|) |u_p| <= (3 + 1) u |u_p| (|G|_F <= 3 for k_p <= 9);
+    the steps of one height act on disjoint subtrees and the errors of lower
+    heights pass through orthogonal maps without growth, so a body of height
+    H errs by at most 4 H u |v| (+ u for bfloat16 output rounding).  Held per
+    body against the oracle on the rounded inputs; the measured error is
+    reported (print) and is far below this first-order bound."""
+    bt = W.shell_batch(m=5, nmin=40, nmax=1500, seed=7)
+    ctx = _ctx(bt)
+    dev = _dev()
+    rng = np.random.default_rng(300 + k)
+    V = torch.from_numpy(rng.standard_normal((3 * bt.N, k))).to(dev, dtype)
+    Wr = torch.from_numpy(rng.standard_normal((bt.n_residues, k))).to(dev, dtype)
+    ctx.reserve_block(k, dtype)
+    QV = ctx.apply_Q_block(V, tensor_cores=True).double().cpu().numpy()
+    QTW = ctx.apply_QT_block(Wr, tensor_cores=True).double().cpu().numpy()
+    ctx.sync()
+    Vd = V.double().cpu().numpy()
+    Wd = Wr.double().cpu().numpy()
+    u = TC_U[dtype]
+    H = [int(oracle.Body(*bt.body(j)).tree()["height"].max()) for j in range(bt.m)]
+    worst = 0.0
+    for c in range(k):
+        rq, rqt = oracle.batch_apply(bt.off, bt.x, bt.y, bt.z, W.interleave(*Vd[:, c].reshape(3, bt.N)), Wd[:, c])
+        got_t = W.interleave(*QTW[:, c].reshape(3, bt.N))
+        ro = 0
+        for j in range(bt.m):
+            o, n = int(bt.off[j]), int(bt.off[j + 1] - bt.off[j])
+            bound = (4 * H[j] + 1) * u
+            e1 = np.linalg.norm(QV[ro:ro + 3 * n - 6, c] - rq[ro:ro + 3 * n - 6]) / np.linalg.norm(
+                Vd[:, c].reshape(3, bt.N)[:, o:o + n])
+            e2 = np.linalg.norm(got_t[3 * o:3 * (o + n)] - rqt[3 * o:3 * (o + n)]) / np.linalg.norm(
+                Wd[ro:ro + 3 * n - 6, c])
+            assert e1 <= bound and e2 <= bound, (j, H[j], e1, e2, bound)
+            worst = max(worst, e1, e2)
+            ro += 3 * n - 6
+    print(f"tensor-core block form {dtype} k={k}: worst relative error {worst:.2e}")
+    ctx.close()
+
+
 def test_block_form_equals_single_column_path():
     """FP32: each column of the block form equals the column-major apply of
     that column (same transforms, same arithmetic per column)."""
