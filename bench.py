@@ -340,7 +340,7 @@ def run_ours(args, world, rank, local):
     names = (["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "fused"]
              if args.schedule == "fused" else
              ["small_tree", "aabb", "keys", "sort_radix", "lcp", "bottom_up", "scan", "segments",
-              "schedule", "build", "build_level", "build_tail", "to_tree", "up_seg", "up_top", "down_top",
+              "schedule", "build", "build_level", "build_tail", "to_tree", "up_seg_early", "up_seg", "up_top", "down_top",
               "down_seg", "from_tree"])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)

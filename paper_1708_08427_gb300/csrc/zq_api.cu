@@ -566,12 +566,36 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     ZQ_TRY(st);
     ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[2], c.side[2]));
   }
+  // The upward sweep starts early: the segments whose nodes all lie at or
+  // below the level cut need only the level launches of the build, so they
+  // are swept on a side stream while the nodes above the cut (a few long
+  // dependent chains per body) are built; the other segments and the top
+  // nodes follow the build.
+  const bool early_up = dv != nullptr;
+  auto sweep_up_early = [&]() -> zq_status {
+    ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
+    ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[1], c.fork_ev, 0));
+    if (reorder) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[1], c.join_ev[2], 0));  // v in tree order
+    if (host) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[1], c.join_ev[3], 0));     // v copied in
+    cudaStream_t main = c.stream;
+    const bool saved = c.tree_order;
+    c.stream = c.side[1];
+    c.tree_order = saved || reorder;
+    const zq_status st = zq::launch_apply_Q(c, prec, reorder ? vt : dv, 3 * N, dqv, nullptr, nullptr, 1);
+    c.tree_order = saved;
+    c.stream = main;
+    ZQ_TRY(st);
+    ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[1], c.side[1]));
+    return ZQ_OK;
+  };
   // the two sweeps of the step, each on the stream current at its call
   auto sweep_up = [&]() -> zq_status {
     if (reorder) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[2], 0));
+    if (early_up) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[1], 0));
     const bool saved = c.tree_order;
     c.tree_order = saved || reorder;
-    const zq_status st = zq::launch_apply_Q(c, prec, reorder ? vt : dv, 3 * N, dqv);
+    const zq_status st =
+        zq::launch_apply_Q(c, prec, reorder ? vt : dv, 3 * N, dqv, nullptr, nullptr, early_up ? 2 : 0);
     c.tree_order = saved;
     return st;
   };
@@ -584,7 +608,8 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     return st;
   };
   // only the records of the precision the sweeps use
-  ZQ_TRY(zq::launch_build(c, dx, dy, dz, prec == ZQ_FP64 ? 1 : 2));
+  if (early_up) ZQ_TRY(zq::launch_build(c, dx, dy, dz, prec == ZQ_FP64 ? 1 : 2, sweep_up_early));
+  else ZQ_TRY(zq::launch_build(c, dx, dy, dz, prec == ZQ_FP64 ? 1 : 2));
   c.have_xform = true;
   c.have64 = prec == ZQ_FP64;
   c.have32 = prec == ZQ_FP32;
@@ -618,7 +643,7 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[0], c.side[0]));
     ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[0], 0));
   } else {
-    if (dv) ZQ_TRY(zq_apply_Q(ctx, prec, 1, dv, 3 * N, dqv, R));
+    if (dv) ZQ_TRY(sweep_up());  // joins the early part of the sweep
     if (dw) ZQ_TRY(zq_apply_QT(ctx, prec, 1, dw, R, dqtw, 3 * N));
     if (host) {
       if (qv) ZQ_CUDA_TRY(cudaMemcpyAsync(qv, dqv, R * es, cudaMemcpyDeviceToHost, c.stream));

@@ -28,6 +28,10 @@ namespace zq {
 namespace {
 
 constexpr int kSegThreads = 128;
+#ifndef ZQ_EARLY_SEG_BLOCKS
+#define ZQ_EARLY_SEG_BLOCKS 6
+#endif
+constexpr int kEarlySegBlocksPerSM = ZQ_EARLY_SEG_BLOCKS;
 constexpr int kTopThreads = 256;
 // Bodies with at most this many top nodes: one warp each (k_*_top_warp);
 // more: one thread block each (k_*_top).
@@ -56,6 +60,8 @@ struct SweepArgs {
   const T* root_in;        // down: the root Velocity-set per body (6 m), or null (zero)
   const double* rot;       // per body R_j (9 m, row-major), or null: bead vectors enter as
                            // R_j^T v_i (up) and leave as R_j L_i (down)
+  int32_t cut;             // level cut of the build
+  int seg_mode;            // upward: 0 all segments, 1 root height <= cut, 2 root height > cut
 };
 
 // A body's rotation in registers (on = false: the identity, nothing applied).
@@ -203,6 +209,7 @@ __global__ void __launch_bounds__(kSegThreads) k_up_seg(SweepArgs<T> a) {
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
     const int4 sg = a.seg[i];
     const int32_t p0 = sg.x, nn = sg.y, f = sg.z;
+    if (a.seg_mode != 0 && ((int)a.ph[p0 + nn - 1] <= a.cut) != (a.seg_mode == 1)) continue;  // the whole block
     if (threadIdx.x < 32) {
       const uint32_t w0 = a.prw[p0], w1 = a.prw[p0 + nn];
       prefetch_l2(a.rec + 4 * (int64_t)w0, (w1 - w0) * 4u * (uint32_t)sizeof(T));
@@ -1051,18 +1058,27 @@ SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   a.seg = c.seg; a.seg_r = c.seg_r; a.R = c.R; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;
   a.bead_body = c.bead_body; a.root_out = nullptr; a.root_in = nullptr; a.rot = nullptr;
+  a.cut = c.cut; a.seg_mode = 0;
   return a;
 }
 
 template <typename T>
-zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out, T* root_out, const double* rot) {
+zq_status run_up(Ctx& c, const T* rec, T* xs, const T* v, T* out, T* root_out, const double* rot, int seg_mode) {
   SweepArgs<T> a = make_args<T>(c, rec, xs, v, out);
   a.root_out = root_out;
   a.rot = rot;
-  time_begin(c, "up_seg");
-  if (rot) k_up_seg<T, true><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
-  else k_up_seg<T, false><<<c.num_sms * 16, kSegThreads, 0, c.stream>>>(a);
-  time_end(c, "up_seg");
+  a.seg_mode = seg_mode;
+  // the early part runs beside the build's nodes above the cut: fewer
+  // persistent blocks, so that the build's blocks still find room
+  const unsigned grid = (unsigned)c.num_sms * (seg_mode == 1 ? kEarlySegBlocksPerSM : 16);
+  time_begin(c, seg_mode == 1 ? "up_seg_early" : "up_seg");
+  if (rot) k_up_seg<T, true><<<grid, kSegThreads, 0, c.stream>>>(a);
+  else k_up_seg<T, false><<<grid, kSegThreads, 0, c.stream>>>(a);
+  time_end(c, seg_mode == 1 ? "up_seg_early" : "up_seg");
+  if (seg_mode == 1) {
+    ZQ_CUDA_TRY(cudaGetLastError());
+    return ZQ_OK;
+  }
   const unsigned wblocks = (unsigned)((c.m + kTopThreads / 32 - 1) / (kTopThreads / 32));
   time_begin(c, "up_top");
   if (rot) k_up_top_warp<T, true><<<wblocks, kTopThreads, 0, c.stream>>>(a, (int32_t)c.m);
@@ -1101,12 +1117,12 @@ zq_status run_down(Ctx& c, const T* rec, T* xs, const T* w, T* out, const T* roo
 }  // namespace
 
 zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t /*ldv*/, void* out, void* root_out,
-                         const double* rot) {
+                         const double* rot, int seg_mode) {
   if (prec == ZQ_FP64)
     return run_up<double>(c, c.rec64, c.x64, static_cast<const double*>(v), static_cast<double*>(out),
-                          static_cast<double*>(root_out), rot);
+                          static_cast<double*>(root_out), rot, seg_mode);
   return run_up<float>(c, c.rec32, c.x32, static_cast<const float*>(v), static_cast<float*>(out),
-                       static_cast<float*>(root_out), rot);
+                       static_cast<float*>(root_out), rot, seg_mode);
 }
 
 zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t /*ldo*/, const void* root_in,

@@ -156,7 +156,7 @@ __global__ void k_count_table_dd(const double* __restrict__ tab, float2* __restr
 }
 
 template <class R>
-zq_status run_build(Ctx& c, const BuildArgs& a) {
+zq_status run_build(Ctx& c, const BuildArgs& a, const std::function<zq_status()>& after_levels) {
   const int grid = c.num_sms * kLevelBlocksPerSM;
   // timing brackets: "build" around the whole transform build, and
   // "build_level" around all level launches (few event records in a
@@ -169,6 +169,7 @@ zq_status run_build(Ctx& c, const BuildArgs& a) {
     k_build_level<R><<<grid, kLevelThreads, 0, c.stream>>>(a, h);
   }
   time_end(c, "build_level");
+  if (after_levels) ZQ_TRY_STATUS(after_levels());
   time_begin(c, "build_tail");
   if (c.big_bodies.empty())
     k_build_tail_warp<R><<<(unsigned)((c.m + kTailWarps - 1) / kTailWarps), 32 * kTailWarps, 0, c.stream>>>(
@@ -191,7 +192,8 @@ zq_status launch_count_table_dd(Ctx& c) {
   return ZQ_OK;
 }
 
-zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which) {
+zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which,
+                       const std::function<zq_status()>& after_levels) {
   BuildArgs a;
   a.x = x; a.y = y; a.z = z;
   a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.scnt = c.scnt; a.sheight = c.sheight; a.sid = c.sid;
@@ -203,7 +205,7 @@ zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z
   a.rec32 = (which & 2) ? c.rec32 : nullptr;
   a.err = c.counters + 2;
   c.st_is_dd = c.build_dd;
-  return c.build_dd ? run_build<dd>(c, a) : run_build<double>(c, a);
+  return c.build_dd ? run_build<dd>(c, a, after_levels) : run_build<double>(c, a, after_levels);
 }
 
 }  // namespace zq

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "zq.h"
@@ -30,7 +31,10 @@ constexpr int kMaxBuckets = 3 * kMaxCut + 1;
 // so one thread block can sweep the segment height by height in shared
 // memory.  Nodes above all segments ("top" nodes, more than kSegMax beads)
 // keep position = node id and are swept one thread block per body.
-constexpr int kSegMax = 512;
+#ifndef ZQ_SEG_MAX
+#define ZQ_SEG_MAX 512
+#endif
+constexpr int kSegMax = ZQ_SEG_MAX;
 
 // Node records (float or double words), compact and type-specific.  With
 // A = M^T (k x 3) built from [T22_x | T22_y | K], K = sqrt(n_x n_y/n)[d]x,
@@ -355,7 +359,12 @@ zq_status launch_qgen(Ctx& c, zq_prec prec, int64_t* row_ptr, int32_t* col, void
 zq_status launch_segments(Ctx& c);
 // zq_build.cu
 // which: bit 0 = FP64 records, bit 1 = FP32 records
-zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which);
+// after_levels (may be empty): called once the launches of heights 1..cut
+// are queued and before the nodes above the cut, so the caller can fork
+// work that needs only those nodes (the segments whose root is at most at
+// the cut) onto another stream.
+zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z, int which,
+                       const std::function<zq_status()>& after_levels = {});
 // zq_fused.cu: transforms, Q~ v and Q~^T w of every body in one launch
 // (bodies of at most kSmallSortMax beads; records in the fused layout)
 bool fused_step_possible(const Ctx& c);
@@ -370,8 +379,11 @@ zq_status launch_from_tree(Ctx& c, zq_prec prec, const void* ut, void* u);
 // every body / the root Velocity-set fed to Q~^T (null: zero).  rot (9 m
 // FP64, may be null): per-body rotations R_j, the products taken with
 // Q~ blockdiag(R_j^T) (bead vectors rotated by R_j^T in, R_j out).
+// seg_mode: 0 = every segment and the top nodes; 1 = only the segments
+// whose root height is at most the level cut (no top nodes); 2 = the other
+// segments, then the top nodes (after a mode 1 launch)
 zq_status launch_apply_Q(Ctx& c, zq_prec prec, const void* v, int64_t ldv, void* out,
-                         void* root_out = nullptr, const double* rot = nullptr);
+                         void* root_out = nullptr, const double* rot = nullptr, int seg_mode = 0);
 zq_status launch_apply_QT(Ctx& c, zq_prec prec, const void* w, void* out, int64_t ldo,
                           const void* root_in = nullptr, const double* rot = nullptr);
 // up: out = Q~ V, else out = Q~^T W; rows of k values (see include/zq.h)
