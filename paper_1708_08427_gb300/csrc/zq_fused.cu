@@ -103,9 +103,9 @@ __device__ __forceinline__ void up_step(const FusedArgs<T>& a, int64_t q, int2 c
   }
   const T* r = a.rec + q * kRecMax;
   T* res = a.qv + a.roff[q];
-  if (type == 0) up_node<T, 0, false>(r, X, Y, false, P, res);
-  else if (type == 1) up_node<T, 1, false>(r, X, Y, cc.x >= 0, P, res);
-  else up_node<T, 2, false>(r, X, Y, true, P, res);
+  if (type == 0) up_node<T, 0, kLdCG>(r, X, Y, false, P, res);
+  else if (type == 1) up_node<T, 1, kLdCG>(r, X, Y, cc.x >= 0, P, res);
+  else up_node<T, 2, kLdCG>(r, X, Y, true, P, res);
   st6(a.xs + 6 * q, P);
 }
 
@@ -122,9 +122,9 @@ __device__ __forceinline__ void down_step(const FusedArgs<T>& a, int64_t q, int2
   }
   const T* r = a.rec + q * kRecMax;
   const T* w = a.w + a.roff[q];
-  if (type == 0) down_node<T, 0, false>(r, Lp, w, false, Lx, Ly);
-  else if (type == 1) down_node<T, 1, false>(r, Lp, w, cc.x >= 0, Lx, Ly);
-  else down_node<T, 2, false>(r, Lp, w, true, Lx, Ly);
+  if (type == 0) down_node<T, 0, kLdCG>(r, Lp, w, false, Lx, Ly);
+  else if (type == 1) down_node<T, 1, kLdCG>(r, Lp, w, cc.x >= 0, Lx, Ly);
+  else down_node<T, 2, kLdCG>(r, Lp, w, true, Lx, Ly);
   const int32_t ch[2] = {cc.x, cc.y};
   const T* L[2] = {Lx, Ly};
 #pragma unroll

@@ -21,22 +21,26 @@ namespace zq {
 
 namespace {
 
-// Load W words of a record (16-byte vector loads; NC: through the read-only
-// path, for records no thread of the running kernel writes).
-template <typename T, int W, bool NC = true>
-__device__ __forceinline__ void load_rec(const T* __restrict__ g, T (&r)[W]) {
+// How a record is read: through the read-only path (records no thread of
+// the running kernel writes), or with coherent L2 loads (records written in
+// the same launch).
+constexpr int kLdNC = 0, kLdCG = 1;
+
+// Load W words of a record (16-byte vector loads).
+template <typename T, int W, int LD = kLdNC>
+__device__ __forceinline__ void load_rec(const T* g, T (&r)[W]) {
   if constexpr (sizeof(T) == 4) {
     const float4* p = reinterpret_cast<const float4*>(g);
 #pragma unroll
     for (int i = 0; i < W / 4; ++i) {
-      const float4 q = NC ? __ldg(p + i) : p[i];
+      const float4 q = LD == kLdNC ? __ldg(p + i) : __ldcg(p + i);
       r[4 * i] = q.x; r[4 * i + 1] = q.y; r[4 * i + 2] = q.z; r[4 * i + 3] = q.w;
     }
   } else {
     const double2* p = reinterpret_cast<const double2*>(g);
 #pragma unroll
     for (int i = 0; i < W / 2; ++i) {
-      const double2 q = NC ? __ldg(p + i) : p[i];
+      const double2 q = LD == kLdNC ? __ldg(p + i) : __ldcg(p + i);
       r[2 * i] = q.x; r[2 * i + 1] = q.y;
     }
   }
@@ -109,11 +113,11 @@ __device__ __forceinline__ void g9(const T* r, T* u, bool transpose) {
 // --------------------------------------------------------- node: upward
 // X, Y: the children's Info-sets [t; r] (r unused for leaves).  Writes the
 // node's Info-set to P and its residues to res.
-template <typename T, int TYPE, bool NC = true>
-__device__ __forceinline__ void up_node(const T* __restrict__ recp, const T* X, const T* Y, bool xi,
+template <typename T, int TYPE, int LD = kLdNC>
+__device__ __forceinline__ void up_node(const T* recp, const T* X, const T* Y, bool xi,
                                         T* P, T* __restrict__ res) {
   T r[rec_words(TYPE)];
-  load_rec<T, rec_words(TYPE), NC>(recp, r);
+  load_rec<T, rec_words(TYPE), LD>(recp, r);
   const T al = r[0], be = r[1];
   T u[9];
   int k = 0;
@@ -149,11 +153,11 @@ __device__ __forceinline__ void up_node(const T* __restrict__ recp, const T* X, 
 }
 
 // ------------------------------------------------------- node: downward
-template <typename T, int TYPE, bool NC = true>
-__device__ __forceinline__ void down_node(const T* __restrict__ recp, const T* Lp, const T* __restrict__ w,
+template <typename T, int TYPE, int LD = kLdNC>
+__device__ __forceinline__ void down_node(const T* recp, const T* Lp, const T* __restrict__ w,
                                           bool xi, T* Lx, T* Ly) {
   T r[rec_words(TYPE)];
-  load_rec<T, rec_words(TYPE), NC>(recp, r);
+  load_rec<T, rec_words(TYPE), LD>(recp, r);
   const T al = r[0], be = r[1];
   T z[9];
   z[0] = Lp[3]; z[1] = Lp[4]; z[2] = Lp[5];
