@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 / apply-only / e2e / CPU legs")
     ap.add_argument("--extras", default="all",
                     help="comma-separated subset of the extra legs: error, build_other, fp64_step, apply, qgen, "
-                         "e2e, multirhs, bd_loop, cpu (default all)")
+                         "e2e, multirhs, ellipsoid, bd_loop, cpu (default all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the per-kernel timing pass (the dominant kernel is then build_level)")
@@ -455,7 +455,7 @@ def run_ours(args, world, rank, local):
     # the outputs of the last timed step against the FP64 oracle (rank 0):
     # the error the metric is stated at
     legs = set() if args.no_extras else (
-        {"error", "build_other", "fp64_step", "apply", "qgen", "e2e", "multirhs", "bd_loop", "cpu"}
+        {"error", "build_other", "fp64_step", "apply", "qgen", "e2e", "multirhs", "ellipsoid", "bd_loop", "cpu"}
         if args.extras == "all" else set(args.extras.split(",")))
     if rank == 0 and "error" in legs:
         stream.synchronize()
@@ -467,9 +467,11 @@ def run_ours(args, world, rank, local):
     sweeps = {}
     for nm in ("up_seg", "down_seg"):
         if phases.get(nm):
+            # the upward sweep's segments run in two launches (those at or
+            # below the level cut beside the build, the rest after it)
+            ms = phases[nm] + (phases.get("up_seg_early", 0.0) if nm == "up_seg" else 0.0)
             byt = sweep_bytes(census, N, R, 4, gather=False)
-            sweeps[nm] = {"ms": phases[nm], "algorithmic_bytes": byt,
-                          "hbm_frac": byt / (phases[nm] / 1e3) / 1e9 / hbm_peak}
+            sweeps[nm] = {"ms": ms, "algorithmic_bytes": byt, "hbm_frac": byt / (ms / 1e3) / 1e9 / hbm_peak}
     roofline["sweeps_in_step"] = sweeps
 
     if not args.no_graph:
@@ -494,6 +496,8 @@ def run_ours(args, world, rank, local):
         out["e2e"] = e2e(args, ctx, bt, stream, world, dev)
     if "multirhs" in legs:
         out["multirhs"] = multirhs(args, stream, flush, world, dev, rank)
+    if "ellipsoid" in legs and args.workload != "ellipsoid":
+        out["ellipsoid_2e20"] = ellipsoid_leg(args, stream, flush, world, dev, rank)
     if "bd_loop" in legs:
         out["bd_loop"] = bd_loop(args, stream, flush, world, dev, rank)
         out["bd_loop_rotation_reuse"] = bd_loop(args, stream, flush, world, dev, rank, reuse=True)
@@ -522,7 +526,8 @@ def run_ours(args, world, rank, local):
                       "up_frac": round(sweeps["up_seg"]["hbm_frac"], 3) if "up_seg" in sweeps else None,
                       "down_frac": round(sweeps["down_seg"]["hbm_frac"], 3) if "down_seg" in sweeps else None,
                       "pair_tree_frac": round(cmp["apply_pair_fp32_tree_order_hbm_frac"], 3)
-                      if "apply_pair_fp32_tree_order_hbm_frac" in cmp else None}
+                      if "apply_pair_fp32_tree_order_hbm_frac" in cmp else None,
+                      "ellipsoid_ms": round(out["ellipsoid_2e20"]["ms_per_step"], 4) if "ellipsoid_2e20" in out else None}
     return out
 
 
@@ -827,6 +832,42 @@ def multirhs(args, stream, flush, world, dev, rank, k=64):
     res["fp32_column_by_column"] = r
     ctx.close()
     return res
+
+
+def ellipsoid_leg(args, stream, flush, world, dev, rank):
+    """One body of 2^20 beads (the ellipsoid with semi-axes (3, 2, 1) sqrt(n)/100
+    and radial jitter N(0, 0.01^2)): the same step (tree, double-single
+    transforms, FP32 Q~v and Q~^T w, one zq_pipeline call replayed from the
+    library's graph), each level cut of the tuner timed; the body is too
+    large for the fused step.  Its per-bead rate against the batched step
+    shows the cost of the large-body path."""
+    import torch
+
+    from paper_1708_08427_gb300 import workloads as W
+    from paper_1708_08427_gb300 import zq
+    from paper_1708_08427_gb300.tune import tune_level_cut
+
+    bt = W.ellipsoid_body(n=1 << 20, seed=rank)
+    N, R = bt.N, bt.n_residues
+    rng = np.random.default_rng(5)
+    with torch.cuda.stream(stream):
+        x, y, z = (torch.from_numpy(a.copy()).to(dev) for a in (bt.x, bt.y, bt.z))
+        v = torch.from_numpy(rng.standard_normal((3, N))).to(dev, torch.float32)
+        w = torch.from_numpy(rng.standard_normal(R)).to(dev, torch.float32)
+        qv = torch.empty(R, device=dev)
+        qtw = torch.empty((3, N), device=dev)
+    stream.synchronize()
+    ctx = zq.Context(dev.index, stream)
+    cut, times = tune_level_cut(ctx, bt.off, x, y, z, v, qv, w, qtw, graph=not args.no_graph)
+
+    def fn():
+        ctx.pipeline(bt.off, x, y, z, v, qv, w, qtw, level_cut=cut, graph=not args.no_graph)
+
+    r = timed(args, fn, stream, flush, world, dev, N, graph=False)
+    ctx.close()
+    r.update({"workload": "one ellipsoid body, n=2^20, semi-axes (3,2,1)*sqrt(n)/100, radial jitter N(0,0.01^2)",
+              "level_cut": cut, "level_cut_tuning_ms": times})
+    return r
 
 
 def bd_loop(args, stream, flush, world, dev, rank, steps_in_graph=10, reuse=False):
