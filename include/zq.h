@@ -309,9 +309,10 @@ zq_status zq_set_build_arith(zq_ctx *ctx, zq_build_arith arith);
  *   ZQ_STEP_LEVELS (default): the transforms level by level over all bodies
  *     (one launch per height up to the level cut, then one block or warp
  *     per body), then the sweeps on segments of at most 512 beads.
- *   ZQ_STEP_FUSED: one persistent launch; a thread block takes the next
- *     body from a queue ordered by bead count (largest first) and runs its
- *     transforms with Q~ v, then Q~^T w, height by height.  Used when every
+ *   ZQ_STEP_FUSED: one launch; the bodies are dealt to the thread blocks
+ *     largest first, each to the block with the fewest nodes so far, and a
+ *     block runs its bodies' transforms with Q~ v, then Q~^T w, height by
+ *     height.  Used when every
  *     body has at most 8192 beads (else the step falls back to
  *     ZQ_STEP_LEVELS).  The transform arithmetic and the node steps are the
  *     same, so both schedules give the same bits.  The records are stored

@@ -26,7 +26,7 @@ zq_status grow(T** p, int64_t count) {
 }
 
 void free_all(Ctx& c) {
-  void* ps[] = {c.off, c.small_d, c.lpt, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
+  void* ps[] = {c.off, c.small_d, c.fused_bin_start, c.fused_bin_bodies, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.root_slot, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.flag, c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
                 c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage, c.ord,
@@ -67,7 +67,8 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     const int64_t nodes = N;  // >= N - m
     ZQ_TRY(grow(&c.off, m + 1));
     ZQ_TRY(grow(&c.small_d, m));
-    ZQ_TRY(grow(&c.lpt, m));
+    ZQ_TRY(grow(&c.fused_bin_start, m + 1));
+    ZQ_TRY(grow(&c.fused_bin_bodies, m));
     ZQ_TRY(grow(&c.bead_body, N));
     ZQ_TRY(grow(&c.aabb, 6 * m));
     ZQ_TRY(grow(&c.body_scale, 3 * m));
@@ -248,17 +249,36 @@ static zq_status build_tree_impl(zq_ctx* ctx, int64_t m, const int64_t* off, con
       c.small_bodies.insert(c.small_bodies.end(), cls[k].begin(), cls[k].end());
     }
     c.small_class_start[4] = (int)c.small_bodies.size();
-    // the fused step's queue: largest bodies first (ties by id)
-    c.lpt_h.resize((size_t)m);
-    for (int64_t j = 0; j < m; ++j) c.lpt_h[(size_t)j] = (int32_t)j;
-    std::stable_sort(c.lpt_h.begin(), c.lpt_h.end(),
+    // the fused step's blocks: bodies largest first (ties by id), each to
+    // the block with the fewest nodes so far; four blocks per SM
+    std::vector<int32_t> order((size_t)m);
+    for (int64_t j = 0; j < m; ++j) order[(size_t)j] = (int32_t)j;
+    std::stable_sort(order.begin(), order.end(),
                      [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    c.fused_bins = (int32_t)std::min<int64_t>((int64_t)c.num_sms * 4, m);
+    std::vector<std::vector<int32_t>> bins((size_t)c.fused_bins);
+    std::vector<std::pair<int64_t, int32_t>> heap;  // (nodes, bin), min-heap
+    for (int32_t b = 0; b < c.fused_bins; ++b) heap.push_back({0, b});
+    auto later = [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) { return x > y; };
+    for (const int32_t j : order) {
+      std::pop_heap(heap.begin(), heap.end(), later);
+      auto& top = heap.back();
+      bins[(size_t)top.second].push_back(j);
+      top.first += off[j + 1] - off[j] - 1;
+      std::push_heap(heap.begin(), heap.end(), later);
+    }
+    c.fused_bins_h.assign(1, 0);
+    for (const auto& bin : bins) c.fused_bins_h.push_back(c.fused_bins_h.back() + (int32_t)bin.size());
+    for (const auto& bin : bins) c.fused_bins_h.insert(c.fused_bins_h.end(), bin.begin(), bin.end());
   }
   ZQ_CUDA_TRY(cudaMemcpyAsync(c.off, off, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
   if (!c.small_bodies.empty())
     ZQ_CUDA_TRY(cudaMemcpyAsync(c.small_d, c.small_bodies.data(), c.small_bodies.size() * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, c.stream));
-  ZQ_CUDA_TRY(cudaMemcpyAsync(c.lpt, c.lpt_h.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
+  ZQ_CUDA_TRY(cudaMemcpyAsync(c.fused_bin_start, c.fused_bins_h.data(), (c.fused_bins + 1) * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, c.stream));
+  ZQ_CUDA_TRY(cudaMemcpyAsync(c.fused_bin_bodies, c.fused_bins_h.data() + c.fused_bins + 1, m * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, c.stream));
   // the host vectors are read by the copies above: keep them alive until then
   ZQ_CUDA_TRY(cudaStreamSynchronize(c.stream));
   ZQ_TRY(zq::launch_bead_body(c));

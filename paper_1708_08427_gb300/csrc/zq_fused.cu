@@ -5,16 +5,16 @@
 // each body's node transforms (Sec. 3, Eq. 3.5, Case I of Eqs. 3.9-3.10),
 // its upward sweep Q~ v (Algorithm 2, Eqs. 4.2-4.3) and its downward sweep
 // Q~^T w (Algorithm 3, Theorem 4.3) can run to completion in one thread
-// block without waiting for any other body.  A block takes the next body
-// from a queue ordered by bead count, largest first (longest processing
-// time first, so the long dependent chains of the large bodies start early
-// and the small bodies fill in behind them), sorts the body's nodes by
-// height in shared memory, then:
+// block without waiting for any other body.  The bodies are dealt to the
+// thread blocks largest first, each to the block with the fewest nodes so
+// far (longest processing time first, on the host at plan time).  A block
+// takes its bodies in groups of at most kFusedMaxNodes nodes, sorts the
+// group's nodes by (height, type) in shared memory, then:
 //   heights 1, 2, ...: each node's transform (the node code of
 //     zq_build_node.cuh, the same arithmetic as the level build) and, right
 //     after it, the node's upward step from its children's Info-sets;
 //   heights H, H - 1, ...: each node's downward step, from its Velocity-set
-//     to its children's (the root's is 0).
+//     to its children's (each body root's is 0).
 // One barrier per height.  There is no schedule across bodies: no level
 // launches, no segment or bucket schedule, no tree-order passes; bead
 // vectors are read and written through the tree's permutation directly.
@@ -43,8 +43,7 @@ constexpr int kFusedThreads = ZQ_FUSED_THREADS;
 // nodes are sorted by (height, type), type = internal children (0, 1, 2),
 // so that a warp mostly runs one kind of node transform
 constexpr int kFusedBins = 3 * (kMaxHeight + 2);
-constexpr int kFusedMaxNodes = kSmallSortMax - 1;  // bodies of at most kSmallSortMax beads
-static_assert(kFusedMaxNodes < 32768, "local node indices are int16");
+constexpr int kFusedMaxNodes = kSmallSortMax - 1;  // nodes of one group; bodies of at most kSmallSortMax beads
 
 template <typename T>
 struct FusedArgs {
@@ -54,8 +53,9 @@ struct FusedArgs {
   const int32_t* cr;
   const int32_t* roff;
   const uint8_t* height;
-  const int32_t* lpt;    // body ids, largest first
-  int32_t* queue;        // next entry of lpt (zeroed before the launch)
+  const int32_t* bin_start;   // [bins + 1]: the bodies of block b are bin_bodies[bin_start[b] ..]
+  const int32_t* bin_bodies;
+  const int32_t* root;        // root node id of every body
   int32_t m;
   int64_t N;
   bool tree_order;       // bead planes indexed by sorted position, not by bead
@@ -142,28 +142,36 @@ __device__ __forceinline__ void down_step(const FusedArgs<T>& a, int64_t q, int2
 
 template <class R, typename T>
 __global__ void __launch_bounds__(kFusedThreads) k_fused_step(FusedArgs<T> a) {
-  __shared__ int16_t ids[kFusedMaxNodes];
+  __shared__ int32_t ids[kFusedMaxNodes];
   __shared__ int32_t hs[kFusedBins];    // first index of each (height, type) in ids
   __shared__ int32_t fill[kFusedBins];
-  __shared__ int32_t cur, hmax;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      cur = atomicAdd(a.queue, 1);
-      hmax = 0;
+  __shared__ int32_t hmax;
+  const int32_t g0 = a.bin_start[blockIdx.x], g1 = a.bin_start[blockIdx.x + 1];
+  // the block's bodies in groups of at most kFusedMaxNodes nodes, each
+  // group's nodes processed together, height by height
+  for (int32_t gb = g0; gb < g1;) {
+    int32_t ge = gb, total = 0;
+    while (ge < g1) {
+      const int32_t j = a.bin_bodies[ge];
+      const int32_t nn = (int32_t)(a.off[j + 1] - a.off[j]) - 1;
+      if (ge > gb && total + nn > kFusedMaxNodes) break;
+      total += nn;
+      ++ge;
     }
+    if (threadIdx.x == 0) hmax = 0;
     for (int h = threadIdx.x; h < kFusedBins; h += blockDim.x) fill[h] = 0;
     __syncthreads();
-    const int32_t jb = cur;
-    if (jb >= a.m) return;  // the whole block
-    const int32_t j = a.lpt[jb];
-    const int64_t o = a.off[j];
-    const int32_t nn = (int32_t)(a.off[j + 1] - o) - 1;
-    const int64_t q0 = o - j;  // the body's first node id
-    // counting sort of the body's nodes by (height, type)
-    for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
-      const int h = a.height[q0 + t];
-      atomicAdd(&fill[3 * h + (a.cl[q0 + t] >= 0) + (a.cr[q0 + t] >= 0)], 1);
-      atomicMax(&hmax, h);
+    // counting sort of the group's nodes by (height, type)
+    for (int32_t e = gb; e < ge; ++e) {
+      const int32_t j = a.bin_bodies[e];
+      const int64_t q0 = a.off[j] - j;
+      const int32_t nn = (int32_t)(a.off[j + 1] - a.off[j]) - 1;
+      for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int64_t q = q0 + t;
+        const int h = a.height[q];
+        atomicAdd(&fill[3 * h + (a.cl[q] >= 0) + (a.cr[q] >= 0)], 1);
+        atomicMax(&hmax, h);
+      }
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive scan of the counts by the first warp
@@ -192,15 +200,22 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused_step(FusedArgs<T> a) {
       }
     }
     __syncthreads();
-    for (int32_t t = threadIdx.x; t < nn; t += blockDim.x)
-      ids[atomicAdd(&fill[3 * a.height[q0 + t] + (a.cl[q0 + t] >= 0) + (a.cr[q0 + t] >= 0)], 1)] = (int16_t)t;
+    for (int32_t e = gb; e < ge; ++e) {
+      const int32_t j = a.bin_bodies[e];
+      const int64_t q0 = a.off[j] - j;
+      const int32_t nn = (int32_t)(a.off[j + 1] - a.off[j]) - 1;
+      for (int32_t t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int64_t q = q0 + t;
+        ids[atomicAdd(&fill[3 * a.height[q] + (a.cl[q] >= 0) + (a.cr[q] >= 0)], 1)] = (int32_t)q;
+      }
+    }
     __syncthreads();
     const int H = hmax;
     // upward: transforms, then Q~ v, height by height
     for (int h = 1; h <= H; ++h) {
-      const int32_t k1 = h < H ? hs[3 * h + 3] : nn;
+      const int32_t k1 = h < H ? hs[3 * h + 3] : total;
       for (int32_t k = hs[3 * h] + threadIdx.x; k < k1; k += blockDim.x) {
-        const int64_t q = q0 + ids[k];
+        const int64_t q = ids[k];
         const int2 cc = make_int2(a.cl[q], a.cr[q]);
         const int type = (cc.x >= 0) + (cc.y >= 0);
         const int64_t rw = q * kRecMax;
@@ -211,30 +226,29 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused_step(FusedArgs<T> a) {
       }
       __syncthreads();
     }
-    // downward: Q~^T w from the root
+    // downward: Q~^T w from each body's root, whose Velocity-set is 0
     if (a.w) {
+      for (int32_t e = gb + (int32_t)threadIdx.x / 8; e < ge; e += (int32_t)blockDim.x / 8)
+        if (threadIdx.x % 8 < 6) a.xs[6 * (int64_t)a.root[a.bin_bodies[e]] + threadIdx.x % 8] = T(0);
+      __syncthreads();
       for (int h = H; h >= 1; --h) {
-        const int32_t k1 = h < H ? hs[3 * h + 3] : nn;
+        const int32_t k1 = h < H ? hs[3 * h + 3] : total;
         for (int32_t k = hs[3 * h] + threadIdx.x; k < k1; k += blockDim.x) {
-          const int64_t q = q0 + ids[k];
+          const int64_t q = ids[k];
           const int2 cc = make_int2(a.cl[q], a.cr[q]);
-          down_step(a, q, cc, (cc.x >= 0) + (cc.y >= 0), h == H);
+          down_step(a, q, cc, (cc.x >= 0) + (cc.y >= 0), false);
         }
         __syncthreads();
       }
     }
+    gb = ge;
   }
 }
 
 template <class R, typename T>
 zq_status run_fused(Ctx& c, const FusedArgs<T>& a) {
-  int per_sm = 0;
-  ZQ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_step<R, T>, kFusedThreads, 0));
-  if (per_sm < 1) per_sm = 1;
-  const int64_t grid = std::min<int64_t>((int64_t)c.num_sms * per_sm, c.m);
-  ZQ_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(int32_t), c.stream));
   time_begin(c, "fused");
-  k_fused_step<R, T><<<(unsigned)grid, kFusedThreads, 0, c.stream>>>(a);
+  k_fused_step<R, T><<<(unsigned)c.fused_bins, kFusedThreads, 0, c.stream>>>(a);
   time_end(c, "fused");
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
@@ -242,7 +256,7 @@ zq_status run_fused(Ctx& c, const FusedArgs<T>& a) {
 
 }  // namespace
 
-bool fused_step_possible(const Ctx& c) { return c.have_tree && c.big_bodies.empty() && c.m > 0; }
+bool fused_step_possible(const Ctx& c) { return c.have_tree && c.big_bodies.empty() && c.fused_bins > 0; }
 
 zq_status launch_fused_step(Ctx& c, zq_prec prec, const double* x, const double* y, const double* z,
                             const void* v, void* qv, const void* w, void* qtw) {
@@ -262,7 +276,8 @@ zq_status launch_fused_step(Ctx& c, zq_prec prec, const double* x, const double*
     using T = std::remove_pointer_t<decltype(xs)>;
     a.b = b;
     a.off = c.off; a.cl = c.cl; a.cr = c.cr; a.roff = c.roff; a.height = c.height;
-    a.lpt = c.lpt; a.queue = c.counters; a.m = (int32_t)c.m; a.N = c.N; a.tree_order = c.tree_order;
+    a.bin_start = c.fused_bin_start; a.bin_bodies = c.fused_bin_bodies; a.root = c.root;
+    a.m = (int32_t)c.m; a.N = c.N; a.tree_order = c.tree_order;
     a.v = static_cast<const T*>(v); a.qv = static_cast<T*>(qv);
     a.w = static_cast<const T*>(w); a.qtw = static_cast<T*>(qtw);
     a.xs = xs; a.rec = rec;

@@ -86,7 +86,7 @@ struct Ctx {
   bool have_sched = false; // the segment and bucket schedules of the current tree exist
   bool st_is_dd = false;   // representation of st64 written by the last build
   std::vector<int64_t> off_h;
-  std::vector<int32_t> lpt_h;         // host copy of lpt (kept alive for its upload)
+  std::vector<int32_t> fused_bins_h;  // host copies (kept alive for their upload): starts, then bodies
   std::vector<int32_t> small_bodies;  // n_j <= kSmallSortMax, grouped by size class
   std::vector<int32_t> big_bodies;    // n_j > kSmallSortMax (device-wide tree kernels)
   int small_class_start[5] = {0, 0, 0, 0, 0};
@@ -94,7 +94,11 @@ struct Ctx {
   // device buffers (bodies)
   int64_t* off = nullptr;        // [m+1]
   int32_t* small_d = nullptr;    // [m] ids of small bodies
-  int32_t* lpt = nullptr;        // [m] body ids by bead count, largest first (fused step queue)
+  // fused step: the bodies dealt to fused_bins thread blocks, largest
+  // first, each to the block with the fewest nodes so far (LPT)
+  int32_t fused_bins = 0;
+  int32_t* fused_bin_start = nullptr;   // [m + 1] (first fused_bins + 1 used)
+  int32_t* fused_bin_bodies = nullptr;  // [m]
   int32_t* bead_body = nullptr;  // [N] body of each bead / sorted position
   uint64_t* aabb = nullptr;      // [m * 6] ordered-int encoded lo[3], hi[3]
   double* body_scale = nullptr;  // [m * 3] 1 / (hi - lo) per axis (0 if hi == lo)
