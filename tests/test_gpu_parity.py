@@ -229,6 +229,22 @@ def test_results_do_not_depend_on_level_cut():
             assert torch.equal(a, b)
 
 
+def test_size_class_and_segment_boundaries():
+    """Bodies on both sides of every size boundary of the schedules: the
+    per-block tree classes (1024, 2048, 4096, 8192 beads; 8193 goes to the
+    device-wide sort), the 512-bead segments (a whole-body segment, and a
+    body with one node above its segments) and the 64-top-node warp path:
+    tree bit-exact, both products against the oracle."""
+    sizes = [511, 512, 513, 1024, 1025, 2048, 2049, 4096, 4097, 8192, 8193]
+    bodies = [np.stack(W.shell_body(n, seed=70 + i).body(0), 1) for i, n in enumerate(sizes)]
+    bt = _batch_from_points(bodies)
+    ctx, _ = make_ctx(bt, cut=12)
+    ob = oracle_bodies(bt)
+    check_tree(ctx, bt, ob)
+    check_apply(ctx, bt, np.float64, seed=11)
+    check_apply(ctx, bt, np.float32, seed=11)
+
+
 def test_large_body_radix_sort_path():
     """A body above the per-block sort limit (device radix sort), with many
     nodes above the level cut (one block for the whole body's top)."""
