@@ -5,11 +5,12 @@
 //   2. 21-bit quantisation and bisection keys (z, then y, then x per octree
 //      level, most significant first);
 //   3. stable LSD radix sort of (key, body-local index) in shared memory,
-//      8-bit digits, warp-level ranks from ballots: four passes over the
-//      high 32 key bits, then each run of
-//      equal high halves (rare: beads closer than 2^-10 of the box) sorted
-//      by insertion; bodies with a run of more than 32 such beads take all
-//      eight passes instead.  Equal keys keep index order;
+//      8-bit digits, warp-level ranks from ballots: kHighPasses passes over
+//      the high 8 kHighPasses key bits, then each run of equal high bits
+//      (beads in one cell of the first 8 kHighPasses / 3 octree levels; a
+//      few beads on a shell) sorted by insertion; bodies with a run of more
+//      than 32 such beads take all eight passes instead.  Equal keys keep
+//      index order;
 //   4. LCP of sorted neighbours (63 coordinate levels, then 32 index levels);
 //   5. bottom-up construction: a node's parent is the neighbouring split
 //      with the larger LCP; each child deposits (code, range end, height) in
@@ -23,6 +24,18 @@
 namespace zq {
 
 namespace {
+
+// Radix passes over the high key bits before the run fix-up.  Two passes
+// (the first 5 1/3 octree levels) leave runs of at most about ten beads on
+// the shells of up to 8192 beads; each pass costs about a quarter of the
+// kernel.
+#ifndef ZQ_SORT_HIGH_PASSES
+#define ZQ_SORT_HIGH_PASSES 2
+#endif
+constexpr int kHighPasses = ZQ_SORT_HIGH_PASSES;
+// (an even count: the sorted order ends in the first buffer)
+static_assert(kHighPasses == 2 || kHighPasses == 4, "an even number of passes over at most the high half");
+constexpr int kHighShift = 64 - 8 * kHighPasses;
 
 struct SmallTreeArgs {
   const double* x;
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   const unsigned lt = (1u << lane) - 1u;
   const int per_warp = (n + NW - 1) / NW;
   __shared__ int long_run;
-  int pass_lo = 4;  // first the high 32 key bits only (see the fix-up below)
+  int pass_lo = 8 - kHighPasses;  // first the high key bits only (see the fix-up below)
   for (;;) {
   uint64_t* kin = keyA;
   uint64_t* kout = keyB;
@@ -264,19 +277,19 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
     uint64_t* tk = kin; kin = kout; kout = tk;
     uint16_t* ti = iin; iin = iout; iout = ti;
   }
-  // after 4 or 8 passes the sorted data is back in keyA / idxA
+  // after an even number of passes the sorted data is back in keyA / idxA
   if (pass_lo == 0) break;
-  // Fix-up of the 4-pass order: beads whose keys share the high 32 bits
-  // (the first 10 2/3 octree levels) are in index order; each such run is
-  // sorted by the low bits (stable, so equal keys keep index order).  A run
-  // longer than 32 beads sends the body through all 8 passes instead.
+  // Fix-up of the high-bit order: beads whose keys share the high bits are
+  // in index order; each such run is sorted by the low bits (stable, so
+  // equal keys keep index order).  A run longer than 32 beads sends the
+  // body through all 8 passes instead.
   if (tid == 0) long_run = 0;
   __syncthreads();
   for (int p = tid; p < n; p += THREADS) {
-    const uint32_t hk = (uint32_t)(keyA[p] >> 32);
-    if (p > 0 && (uint32_t)(keyA[p - 1] >> 32) == hk) continue;   // not a run start
+    const uint64_t hk = keyA[p] >> kHighShift;
+    if (p > 0 && (keyA[p - 1] >> kHighShift) == hk) continue;   // not a run start
     int L = 1;
-    while (p + L < n && L <= 32 && (uint32_t)(keyA[p + L] >> 32) == hk) ++L;
+    while (p + L < n && L <= 32 && (keyA[p + L] >> kHighShift) == hk) ++L;
     if (L == 1) continue;
     if (L > 32) {
       long_run = 1;
