@@ -197,7 +197,7 @@ zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z
   BuildArgs a;
   a.x = x; a.y = y; a.z = z;
   a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.scnt = c.scnt; a.sheight = c.sheight; a.sid = c.sid;
-  a.bstart = c.bstart; a.srw = c.srw; a.root_slot = c.root_slot; a.cut = c.cut;
+  a.bstart = c.bstart; a.srw = c.srw; a.cut = c.cut;
   a.ctab = c.count_tab;
   a.ctab2 = c.count_tab2;
   a.st = c.st64;

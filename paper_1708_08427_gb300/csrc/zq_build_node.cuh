@@ -59,7 +59,6 @@ struct BuildArgs {
   const int32_t* sid;
   const int32_t* bstart;
   const int32_t* srw;   // record offset of each slot, 4-word units (uint32)
-  const int32_t* root_slot;
   const double* ctab;   // sqrt(n) [0, kCountTab), 1/sqrt(n) [kCountTab, 2 kCountTab)
   const float2* ctab2;  // the same as double-single pairs
   int cut;

@@ -264,7 +264,7 @@ zq_status launch_fused_step(Ctx& c, zq_prec prec, const double* x, const double*
   BuildArgs b;
   b.x = x; b.y = y; b.z = z;
   b.off = c.off; b.perm = c.perm; b.sc = nullptr; b.scnt = c.cnt; b.sheight = nullptr; b.sid = nullptr;
-  b.bstart = nullptr; b.srw = nullptr; b.root_slot = nullptr; b.cut = c.cut;
+  b.bstart = nullptr; b.srw = nullptr; b.cut = c.cut;
   b.ctab = c.count_tab;
   b.ctab2 = c.count_tab2;
   b.st = c.st64;

@@ -105,7 +105,6 @@ struct Ctx {
   double* count_tab = nullptr;   // [2 * kCountTab]: sqrt(n), 1/sqrt(n)
   float2* count_tab2 = nullptr;  // the same as double-single pairs
   int32_t* root = nullptr;       // [m] root node id
-  int32_t* root_slot = nullptr;  // [m] root slot
   // beads
   uint64_t* key = nullptr;       // [N] Morton keys in bead order
   uint64_t* skey = nullptr;      // [N] keys in sorted order

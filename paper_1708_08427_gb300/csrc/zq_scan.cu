@@ -1,6 +1,8 @@
 // zq_scan.cu -- exclusive prefix sums of int32 (residue offsets, list
-// compaction) and int64 (nonzero counts of the explicit Q~).  Three launches: per-block totals, one block scanning the
-// totals with a running carry, per-block scan plus carry.
+// compaction) and int64 (nonzero counts of the explicit Q~).  Up to 192 KB
+// of values: one launch, one block.  Longer arrays: three
+// launches (per-block totals, one block scanning the totals with a running
+// carry, per-block scan plus carry).
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -91,6 +93,38 @@ __global__ void k_block_scan(const I* __restrict__ in, int64_t n, const I* __res
   }
 }
 
+// Arrays of at most one_block_max<I>() values: one block.  The array is loaded
+// into shared memory with coalesced loads (all in flight at once), thread t
+// scans its consecutive chunk there, a block scan of the chunk sums gives
+// the chunk prefixes, and the result goes out with coalesced stores.
+constexpr int kOneBlockBytes = 192 * 1024;
+template <typename I>
+constexpr int64_t one_block_max() { return kOneBlockBytes / (int64_t)sizeof(I); }
+
+template <typename I>
+__global__ void __launch_bounds__(kThreads) k_scan_one_block(const I* in, int64_t n, I* out, I* total) {
+  extern __shared__ __align__(16) unsigned char scan_smem[];
+  I* v = reinterpret_cast<I*>(scan_smem);
+  __shared__ I sh[33];
+  for (int64_t i = threadIdx.x; i < n; i += kThreads) v[i] = in[i];
+  __syncthreads();
+  const int64_t per = (n + kThreads - 1) / kThreads;
+  const int64_t b0 = (int64_t)threadIdx.x * per;
+  const int64_t b1 = b0 + per < n ? b0 + per : n;
+  I s = 0;
+  for (int64_t i = b0; i < b1; ++i) s += v[i];
+  I t;
+  I run = block_excl_scan(s, sh, &t);  // ends with a barrier: every chunk sum is taken
+  for (int64_t i = b0; i < b1; ++i) {
+    const I x = v[i];
+    v[i] = run;
+    run += x;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += kThreads) out[i] = v[i];
+  if (threadIdx.x == 0 && total) *total = t;
+}
+
 }  // namespace
 
 int64_t scan_tmp_words(int64_t n) { return (n + kTileN - 1) / kTileN + 1; }
@@ -100,6 +134,16 @@ zq_status scan_impl(Ctx& c, const I* in, I* out, int64_t n, I* tmp, I* total) {
   cudaStream_t s = c.stream;
   if (n <= 0) {
     if (total) ZQ_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(I), s));
+    return ZQ_OK;
+  }
+  if (n <= one_block_max<I>()) {
+    const int smem = (int)(n * (int64_t)sizeof(I));
+    if (smem > 48 * 1024)
+      ZQ_CUDA_TRY(cudaFuncSetAttribute(k_scan_one_block<I>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOneBlockBytes));
+    time_begin(c, "scan");
+    k_scan_one_block<I><<<1, kThreads, smem, s>>>(in, n, out, total);
+    time_end(c, "scan");
+    ZQ_CUDA_TRY(cudaGetLastError());
     return ZQ_OK;
   }
   int64_t nb = (n + kTileN - 1) / kTileN;

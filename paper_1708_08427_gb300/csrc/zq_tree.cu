@@ -334,8 +334,12 @@ __global__ void __launch_bounds__(kThreads)
 k_bucket_scatter(const uint8_t* __restrict__ height, const int32_t* __restrict__ cl,
                  const int32_t* __restrict__ cr, int64_t nodes, int cut, int nb,
                  const int32_t* __restrict__ hist, int64_t nblk, int32_t* __restrict__ sid,
-                 int32_t* __restrict__ slot_of) {
+                 int32_t* __restrict__ slot_of, int32_t* __restrict__ bstart) {
   __shared__ int32_t wc[kBWarps][kMaxBuckets];
+  if (blockIdx.x == 0) {  // first slot of each bucket (the first block's start in it), then the end
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) bstart[b] = hist[(int64_t)b * nblk];
+    if (threadIdx.x == 0) bstart[nb] = (int32_t)nodes;
+  }
   for (int i = threadIdx.x; i < kBWarps * kMaxBuckets; i += blockDim.x) (&wc[0][0])[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -371,12 +375,6 @@ k_bucket_scatter(const uint8_t* __restrict__ height, const int32_t* __restrict__
   }
 }
 
-__global__ void k_bucket_starts(const int32_t* __restrict__ hist, int64_t nblk, int nb, int64_t nodes,
-                                int32_t* __restrict__ bstart) {
-  const int b = threadIdx.x;
-  if (b < nb) bstart[b] = hist[(int64_t)b * nblk];
-  if (b == nb) bstart[nb] = (int32_t)nodes;
-}
 
 // Per-slot data that depends on the tree and the slots only (it runs while
 // the segment schedule is still being made on its side stream).
@@ -405,11 +403,6 @@ __global__ void k_slot_records(int64_t nodes, const int32_t* __restrict__ sid, c
   srw[s] = prw[pos_of[sid[s]]];
 }
 
-__global__ void k_root_slots(int64_t m, const int32_t* __restrict__ root,
-                             const int32_t* __restrict__ slot_of, int32_t* __restrict__ root_slot) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < m) root_slot[j] = slot_of[root[j]];
-}
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
@@ -507,17 +500,11 @@ zq_status launch_schedules(Ctx& c) {
   if (st != ZQ_OK) return st;
   time_begin(c, "schedule");
   k_bucket_scatter<<<(unsigned)nblk, kThreads, 0, s>>>(c.height, c.cl, c.cr, c.nodes, c.cut, nb, hist, nblk,
-                                                      c.sid, c.slot_of);
-  time_end(c, "schedule");
-  time_begin(c, "schedule");
-  k_bucket_starts<<<1, 128, 0, s>>>(hist, nblk, nb, c.nodes, c.bstart);
+                                                      c.sid, c.slot_of, c.bstart);
   time_end(c, "schedule");
   time_begin(c, "schedule");
   k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.roff, c.cnt,
                                                    c.height, c.sc, c.sroff, c.scnt, c.sheight);
-  time_end(c, "schedule");
-  time_begin(c, "schedule");
-  k_root_slots<<<blocks(c.m), kThreads, 0, s>>>(c.m, c.root, c.slot_of, c.root_slot);
   time_end(c, "schedule");
   ZQ_CUDA_TRY(cudaStreamWaitEvent(s, c.join_ev[1], 0));  // the segment schedule (positions, prw)
   time_begin(c, "schedule");
