@@ -101,7 +101,7 @@ struct Ctx {
   int32_t* fused_bin_bodies = nullptr;  // [m]
   int32_t* bead_body = nullptr;  // [N] body of each bead / sorted position
   uint64_t* aabb = nullptr;      // [m * 6] ordered-int encoded lo[3], hi[3]
-  double* body_scale = nullptr;  // [m * 3] 1 / (hi - lo) per axis (0 if hi == lo)
+  double* body_scale = nullptr;  // [m * 3] 2^21 / (hi - lo) per axis (0 if hi == lo)
   double* count_tab = nullptr;   // [2 * kCountTab]: sqrt(n), 1/sqrt(n)
   float2* count_tab2 = nullptr;  // the same as double-single pairs
   int32_t* root = nullptr;       // [m] root node id
@@ -310,6 +310,57 @@ __device__ bool sort_by_height(int32_t n, Item item, HeightSort& S) {
   }
   __syncthreads();
   return true;
+}
+
+// Bisection keys (Sec. 2.1): q = floor((p - lo) / (hi - lo) * 2^21) per
+// axis, clamped to 2^21 - 1, in FP64 with correctly rounded subtraction and
+// division (the tree is bit-exact with the oracle's).
+__device__ __forceinline__ uint32_t quantise_exact(double p, double lo, double hi) {
+  if (!(hi > lo)) return 0u;
+  const double t = __ddiv_rn(__dsub_rn(p, lo), __dsub_rn(hi, lo));
+  const double s = floor(__dmul_rn(t, (double)(1u << kQBits)));
+  const double top = (double)((1u << kQBits) - 1);
+  return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
+}
+
+// The same value: the product with inv21 = 2^21 / (hi - lo) differs from
+// the correctly rounded quotient by a few ulps, so its floor is taken from
+// the bits of s when s is more than 2^-26 from an integer (integer
+// instructions only), and the exact formula is used otherwise.  The caller
+// has checked hi > lo (a flat axis quantises to 0).
+__device__ __forceinline__ uint32_t quantise_bits(double p, double lo, double hi, double inv21) {
+  const double s = __dmul_rn(__dsub_rn(p, lo), inv21);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if ((b >> 63) == 0 && e >= 0 && e <= 20) {
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int fbits = 52 - e;
+    const unsigned long long ip = M >> fbits;
+    const unsigned long long fr = M & ((1ull << fbits) - 1);
+    const unsigned long long margin = 1ull << (fbits - 26);
+    if (fr > margin && fr < (1ull << fbits) - margin && ip < (1ull << kQBits) - 1) return (uint32_t)ip;
+  } else if ((b >> 63) == 0 && e < 0 && e >= -26) {
+    // 2^-26 <= s < 1: floor 0 unless s is within 2^-26 of 1
+    if (s < 1.0 - 0x1p-26) return 0u;
+  }
+  return quantise_exact(p, lo, hi);
+}
+
+// Bit interleave: bit b of v to bit 3 b.
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t s = v & 0x1fffffull;
+  s = (s | (s << 32)) & 0x1f00000000ffffull;
+  s = (s | (s << 16)) & 0x1f0000ff0000ffull;
+  s = (s | (s << 8)) & 0x100f00f00f00f00full;
+  s = (s | (s << 4)) & 0x10c30c30c30c30c3ull;
+  s = (s | (s << 2)) & 0x1249249249249249ull;
+  return s;
+}
+
+// Key of a bead: z, then y, then x bit per octree level, most significant
+// first (the bisection order of Sec. 2.1).
+__device__ __forceinline__ uint64_t bead_key(uint32_t qx, uint32_t qy, uint32_t qz) {
+  return spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
 }
 
 // Orderable unsigned encoding of a double (for atomicMin/Max).

@@ -82,48 +82,6 @@ __device__ __forceinline__ int32_t residue_size(unsigned long long pk) {
   return 3 * ((unpack(pk, 13, 1) ^ 1u) + (unpack(pk, 27, 1) ^ 1u));
 }
 
-__device__ __forceinline__ uint32_t quantise_exact(double p, double lo, double hi) {
-  if (!(hi > lo)) return 0u;
-  const double t = __ddiv_rn(__dsub_rn(p, lo), __dsub_rn(hi, lo));
-  const double s = floor(__dmul_rn(t, (double)(1u << kQBits)));
-  const double top = (double)((1u << kQBits) - 1);
-  return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
-}
-
-// floor((p - lo) / (hi - lo) * 2^21) clamped, equal to quantise_exact: the
-// product with inv21 = 2^21 / (hi - lo) differs from the correctly rounded
-// quotient by a few ulps, so its floor is taken from the bits of s when s
-// is more than 2^-26 from an integer (integer instructions only), and the
-// exact formula is used otherwise.
-// The caller has checked hi > lo (a flat axis quantises to 0).
-__device__ __forceinline__ uint32_t quantise_bits(double p, double lo, double hi, double inv21) {
-  const double s = __dmul_rn(__dsub_rn(p, lo), inv21);
-  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  if ((b >> 63) == 0 && e >= 0 && e <= 20) {
-    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int fbits = 52 - e;
-    const unsigned long long ip = M >> fbits;
-    const unsigned long long fr = M & ((1ull << fbits) - 1);
-    const unsigned long long margin = 1ull << (fbits - 26);
-    if (fr > margin && fr < (1ull << fbits) - margin && ip < (1ull << kQBits) - 1) return (uint32_t)ip;
-  } else if ((b >> 63) == 0 && e < 0 && e >= -26) {
-    // 2^-26 <= s < 1: floor 0 unless s is within 2^-26 of 1
-    if (s < 1.0 - 0x1p-26) return 0u;
-  }
-  return quantise_exact(p, lo, hi);
-}
-
-__device__ __forceinline__ uint64_t spread3(uint32_t v) {
-  uint64_t s = v & 0x1fffffull;
-  s = (s | (s << 32)) & 0x1f00000000ffffull;
-  s = (s | (s << 16)) & 0x1f0000ff0000ffull;
-  s = (s | (s << 8)) & 0x100f00f00f00f00full;
-  s = (s | (s << 4)) & 0x10c30c30c30c30c3ull;
-  s = (s | (s << 2)) & 0x1249249249249249ull;
-  return s;
-}
-
 // Block-wide exclusive scan of one int per thread (THREADS a multiple of 32).
 template <int THREADS>
 __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
@@ -196,7 +154,7 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
       uint32_t q[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) q[c] = flat[c] ? 0u : quantise_bits(p[c], lo[c], hi[c], inv[c]);
-      keyA[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+      keyA[i] = bead_key(q[0], q[1], q[2]);
       idxA[i] = (uint16_t)i;
     }
   }

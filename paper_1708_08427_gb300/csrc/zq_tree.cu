@@ -129,47 +129,14 @@ __global__ void __launch_bounds__(kThreads) k_aabb(const double* __restrict__ x,
   if (bad) atomicOr(err, kErrNonFinite);
 }
 
-// Spread the 21 low bits of v to every third bit (bit b -> bit 3b).
-__device__ inline uint64_t spread3(uint32_t v) {
-  uint64_t s = v & 0x1fffffull;
-  s = (s | (s << 32)) & 0x1f00000000ffffull;
-  s = (s | (s << 16)) & 0x1f0000ff0000ffull;
-  s = (s | (s << 8)) & 0x100f00f00f00f00full;
-  s = (s | (s << 4)) & 0x10c30c30c30c30c3ull;
-  s = (s | (s << 2)) & 0x1249249249249249ull;
-  return s;
-}
-
-// q = min(floor((p - lo) / (hi - lo) * 2^21), 2^21 - 1); 0 when hi == lo.
-// Subtraction and division are IEEE correctly rounded; the product by 2^21
-// is exact, so the result matches any IEEE implementation of the formula.
-__device__ inline uint32_t quantise(double p, double lo, double hi) {
-  if (!(hi > lo)) return 0u;
-  double t = __ddiv_rn(__dsub_rn(p, lo), __dsub_rn(hi, lo));
-  double s = floor(__dmul_rn(t, (double)(1u << kQBits)));
-  const double top = (double)((1u << kQBits) - 1);
-  return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
-}
-
-// Same result as quantise() with the division replaced, in all but a
-// vanishing fraction of cases, by a product with 1 / (hi - lo): the two
-// quotients differ by a few ulps, so when t * 2^21 lies more than 2^-26
-// from an integer both floors agree; otherwise the exact formula is used.
-__device__ inline uint32_t quantise_fast(double p, double lo, double hi, double inv) {
-  if (!(hi > lo)) return 0u;
-  const double s = __dmul_rn(__dmul_rn(__dsub_rn(p, lo), inv), (double)(1u << kQBits));
-  const double f = floor(s);
-  const double r = s - f;
-  if (r > 0x1p-26 && r < 1.0 - 0x1p-26 && s < (double)((1u << kQBits) - 1)) return (uint32_t)f;
-  return quantise(p, lo, hi);
-}
-
+// Per body and axis: inv21 = 2^21 / (hi - lo) (0 for a flat axis), the
+// factor of quantise_bits (zq_internal.cuh).
 __global__ void k_body_scale(int64_t m, const unsigned long long* __restrict__ lo,
                              const unsigned long long* __restrict__ hi, double* __restrict__ scale) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * m) return;
   const double l = ord_decode(lo[t]), h = ord_decode(hi[t]);
-  scale[t] = h > l ? 1.0 / (h - l) : 0.0;
+  scale[t] = h > l ? (double)(1u << kQBits) / (h - l) : 0.0;
 }
 
 __global__ void k_count_table(double* __restrict__ tab) {
@@ -180,6 +147,8 @@ __global__ void k_count_table(double* __restrict__ tab) {
   tab[kCountTab + n] = n > 0 ? 1.0 / s : 0.0;
 }
 
+// Keys of the beads of bodies above kSmallSortMax (the per-body tree
+// kernels compute their own).
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, const int32_t* __restrict__ bead_body,
                        const int64_t* __restrict__ off, int64_t N,
@@ -193,9 +162,11 @@ __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ 
   uint32_t q[3];
   const double p[3] = {x[i], y[i], z[i]};
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-    q[a] = quantise_fast(p[a], ord_decode(lo[3 * j + a]), ord_decode(hi[3 * j + a]), scale[3 * j + a]);
-  key[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+  for (int a = 0; a < 3; ++a) {
+    const double l = ord_decode(lo[3 * j + a]), h = ord_decode(hi[3 * j + a]);
+    q[a] = h > l ? quantise_bits(p[a], l, h, scale[3 * j + a]) : 0u;
+  }
+  key[i] = bead_key(q[0], q[1], q[2]);
 }
 
 // Depth of the bisection separating sorted neighbours s and s+1 of a body:
@@ -435,7 +406,7 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z,
   unsigned long long* hi = lo + 3 * c.m;
   int32_t* err = c.counters + 2;
   // every body's bounding box in one pass over the coordinates (coalesced,
-  // and it leaves them in L2 for the key pass of the per-body kernels)
+  // and it leaves them in L2 for the key pass)
   ZQ_CUDA_TRY(cudaMemsetAsync(lo, 0xff, 3 * c.m * sizeof(uint64_t), s));
   ZQ_CUDA_TRY(cudaMemsetAsync(hi, 0x00, 3 * c.m * sizeof(uint64_t), s));
   time_begin(c, "aabb");
