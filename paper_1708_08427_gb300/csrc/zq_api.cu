@@ -164,9 +164,16 @@ zq_status zq_create(zq_ctx** ctx, int device, void* cuda_stream) {
     delete h;
     return ZQ_ECUDA;
   }
-  bool ok = cudaEventCreateWithFlags(&h->c.fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  // Side stream priorities: 0 runs zq_pipeline's downward sweep, which
+  // follows the transform build on the step's critical path (highest);
+  // 1 runs the early upward sweep beside the build's latency-bound upper
+  // heights (lowest); 2 and 3 the default.
+  int prio_low = 0, prio_high = 0;
+  bool ok = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->c.fork_ev, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < 4 && ok; ++i) {
-    ok = cudaStreamCreateWithFlags(&h->c.side[i], cudaStreamNonBlocking) == cudaSuccess &&
+    const int prio = i == 0 ? prio_high : (i == 1 ? prio_low : 0);
+    ok = cudaStreamCreateWithPriority(&h->c.side[i], cudaStreamNonBlocking, prio) == cudaSuccess &&
          cudaEventCreateWithFlags(&h->c.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
