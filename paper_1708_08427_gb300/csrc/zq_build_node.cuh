@@ -2,7 +2,9 @@
 // build (zq_build.cu) and the fused per-body step (zq_fused.cu).
 //
 // For a node p with children x (lower half) and y (upper half):
-//   n = n_x + n_y, centroid c_p = (n_x c_x + n_y c_y) / n,
+//   n = n_x + n_y, centroid c_p = (n_x c_x + n_y c_y) / n (evaluated as
+//       c_x - (n_y / n)(c_x - c_y): one FP64 fused multiply-add per axis
+//       beside the offset below),
 //   alpha = sqrt(n_x / n), beta = sqrt(n_y / n),
 //   K = sqrt(n_x n / n_y) R21 with R21 = [c_x - c_p]x, which equals
 //       sqrt(n_x n_y / n) [c_x - c_y]x  (c_x - c_p = (n_y / n)(c_x - c_y)),
@@ -148,11 +150,14 @@ __device__ __forceinline__ void geometry(const BuildArgs& a, const Child<R>& X, 
   const R sx = count_sqrt<R>(a, X.n), sy = count_sqrt<R>(a, Y.n), r = count_rsqrt<R>(a, X.n + Y.n);
   const int n = X.n + Y.n;
   const double rd = n < kCountTab ? __ldg(a.ctab + kCountTab + n) : ::rsqrt((double)n);
-  const double rn = rd * rd, nx = (double)X.n, ny = (double)Y.n;
+  const double wy = (double)Y.n * (rd * rd);  // n_y / n
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    g.cp[i] = (nx * X.c[i] + ny * Y.c[i]) * rn;
-    g.d[i] = Real<R>::from_double(X.c[i] - Y.c[i]);
+    // c_p = (n_x c_x + n_y c_y) / n = c_x - (n_y / n) d: the offset d is
+    // needed anyway, so the centroid takes one fused multiply-add
+    const double d = X.c[i] - Y.c[i];
+    g.cp[i] = fma(-wy, d, X.c[i]);
+    g.d[i] = Real<R>::from_double(d);
   }
   g.al = sx * r;
   g.be = sy * r;
@@ -165,8 +170,9 @@ __device__ __forceinline__ void geometry_pair(const Child<R>& X, const Child<R>&
   const R root_half = Real<R>::from_double(0.70710678118654757);  // sqrt(1/2), correctly rounded
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    g.cp[i] = (X.c[i] + Y.c[i]) * 0.5;
-    g.d[i] = Real<R>::from_double(X.c[i] - Y.c[i]);
+    const double d = X.c[i] - Y.c[i];
+    g.cp[i] = fma(-0.5, d, X.c[i]);  // (c_x + c_y) / 2
+    g.d[i] = Real<R>::from_double(d);
   }
   g.al = g.be = g.sk = root_half;
 }
