@@ -120,7 +120,6 @@ struct Ctx {
   int32_t* first = nullptr;      // [nodes] first sorted position
   int32_t* cnt = nullptr;        // [nodes] beads below
   uint8_t* height = nullptr;     // [nodes]
-  int32_t* flag = nullptr;       // [nodes] bottom-up arrival counters
   int32_t* roff = nullptr;       // [nodes] residue offsets
   int32_t* scan_tmp = nullptr;   // [nodes + blocks] scan workspace
   int32_t* counters = nullptr;   // [4]: spare, spare, err, spare

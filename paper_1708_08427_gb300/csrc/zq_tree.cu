@@ -6,9 +6,11 @@
 // 3. per-body sort by (key, local bead index)  [zq_sort.cu];
 // 4. LCP of neighbouring keys = depth of the bisection that separates them;
 // 5. bottom-up construction: a node's parent is the neighbouring split with
-//    the deeper (larger) LCP; the second child to arrive completes the
-//    parent (range, count, height, residue size 0/3/6 of Sec. 3) -- pruning
-//    of empty boxes and collapse of single-child chains are implicit;
+//    the deeper (larger) LCP; each child deposits its far range end and its
+//    height in the parent's 64-bit slot with one atomic exchange, and the
+//    second to arrive completes the parent (range, count, height, residue
+//    size 0/3/6 of Sec. 3) -- pruning of empty boxes and collapse of
+//    single-child chains are implicit;
 // 6. residue offsets by prefix sum over node ids (split-position order,
 //    bodies concatenated);
 // 7. the processing schedule: a stable bucket sort of the nodes by
@@ -196,7 +198,7 @@ __global__ void k_bottom_up(const int64_t* __restrict__ off, const int32_t* __re
                             int64_t N, const uint8_t* __restrict__ lcp, int32_t* __restrict__ cl,
                             int32_t* __restrict__ cr, int32_t* __restrict__ first,
                             int32_t* __restrict__ cnt, uint8_t* __restrict__ height,
-                            int32_t* __restrict__ flag, int32_t* __restrict__ res,
+                            unsigned long long* __restrict__ slot, int32_t* __restrict__ res,
                             int32_t* __restrict__ root) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N) return;
@@ -217,32 +219,28 @@ __global__ void k_bottom_up(const int64_t* __restrict__ off, const int32_t* __re
     if (l == 0) is_left = true;
     else if (r == n - 1) is_left = false;
     else is_left = lcp[nb + r] > lcp[nb + l - 1];
-    const int64_t q = nb + (is_left ? r : l - 1);
-    if (is_left) {
-      cl[q] = code;
-      first[q] = (int32_t)(o + l);
-    } else {
-      cr[q] = code;
-      cnt[q] = r;  // the parent's last local position, until completion
-    }
-    __threadfence();
-    if (atomicAdd(&flag[q], 1) == 0) break;  // the sibling completes q
-    __threadfence();
-    int32_t sib, lo_, hi_;
-    if (is_left) {
-      sib = __ldcg(&cr[q]);
-      lo_ = l;
-      hi_ = __ldcg(&cnt[q]);
-    } else {
-      sib = __ldcg(&cl[q]);
-      lo_ = __ldcg(&first[q]) - (int32_t)o;
-      hi_ = r;
-    }
-    const int32_t hs = is_leaf(sib) ? 0 : (int32_t)(*(volatile const uint8_t*)&height[sib]);
+    const int32_t g = is_left ? r : l - 1;
+    const int64_t q = nb + g;
+    if (is_left) cl[q] = code;  // each child enters its own code (read after the kernel)
+    else cr[q] = code;
+    // the deposit: this child's far range end and height; the second child
+    // to arrive completes q from it (the exchange carries the data, so no
+    // fence or second read is needed)
+    const unsigned long long mine = (1ull << 63) | ((unsigned long long)(uint32_t)(is_left ? l : r) << 8) |
+                                    (unsigned)h;
+    const unsigned long long other = atomicExch(&slot[q], mine);
+    if (other == 0ull) break;  // the sibling completes q
+    const int32_t end = (int32_t)((other >> 8) & 0x7fffffffull);
+    const int32_t hs = (int32_t)(other & 0xff);
+    const int32_t lo_ = is_left ? l : end;
+    const int32_t hi_ = is_left ? end : r;
+    // the sibling covers [g + 1, hi_] (right) or [lo_, g] (left): internal when longer than one bead
+    const bool sib_internal = is_left ? (hi_ > g + 1) : (lo_ < g);
     h = 1 + (h > hs ? h : hs);
     height[q] = (uint8_t)h;
     cnt[q] = hi_ - lo_ + 1;
-    res[q] = 3 * ((code >= 0) + (sib >= 0));
+    first[q] = (int32_t)(o + lo_);
+    res[q] = 3 * ((code >= 0) + (sib_internal ? 1 : 0));
     code = (int32_t)q;
     l = lo_;
     r = hi_;
@@ -430,10 +428,12 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z,
     time_begin(c, "lcp");
     k_lcp<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.skey, c.perm, c.lcp);
     time_end(c, "lcp");
-    ZQ_CUDA_TRY(cudaMemsetAsync(c.flag, 0, c.nodes * sizeof(int32_t), s));
+    // one 64-bit deposit slot per node (the radix sort's ping-pong keys, free now)
+    unsigned long long* slot = reinterpret_cast<unsigned long long*>(c.key_tmp);
+    ZQ_CUDA_TRY(cudaMemsetAsync(slot, 0, c.nodes * sizeof(unsigned long long), s));
     time_begin(c, "bottom_up");
     k_bottom_up<<<blocks(c.N), kThreads, 0, s>>>(c.off, c.bead_body, c.N, c.lcp, c.cl, c.cr, c.first,
-                                                 c.cnt, c.height, c.flag, c.roff, c.root);
+                                                 c.cnt, c.height, slot, c.roff, c.root);
     time_end(c, "bottom_up");
     ZQ_CUDA_TRY(cudaGetLastError());
   }
