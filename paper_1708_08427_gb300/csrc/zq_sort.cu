@@ -3,9 +3,14 @@
 // separated by their index bits).
 //
 // Bodies above kSmallSortMax beads (smaller ones are sorted inside the
-// per-body tree kernel, zq_smalltree.cu): stable LSD radix sort, 8 passes
-// of 8 bits over the 64-bit key; stability keeps equal keys in bead (=
-// index) order.
+// per-body tree kernel, zq_smalltree.cu): stable LSD radix sort, 4 passes
+// of 8 bits over the high 32 key bits (the first 10 2/3 octree levels);
+// stability keeps equal keys in bead (= index) order.  Then the runs of
+// beads that share their high 32 bits are sorted by the low bits: runs of
+// at most 32 by insertion, one thread each (k_sort_fixup); longer ones,
+// listed by the fix-up, by one thread block each with a stable LSD radix
+// sort over the low 32 bits in global memory (k_sort_runs), which takes any
+// run length and does nothing when no run is listed.
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -102,11 +107,145 @@ k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vi
   }
 }
 
+// Runs of equal high key halves in a body's sorted keys [0, n): each run
+// start p of length 2..32 is insertion-sorted by the full key (stable: the
+// run is in index order); longer runs are listed for k_sort_runs (start,
+// length; the end found by binary search on the sorted high halves).
+constexpr int kFixupMax = 32;
+
+__global__ void k_sort_fixup(uint64_t* __restrict__ key, int32_t* __restrict__ val, int64_t n,
+                             int2* __restrict__ runs, int32_t* __restrict__ nruns) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const uint32_t hk = (uint32_t)(key[p] >> 32);
+  if (p > 0 && (uint32_t)(key[p - 1] >> 32) == hk) return;  // not a run start
+  int64_t L = 1;
+  while (p + L < n && L <= kFixupMax && (uint32_t)(key[p + L] >> 32) == hk) ++L;
+  if (L == 1) return;
+  if (L > kFixupMax) {
+    int64_t lo = p + L, hi = n;  // first position past the run
+    while (lo < hi) {
+      const int64_t md = (lo + hi) >> 1;
+      if ((uint32_t)(key[md] >> 32) == hk) lo = md + 1; else hi = md;
+    }
+    const int32_t slot = atomicAdd(nruns, 1);
+    runs[slot] = make_int2((int32_t)p, (int32_t)(lo - p));
+    return;
+  }
+  for (int64_t u = p + 1; u < p + L; ++u) {
+    const uint64_t k = key[u];
+    const int32_t v = val[u];
+    int64_t w = u - 1;
+    while (w >= p && key[w] > k) {
+      key[w + 1] = key[w];
+      val[w + 1] = val[w];
+      --w;
+    }
+    key[w + 1] = k;
+    val[w + 1] = v;
+  }
+}
+
+// The listed long runs, one block per run: four stable LSD passes of 8 bits
+// over the low key half, in global memory between the run and the same
+// range of the scratch (tmpk, tmpv), a tile of blockDim keys at a time in
+// order (ranks within a warp by digit_peers, then warp by warp), so equal
+// digits keep their order.
+constexpr int kRunThreads = 1024;
+constexpr int kRunWarps = kRunThreads / 32;
+
+__global__ void __launch_bounds__(kRunThreads)
+k_sort_runs(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __restrict__ tmpk,
+            int32_t* __restrict__ tmpv, const int2* __restrict__ runs, const int32_t* __restrict__ nruns) {
+  __shared__ int32_t start[kDigits];
+  __shared__ int32_t wc[kRunWarps][kDigits];
+  const int nr = *nruns;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = blockIdx.x; r < nr; r += gridDim.x) {
+    const int2 run = runs[r];
+    const int64_t p = run.x, L = run.y;
+    uint64_t* kin = key + p;
+    int32_t* vin = val + p;
+    uint64_t* kout = tmpk + p;
+    int32_t* vout = tmpv + p;
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 8 * pass;
+      for (int d = threadIdx.x; d < kDigits; d += blockDim.x) start[d] = 0;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < L; i += blockDim.x) atomicAdd(&start[(kin[i] >> shift) & (kDigits - 1)], 1);
+      __syncthreads();
+      if (threadIdx.x < 32) {  // exclusive scan of the digit counts, 8 per lane
+        constexpr int kPer = kDigits / 32;
+        int32_t v[kPer], t = 0;
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+          v[e] = start[lane * kPer + e];
+          t += v[e];
+        }
+        int32_t inc = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t q = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += q;
+        }
+        int32_t run_ = inc - t;
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+          start[lane * kPer + e] = run_;
+          run_ += v[e];
+        }
+      }
+      __syncthreads();
+      for (int64_t base = 0; base < L; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool ok = i < L;
+        uint64_t k = 0;
+        int32_t v = 0;
+        int dg = kDigits + lane;
+        if (ok) {
+          k = kin[i];
+          v = vin[i];
+          dg = (int)((k >> shift) & (kDigits - 1));
+        }
+        for (int d = lane; d < kDigits; d += 32) wc[warp][d] = 0;
+        __syncwarp();
+        const unsigned peers = digit_peers(dg, ok);
+        if (ok && (peers & lt) == 0) wc[warp][dg] = __popc(peers);
+        __syncthreads();
+        for (int d = threadIdx.x; d < kDigits; d += blockDim.x) {  // warp-by-warp offsets of digit d
+          int32_t run_ = start[d];
+          for (int w = 0; w < kRunWarps; ++w) {
+            const int32_t c = wc[w][d];
+            wc[w][d] = run_;
+            run_ += c;
+          }
+          start[d] = run_;
+        }
+        __syncthreads();
+        if (ok) {
+          const int32_t pos = wc[warp][dg] + __popc(peers & lt);
+          kout[pos] = k;
+          vout[pos] = v;
+        }
+        __syncthreads();
+      }
+      uint64_t* tk = kin; kin = kout; kout = tk;
+      int32_t* tv = vin; vin = vout; vout = tv;
+      __syncthreads();
+    }
+    // four passes: the sorted run is back in key / val
+  }
+}
+
 }  // namespace
 
+// The histogram and its scan scratch, then 2 words of run count (aligned),
+// then the long-run list (an int2 per possible run start).
 int64_t sort_hist_words(int64_t n_max) {
   const int64_t nblk = (n_max + kTile - 1) / kTile;
-  return kDigits * nblk + scan_tmp_words(kDigits * nblk);
+  const int64_t w = kDigits * nblk + scan_tmp_words(kDigits * nblk);
+  return ((w + 1) & ~(int64_t)1) + 2 + 2 * (n_max + 1);
 }
 
 zq_status launch_sort(Ctx& c) {
@@ -116,12 +255,12 @@ zq_status launch_sort(Ctx& c) {
     int64_t nblk = (n + kTile - 1) / kTile;
     int32_t* hist = c.sort_hist;
     int32_t* tmp = c.sort_hist + kDigits * nblk;
-    for (int pass = 0; pass < 8; ++pass) {
+    for (int pass = 4; pass < 8; ++pass) {  // the high 32 key bits
       const uint64_t* kin;
       const int32_t* vin;
       uint64_t* kout;
       int32_t* vout;
-      if (pass == 0) {
+      if (pass == 4) {
         kin = c.key + o; vin = nullptr; kout = c.key_tmp + o; vout = c.perm_tmp + o;
       } else if (pass & 1) {
         kin = c.key_tmp + o; vin = c.perm_tmp + o; kout = c.skey + o; vout = c.perm + o;
@@ -140,6 +279,19 @@ zq_status launch_sort(Ctx& c) {
       time_end(c, "sort_radix");
       ZQ_CUDA_TRY(cudaGetLastError());
     }
+    // runs of equal high halves, sorted by the low bits (the list of long
+    // runs and its count live after the histogram in the sort scratch)
+    int2* runs = reinterpret_cast<int2*>(c.sort_hist + sort_hist_words(n) - 2 * (n + 1));
+    int32_t* nruns = c.sort_hist + sort_hist_words(n) - 2 * (n + 1) - 2;
+    ZQ_CUDA_TRY(cudaMemsetAsync(nruns, 0, sizeof(int32_t), s));
+    time_begin(c, "sort_fixup");
+    k_sort_fixup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.skey + o, c.perm + o, n, runs, nruns);
+    time_end(c, "sort_fixup");
+    time_begin(c, "sort_runs");
+    k_sort_runs<<<(unsigned)c.num_sms, kRunThreads, 0, s>>>(c.skey + o, c.perm + o, c.key_tmp + o, c.perm_tmp + o,
+                                                          runs, nruns);
+    time_end(c, "sort_runs");
+    ZQ_CUDA_TRY(cudaGetLastError());
   }
   return ZQ_OK;
 }

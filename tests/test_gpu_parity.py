@@ -245,6 +245,32 @@ def test_size_class_and_segment_boundaries():
     check_apply(ctx, bt, np.float32, seed=11)
 
 
+def test_large_body_runs_of_shared_high_bits():
+    """A body above the per-block sort limit whose beads share their high 32
+    key bits in runs of every kind the device sort handles after its four
+    high passes: pairs and short runs (insertion fix-up), a run of 40 and a
+    run of 1500 beads spread over a few finest cells (one thread block,
+    LSD passes over the low key bits, the longer one over two tiles), and a
+    run of 300 beads in one finest cell (equal keys: index order).  The tree
+    is bit-exact with the oracle's; the products are held to the
+    conditioning of the clusters (as in test_tight_clusters_sort_exactly)."""
+    rng = np.random.default_rng(77)
+    spread = rng.uniform(-3, 3, (9000, 3))
+    pairs = np.repeat(rng.uniform(-3, 3, (20, 3)), 2, axis=0) + 1e-8 * rng.uniform(0, 1, (40, 3))
+    pts = np.r_[spread, pairs,
+                0.5 + 1e-5 * rng.uniform(0, 1, (40, 3)),
+                -1.0 + 1e-5 * rng.uniform(0, 1, (1500, 3)),
+                2.0 + 1e-9 * rng.uniform(0, 1, (300, 3))]
+    pts = pts[rng.permutation(len(pts))]
+    bt = _batch_from_points([pts])
+    assert bt.N > 8192
+    ctx, _ = make_ctx(bt, cut=8)
+    bodies = oracle_bodies(bt)
+    check_tree(ctx, bt, bodies)
+    tol = max(TOL[np.float64], 8 * 2 * 3.0 * 2.0 ** -53 / 1e-9)
+    check_apply(ctx, bt, np.float64, tol=tol)
+
+
 def test_large_body_radix_sort_path():
     """A body above the per-block sort limit (device radix sort), with many
     nodes above the level cut (one block for the whole body's top)."""
