@@ -256,6 +256,17 @@ __device__ void node_case1(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
   store<R, 12>(a, s, rw, rec, g.cp, L);
 }
 
+// Pairwise sum of v[B..E), all of one sign.
+template <class R, int B, int E>
+__device__ __forceinline__ R sum_same(const R* v) {
+  if constexpr (E - B == 1) {
+    return v[B];
+  } else {
+    constexpr int kMid = (B + E) / 2;
+    return Real<R>::add_same(sum_same<R, B, kMid>(v), sum_same<R, kMid, E>(v));
+  }
+}
+
 // One Householder step (LAPACK dlarfg convention) on a column whose
 // possibly nonzero entries below the diagonal are x[0..M-1]; al is the
 // diagonal entry.  Returns tau (0: no reflection) and scales x into the
@@ -263,20 +274,24 @@ __device__ void node_case1(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
 template <class R, int M>
 __device__ __forceinline__ R reflector(R& al, R (&x)[M]) {
   using RT = Real<R>;
-  R xn2 = x[0] * x[0];
+  // the sums here add terms of one sign (squares; 1 and |al| / norm; al and
+  // -be, which has al's sign), so they take the cheaper one-sign sum; the
+  // squares in a pairwise tree
+  R sq[M];
 #pragma unroll
-  for (int i = 1; i < M; ++i) xn2 = xn2 + x[i] * x[i];
+  for (int i = 0; i < M; ++i) sq[i] = RT::sqr(x[i]);
+  const R xn2 = sum_same<R, 0, M>(sq);
   if (RT::is_zero(xn2)) {
 #pragma unroll
     for (int i = 0; i < M; ++i) x[i] = RT::from_float(0.0f);
     return RT::from_float(0.0f);
   }
-  const R n2 = al * al + xn2;
+  const R n2 = RT::add_same(RT::sqr(al), xn2);
   const R rnorm = RT::rsqrt(n2);
   const R norm = n2 * rnorm;
   const R be = RT::ge_zero(al) ? -norm : norm;
-  const R tau = RT::from_float(1.0f) + RT::abs(al) * rnorm;  // = (be - al) / be
-  const R rden = RT::rcp(al - be);
+  const R tau = RT::add_same(RT::from_float(1.0f), RT::abs(al) * rnorm);  // = (be - al) / be
+  const R rden = RT::rcp(RT::add_same(al, -be));
 #pragma unroll
   for (int i = 0; i < M; ++i) x[i] = x[i] * rden;
   al = be;
