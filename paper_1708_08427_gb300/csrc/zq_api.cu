@@ -28,7 +28,7 @@ zq_status grow(T** p, int64_t count) {
 void free_all(Ctx& c) {
   void* ps[] = {c.off, c.small_d, c.fused_bin_start, c.fused_bin_bodies, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
-                c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc, c.sroff, c.scnt,
+                c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc,
                 c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage, c.ord,
                 c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.seg_r, c.topv,
                 c.top_off, c.nseg, c.srw, c.xblk};
@@ -96,8 +96,6 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.sid, nodes));
     ZQ_TRY(grow(&c.slot_of, nodes));
     ZQ_TRY(grow(&c.sc, nodes));
-    ZQ_TRY(grow(&c.sroff, nodes));
-    ZQ_TRY(grow(&c.scnt, nodes));
     ZQ_TRY(grow(&c.sheight, nodes));
     ZQ_TRY(grow(&c.bstart, zq::kMaxBuckets + 1));
     ZQ_TRY(grow(&c.bhist, zq::bucket_hist_words(nodes)));

@@ -60,13 +60,13 @@ __global__ void __launch_bounds__(kThreads) k_build_tail(BuildArgs a) {
     if (sorted) {
       for (int32_t k = S.hs[h] + threadIdx.x; k < S.hs[h + 1]; k += blockDim.x) {
         const int32_t s = S.ids[k];
-        const int2 cc = a.sc[s];
+        const int4 cc = a.sc[s];
         build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
       }
     } else {
       for (int32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
         if (sh[s] != h) continue;
-        const int2 cc = a.sc[s];
+        const int4 cc = a.sc[s];
         build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
       }
     }
@@ -134,13 +134,13 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_build_tail_warp(BuildArgs a
       const int32_t k0 = h == hmin ? 0 : hs[warp][h - 1], k1 = hs[warp][h];
       for (int32_t k = k0 + lane; k < k1; k += 32) {
         const int32_t s = ids[warp][k];
-        const int2 cc = a.sc[s];
+        const int4 cc = a.sc[s];
         build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
       }
     } else {
       for (int32_t s = lo + lane; s < hi; s += 32) {
         if (sh[s] != h) continue;
-        const int2 cc = a.sc[s];
+        const int4 cc = a.sc[s];
         build_slot<R>(a, s, (cc.x >= 0) + (cc.y >= 0), 4 * (int64_t)(uint32_t)a.srw[s]);
       }
     }
@@ -196,7 +196,7 @@ zq_status launch_build(Ctx& c, const double* x, const double* y, const double* z
                        const std::function<zq_status()>& after_levels) {
   BuildArgs a;
   a.x = x; a.y = y; a.z = z;
-  a.off = c.off; a.perm = c.perm; a.sc = c.sc; a.scnt = c.scnt; a.sheight = c.sheight; a.sid = c.sid;
+  a.off = c.off; a.perm = nullptr; a.sc = c.sc; a.cnt = nullptr; a.sheight = c.sheight; a.sid = c.sid;
   a.bstart = c.bstart; a.srw = c.srw; a.cut = c.cut;
   a.ctab = c.count_tab;
   a.ctab2 = c.count_tab2;

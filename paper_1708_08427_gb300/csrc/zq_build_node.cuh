@@ -38,8 +38,8 @@
 // FP64 from FP64 coordinates (cancellation between nearby absolute
 // positions needs the full 53 bits); K, T22 and the reflections use the
 // chosen type.  A slot's state: centroid (3 doubles), T22 (6 values of the
-// chosen type, 8 bytes each).  The state and the counts are indexed by the
-// caller's node numbering (a slot of the level schedule, or a node id).
+// chosen type, 8 bytes each).  The state is indexed by the caller's node
+// numbering (a slot of the level schedule, or a node id).
 #pragma once
 
 #include "zq_internal.cuh"
@@ -54,9 +54,9 @@ struct BuildArgs {
   const double* y;
   const double* z;
   const int64_t* off;
-  const int32_t* perm;
-  const int2* sc;
-  const int32_t* scnt;
+  const int32_t* perm;  // tree position -> bead (the fused step's leaf lookup)
+  const int4* sc;       // per slot: children (x, y, n_x, n_y), see kids_by_id
+  const int32_t* cnt;   // bead counts by node id (the fused step's child lookup)
   const uint8_t* sheight;
   const int32_t* sid;
   const int32_t* bstart;
@@ -77,9 +77,19 @@ struct Child {
   R L[6];       // packed lower triangle (L00, L10, L11, L20, L21, L22)
 };
 
+// A node's children are passed as (x, y, n_x, n_y): x, y >= 0 index a
+// child's state, x, y < 0 are leaves given as -1 - the bead's coordinate
+// index; n_x, n_y are the children's bead counts.  Every load a node needs
+// (state, count table, a leaf's coordinates) depends on these four words
+// only, so they issue together.
+__device__ __forceinline__ int4 kids_by_id(const BuildArgs& a, int32_t l, int32_t r) {
+  return make_int4(l >= 0 ? l : -1 - a.perm[leaf_pos(l)], r >= 0 ? r : -1 - a.perm[leaf_pos(r)],
+                   l >= 0 ? a.cnt[l] : 1, r >= 0 ? a.cnt[r] : 1);
+}
+
 template <class R>
 __device__ __forceinline__ void load_leaf(const BuildArgs& a, int32_t code, Child<R>& ch) {
-  const int32_t i = a.perm[leaf_pos(code)];
+  const int32_t i = -1 - code;
   ch.n = 1;
   ch.c[0] = a.x[i];
   ch.c[1] = a.y[i];
@@ -105,9 +115,9 @@ __device__ __forceinline__ R from_word(double d) {
 }
 
 template <class R>
-__device__ __forceinline__ void load_node(const BuildArgs& a, int32_t slot, Child<R>& ch) {
+__device__ __forceinline__ void load_node(const BuildArgs& a, int32_t slot, int n, Child<R>& ch) {
   const double2* s = reinterpret_cast<const double2*>(reinterpret_cast<const double*>(a.st) + (int64_t)slot * kState);
-  ch.n = a.scnt[slot];
+  ch.n = n;
   double w[10];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
@@ -206,7 +216,7 @@ __device__ __forceinline__ void store(const BuildArgs& a, int64_t slot, int64_t 
 
 // ------------------------------------------------------------ Case I
 template <class R>
-__device__ void node_case1(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
+__device__ void node_case1(const BuildArgs& a, int64_t s, int4 cc, int64_t rw) {
   using RT = Real<R>;
   Child<R> X, Y;
   load_leaf(a, cc.x, X);
@@ -333,12 +343,12 @@ __device__ __forceinline__ void finish_lq(const BuildArgs& a, int lim, R& A00, R
 // ------------------------------------------------- k = 6 (Case II)
 // A rows: 0-2 = T22_c^T of the internal child, 3-5 = K^T.
 template <class R>
-__device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
+__device__ void node_hh6(const BuildArgs& a, int64_t s, int4 cc, int64_t rw) {
   using RT = Real<R>;
   Child<R> X, Y;
   const bool xi = cc.x >= 0;
-  if (xi) { load_node(a, cc.x, X); load_leaf(a, cc.y, Y); }
-  else { load_leaf(a, cc.x, X); load_node(a, cc.y, Y); }
+  if (xi) { load_node(a, cc.x, cc.z, X); load_leaf(a, cc.y, Y); }
+  else { load_leaf(a, cc.x, X); load_node(a, cc.y, cc.w, Y); }
   Geo<R> g;
   geometry(a, X, Y, g);
   const R* Lc = xi ? X.L : Y.L;
@@ -394,11 +404,11 @@ __device__ void node_hh6(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
 // ------------------------------------------------- k = 9 (general)
 // A rows: 0-2 = T22_x^T, 3-5 = T22_y^T, 6-8 = K^T.
 template <class R>
-__device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
+__device__ void node_hh9(const BuildArgs& a, int64_t s, int4 cc, int64_t rw) {
   using RT = Real<R>;
   Child<R> X, Y;
-  load_node(a, cc.x, X);
-  load_node(a, cc.y, Y);
+  load_node(a, cc.x, cc.z, X);
+  load_node(a, cc.y, cc.w, Y);
   Geo<R> g;
   geometry(a, X, Y, g);
   const R zero = RT::from_float(0.0f);
@@ -458,7 +468,7 @@ __device__ void node_hh9(const BuildArgs& a, int64_t s, int2 cc, int64_t rw) {
 
 template <class R>
 __device__ __forceinline__ void build_slot(const BuildArgs& a, int64_t s, int type, int64_t rw) {
-  const int2 cc = a.sc[s];
+  const int4 cc = a.sc[s];
   if (type == 0) node_case1<R>(a, s, cc, rw);
   else if (type == 1) node_hh6<R>(a, s, cc, rw);
   else node_hh9<R>(a, s, cc, rw);

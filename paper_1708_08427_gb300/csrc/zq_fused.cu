@@ -219,9 +219,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_fused_step(FusedArgs<T> a) {
         const int2 cc = make_int2(a.cl[q], a.cr[q]);
         const int type = (cc.x >= 0) + (cc.y >= 0);
         const int64_t rw = q * kRecMax;
-        if (type == 0) node_case1<R>(a.b, q, cc, rw);
-        else if (type == 1) node_hh6<R>(a.b, q, cc, rw);
-        else node_hh9<R>(a.b, q, cc, rw);
+        const int4 kids = kids_by_id(a.b, cc.x, cc.y);
+        if (type == 0) node_case1<R>(a.b, q, kids, rw);
+        else if (type == 1) node_hh6<R>(a.b, q, kids, rw);
+        else node_hh9<R>(a.b, q, kids, rw);
         if (a.v) up_step(a, q, cc, type);
       }
       __syncthreads();
@@ -263,7 +264,7 @@ zq_status launch_fused_step(Ctx& c, zq_prec prec, const double* x, const double*
   if (!fused_step_possible(c)) return ZQ_ESTATE;
   BuildArgs b;
   b.x = x; b.y = y; b.z = z;
-  b.off = c.off; b.perm = c.perm; b.sc = nullptr; b.scnt = c.cnt; b.sheight = nullptr; b.sid = nullptr;
+  b.off = c.off; b.perm = c.perm; b.sc = nullptr; b.cnt = c.cnt; b.sheight = nullptr; b.sid = nullptr;
   b.bstart = nullptr; b.srw = nullptr; b.cut = c.cut;
   b.ctab = c.count_tab;
   b.ctab2 = c.count_tab2;

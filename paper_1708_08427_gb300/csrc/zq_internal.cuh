@@ -126,9 +126,8 @@ struct Ctx {
   // schedule, indexed by slot (the processing order; see kDefaultCut)
   int32_t* sid = nullptr;        // [nodes] slot -> node id
   int32_t* slot_of = nullptr;    // [nodes] node id -> slot
-  int2* sc = nullptr;            // [nodes] child codes: >= 0 child slot, < 0 leaf
-  int32_t* sroff = nullptr;      // [nodes] residue offset
-  int32_t* scnt = nullptr;       // [nodes] beads below
+  int4* sc = nullptr;            // [nodes] children: (x, y, n_x, n_y); x, y >= 0 child
+                                 // slot, < 0 leaf: -1 - its bead's coordinate index
   uint8_t* sheight = nullptr;    // [nodes] height
   int32_t* bstart = nullptr;     // [kMaxBuckets + 1] first slot of each bucket
   int32_t* bhist = nullptr;      // bucket-sort histograms

@@ -346,20 +346,21 @@ k_bucket_scatter(const uint8_t* __restrict__ height, const int32_t* __restrict__
 
 
 // Per-slot data that depends on the tree and the slots only (it runs while
-// the segment schedule is still being made on its side stream).
+// the segment schedule is still being made on its side stream).  Each slot
+// gets its children with their bead counts, and a leaf child as the index
+// of its bead's coordinates: the build then reads a child's state, its
+// count-table entries and a leaf's coordinates in one round of loads.
 __global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
                             const int32_t* __restrict__ slot_of, const int32_t* __restrict__ cl,
-                            const int32_t* __restrict__ cr, const int32_t* __restrict__ roff,
+                            const int32_t* __restrict__ cr, const int32_t* __restrict__ perm,
                             const int32_t* __restrict__ cnt, const uint8_t* __restrict__ height,
-                            int2* __restrict__ sc, int32_t* __restrict__ sroff,
-                            int32_t* __restrict__ scnt, uint8_t* __restrict__ sheight) {
+                            int4* __restrict__ sc, uint8_t* __restrict__ sheight) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nodes) return;
   const int32_t q = sid[s];
   const int32_t a = cl[q], b = cr[q];
-  sc[s] = make_int2(a >= 0 ? slot_of[a] : a, b >= 0 ? slot_of[b] : b);
-  sroff[s] = roff[q];
-  scnt[s] = cnt[q];
+  sc[s] = make_int4(a >= 0 ? slot_of[a] : -1 - perm[leaf_pos(a)], b >= 0 ? slot_of[b] : -1 - perm[leaf_pos(b)],
+                    a >= 0 ? cnt[a] : 1, b >= 0 ? cnt[b] : 1);
   sheight[s] = height[q];
 }
 
@@ -474,8 +475,8 @@ zq_status launch_schedules(Ctx& c) {
                                                       c.sid, c.slot_of, c.bstart);
   time_end(c, "schedule");
   time_begin(c, "schedule");
-  k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.roff, c.cnt,
-                                                   c.height, c.sc, c.sroff, c.scnt, c.sheight);
+  k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.perm, c.cnt,
+                                                   c.height, c.sc, c.sheight);
   time_end(c, "schedule");
   ZQ_CUDA_TRY(cudaStreamWaitEvent(s, c.join_ev[1], 0));  // the segment schedule (positions, prw)
   time_begin(c, "schedule");
