@@ -26,7 +26,7 @@ zq_status grow(T** p, int64_t count) {
 }
 
 void free_all(Ctx& c) {
-  void* ps[] = {c.off, c.small_d, c.fused_bin_start, c.fused_bin_bodies, c.bead_body, c.aabb, c.body_scale, c.count_tab, c.count_tab2, c.root, c.key, c.skey, c.perm,
+  void* ps[] = {c.off, c.small_d, c.fused_bin_start, c.fused_bin_bodies, c.bead_body, c.aabb, c.body_q, c.count_tab, c.count_tab2, c.root, c.key, c.skey, c.perm,
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc,
                 c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage, c.ord,
@@ -71,7 +71,7 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.fused_bin_bodies, m));
     ZQ_TRY(grow(&c.bead_body, N));
     ZQ_TRY(grow(&c.aabb, 6 * m));
-    ZQ_TRY(grow(&c.body_scale, 3 * m));
+    ZQ_TRY(grow(&c.body_q, 3 * m));
     ZQ_TRY(grow(&c.root, m));
     ZQ_TRY(grow(&c.key, N));
     ZQ_TRY(grow(&c.skey, N));

@@ -64,6 +64,8 @@ constexpr int kCountTab = 1 << 16;
 constexpr int kErrNonFinite = 1;
 constexpr int kErrDegenerate = 2;
 
+struct AxisQuant;  // quantiser constants of one body and axis (below)
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -101,7 +103,7 @@ struct Ctx {
   int32_t* fused_bin_bodies = nullptr;  // [m]
   int32_t* bead_body = nullptr;  // [N] body of each bead / sorted position
   uint64_t* aabb = nullptr;      // [m * 6] ordered-int encoded lo[3], hi[3]
-  double* body_scale = nullptr;  // [m * 3] 2^21 / (hi - lo) per axis (0 if hi == lo)
+  AxisQuant* body_q = nullptr;   // [m * 3] quantiser constants per axis (bodies above kSmallSortMax)
   double* count_tab = nullptr;   // [2 * kCountTab]: sqrt(n), 1/sqrt(n)
   float2* count_tab2 = nullptr;  // the same as double-single pairs
   int32_t* root = nullptr;       // [m] root node id
@@ -321,25 +323,61 @@ __device__ __forceinline__ uint32_t quantise_exact(double p, double lo, double h
   return s >= top ? ((1u << kQBits) - 1) : (uint32_t)s;
 }
 
-// The same value: the product with inv21 = 2^21 / (hi - lo) differs from
-// the correctly rounded quotient by a few ulps, so its floor is taken from
-// the bits of s when s is more than 2^-26 from an integer (integer
-// instructions only), and the exact formula is used otherwise.  The caller
-// has checked hi > lo (a flat axis quantises to 0).
-__device__ __forceinline__ uint32_t quantise_bits(double p, double lo, double hi, double inv21) {
-  const double s = __dmul_rn(__dsub_rn(p, lo), inv21);
-  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+// The quantiser's constants for one body and axis.  The scaled coordinate
+// p s + c (s = 2^21 / (hi - lo), c = -lo s) is one FP64 fused multiply-add;
+// it differs from 2^21 times quantise_exact's quotient by less than
+//   2^21 (3 + 3) 2^-53 + |lo| s 2^-53
+// (the roundings of hi - lo, s, c and the fused multiply-add, and of the
+// exact formula's subtraction and division; the second term from c), so
+// its floor is the exact formula's whenever it lies farther than
+// B = 2^-27 + |lo| s 2^-51 (the bound with a factor of 4 to spare) from
+// every integer.  beta is the exponent with B < 2^-beta; -1 marks a flat
+// axis (every bead quantises to 0), 0 a body so small against its
+// coordinates that only the exact formula is used.
+struct AxisQuant {
+  double s, c;
+  int beta;
+};
+
+__device__ __forceinline__ AxisQuant axis_quant(double lo, double hi) {
+  AxisQuant q;
+  if (!(hi > lo)) {
+    q.s = 0.0;
+    q.c = 0.0;
+    q.beta = -1;
+    return q;
+  }
+  q.s = (double)(1u << kQBits) / (hi - lo);
+  q.c = __dmul_rn(-lo, q.s);
+  const double B = 0x1p-27 + fabs(lo) * q.s * 0x1p-51;
+  const int beta = -(ilogb(B) + 1);
+  q.beta = beta > 0 ? beta : 0;
+  return q;
+}
+
+// quantise_exact(p, lo, hi) for a body whose axis is not flat (q.beta >=
+// 0): the floor is read from the bits of p s + c (integer instructions
+// only) unless that value lies within 2^-beta of an integer, is negative,
+// or reaches the top cell; those beads take the exact formula.
+__device__ __forceinline__ uint32_t quantise_fma(double p, const AxisQuant& q, double lo, double hi) {
+  const double v = __fma_rn(p, q.s, q.c);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  if ((b >> 63) == 0 && e >= 0 && e <= 20) {
+  const int beta = q.beta;
+  if ((b >> 63) == 0 && beta > 0) {
     const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int fbits = 52 - e;
-    const unsigned long long ip = M >> fbits;
-    const unsigned long long fr = M & ((1ull << fbits) - 1);
-    const unsigned long long margin = 1ull << (fbits - 26);
-    if (fr > margin && fr < (1ull << fbits) - margin && ip < (1ull << kQBits) - 1) return (uint32_t)ip;
-  } else if ((b >> 63) == 0 && e < 0 && e >= -26) {
-    // 2^-26 <= s < 1: floor 0 unless s is within 2^-26 of 1
-    if (s < 1.0 - 0x1p-26) return 0u;
+    if (e >= 0 && e <= 20) {
+      // v = M 2^(e - 52): integer part and fraction in units of 2^(e - 52)
+      const int fbits = 52 - e;
+      const unsigned long long ip = M >> fbits;
+      const unsigned long long fr = M & ((1ull << fbits) - 1);
+      const unsigned long long margin = fbits > beta ? 1ull << (fbits - beta) : 1ull;
+      if (fr > margin && fr < (1ull << fbits) - margin && ip < (1ull << kQBits) - 1) return (uint32_t)ip;
+    } else if (e < 0 && e >= -beta) {
+      // 2^-beta <= v < 1: the floor is 0 unless v is within 2^-beta of 1
+      // (for v in [1/2, 1), v = M 2^-53)
+      if (e <= -2 || (1ull << 53) - M >= (1ull << (53 - beta))) return 0u;
+    }
   }
   return quantise_exact(p, lo, hi);
 }

@@ -113,7 +113,7 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32
 }
 
 template <int MAXN, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_small_tree(SmallTreeArgs a) {
   constexpr int NW = THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* keyA = reinterpret_cast<uint64_t*>(smem);
@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
   uint16_t* idxB = idxA + MAXN;
   int32_t* whist = reinterpret_cast<int32_t*>(idxB + MAXN);  // [NW][256]
   __shared__ int32_t sh[33];
-  __shared__ double lim[9];  // lo[3], hi[3], 2^21 / (hi - lo)[3]
+  __shared__ double lim[6];  // lo[3], hi[3]
+  __shared__ AxisQuant aq[3];
 
   const int32_t j = a.bodies[blockIdx.x];
   const int64_t o = a.off[j];
@@ -135,25 +136,21 @@ __global__ void __launch_bounds__(THREADS) k_small_tree(SmallTreeArgs a) {
     const double l = ord_decode(a.lo[3 * j + tid]), h = ord_decode(a.hi[3 * j + tid]);
     lim[tid] = l;
     lim[3 + tid] = h;
-    lim[6 + tid] = h > l ? (double)(1u << kQBits) / (h - l) : 0.0;
+    aq[tid] = axis_quant(l, h);
   }
   __syncthreads();
 
-  // ---- 2. keys
+  // ---- 2. keys: one FP64 fused multiply-add per axis (the FP64 pipe runs
+  // at 1/64 of the FP32 rate here, and every block of a launch starts with
+  // this loop); the few beads near a cell boundary take the exact formula
   {
-    // per-axis constants in registers; FP64 is 1/64 rate here, so the
-    // flat-axis test is made once, not per bead
-    const double lo[3] = {lim[0], lim[1], lim[2]}, hi[3] = {lim[3], lim[4], lim[5]};
-    const double inv[3] = {lim[6], lim[7], lim[8]};
-    bool flat[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) flat[c] = !(hi[c] > lo[c]);
+    const AxisQuant Q[3] = {aq[0], aq[1], aq[2]};
 #pragma unroll 4
     for (int i = tid; i < n; i += THREADS) {
       const double p[3] = {a.x[o + i], a.y[o + i], a.z[o + i]};
       uint32_t q[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) q[c] = flat[c] ? 0u : quantise_bits(p[c], lo[c], hi[c], inv[c]);
+      for (int c = 0; c < 3; ++c) q[c] = Q[c].beta < 0 ? 0u : quantise_fma(p[c], Q[c], lim[c], lim[3 + c]);
       keyA[i] = bead_key(q[0], q[1], q[2]);
       idxA[i] = (uint16_t)i;
     }

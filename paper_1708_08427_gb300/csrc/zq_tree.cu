@@ -131,14 +131,12 @@ __global__ void __launch_bounds__(kThreads) k_aabb(const double* __restrict__ x,
   if (bad) atomicOr(err, kErrNonFinite);
 }
 
-// Per body and axis: inv21 = 2^21 / (hi - lo) (0 for a flat axis), the
-// factor of quantise_bits (zq_internal.cuh).
+// Per body and axis: the quantiser's constants (axis_quant, zq_internal.cuh).
 __global__ void k_body_scale(int64_t m, const unsigned long long* __restrict__ lo,
-                             const unsigned long long* __restrict__ hi, double* __restrict__ scale) {
+                             const unsigned long long* __restrict__ hi, AxisQuant* __restrict__ q) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * m) return;
-  const double l = ord_decode(lo[t]), h = ord_decode(hi[t]);
-  scale[t] = h > l ? (double)(1u << kQBits) / (h - l) : 0.0;
+  q[t] = axis_quant(ord_decode(lo[t]), ord_decode(hi[t]));
 }
 
 __global__ void k_count_table(double* __restrict__ tab) {
@@ -155,7 +153,7 @@ __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ 
                        const double* __restrict__ z, const int32_t* __restrict__ bead_body,
                        const int64_t* __restrict__ off, int64_t N,
                        const unsigned long long* __restrict__ lo,
-                       const unsigned long long* __restrict__ hi, const double* __restrict__ scale,
+                       const unsigned long long* __restrict__ hi, const AxisQuant* __restrict__ bq,
                        uint64_t* __restrict__ key) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -165,8 +163,8 @@ __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ 
   const double p[3] = {x[i], y[i], z[i]};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double l = ord_decode(lo[3 * j + a]), h = ord_decode(hi[3 * j + a]);
-    q[a] = h > l ? quantise_bits(p[a], l, h, scale[3 * j + a]) : 0u;
+    const AxisQuant aq = bq[3 * j + a];
+    q[a] = aq.beta < 0 ? 0u : quantise_fma(p[a], aq, ord_decode(lo[3 * j + a]), ord_decode(hi[3 * j + a]));
   }
   key[i] = bead_key(q[0], q[1], q[2]);
 }
@@ -418,10 +416,10 @@ zq_status launch_tree(Ctx& c, const double* x, const double* y, const double* z,
   // larger bodies: device-wide kernels (they skip the beads of small bodies)
   if (!c.big_bodies.empty()) {
     time_begin(c, "keys");
-    k_body_scale<<<blocks(3 * c.m), kThreads, 0, s>>>(c.m, lo, hi, c.body_scale);
+    k_body_scale<<<blocks(3 * c.m), kThreads, 0, s>>>(c.m, lo, hi, c.body_q);
     time_end(c, "keys");
     time_begin(c, "keys");
-    k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.off, c.N, lo, hi, c.body_scale, c.key);
+    k_keys<<<blocks(c.N), kThreads, 0, s>>>(x, y, z, c.bead_body, c.off, c.N, lo, hi, c.body_q, c.key);
     time_end(c, "keys");
     ZQ_CUDA_TRY(cudaGetLastError());
     st = launch_sort(c);

@@ -283,6 +283,54 @@ def test_large_body_radix_sort_path():
     check_apply(ctx, bt, np.float32)
 
 
+def _boundary_body(rng, n, lo, size):
+    """n beads of a body with bounding box [lo, lo + size]^3 (corners
+    included), most of them on, or one ulp either side of, the boundaries
+    of the 2^21 quantisation cells of each axis (the beads whose keys the
+    tree kernels decide by the exact formula), the rest uniform."""
+    hi = lo + size
+    w = (hi - lo) / 2.0 ** 21
+    cells = rng.integers(0, 2 ** 21, (n, 3))
+    P = lo + cells * w
+    step = rng.integers(-1, 2, (n, 3))
+    P = np.where(step > 0, np.nextafter(P, np.inf), np.where(step < 0, np.nextafter(P, -np.inf), P))
+    uni = rng.random(n) < 0.25
+    P[uni] = rng.uniform(lo, hi, (int(uni.sum()), 3))
+    P = np.clip(P, lo, hi)
+    P[0] = lo
+    P[1] = hi
+    return P
+
+
+def test_keys_at_cell_boundaries_and_far_bodies():
+    """The tree kernels quantise each coordinate with one fused multiply-add
+    and fall back to the exact FP64 formula within a bound of a cell
+    boundary (a bound that grows with |lo| / (hi - lo)).  Beads on and one
+    ulp beside cell boundaries, bodies far from the origin (up to 1e9 times
+    their size, where every bead takes the exact formula), a body of size
+    1e-6, and a body above the per-block sort limit (the device-wide key
+    pass): every tree is bit-exact with the oracle's."""
+    dev = _dev()
+    zq = _zq()
+    rng = np.random.default_rng(2024)
+    pts = [
+        _boundary_body(rng, 700, 0.0, 1.0),
+        _boundary_body(rng, 900, -3.7, 37.0),
+        _boundary_body(rng, 600, 1e6, 1.0),
+        _boundary_body(rng, 600, -2.5e7, 3.0),
+        _boundary_body(rng, 500, 1e9, 1.0),
+        _boundary_body(rng, 400, 3.0, 1e-6),
+        _boundary_body(rng, 1500, 12.0, 0.75),
+        _boundary_body(rng, 9000, -40.0, 80.0),
+    ]
+    bt = _batch_from_points(pts)
+    x, y, z = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (bt.x, bt.y, bt.z))
+    ctx = zq.Context(0)
+    ctx.build_tree_batched(bt.off, x, y, z, 6)
+    check_tree(ctx, bt, oracle_bodies(bt))
+    ctx.close()
+
+
 def _batch_from_points(bodies_pts):
     off = np.zeros(len(bodies_pts) + 1, np.int64)
     off[1:] = np.cumsum([p.shape[0] for p in bodies_pts])
