@@ -30,8 +30,8 @@ void free_all(Ctx& c) {
                 c.key_tmp, c.perm_tmp, c.sort_hist, c.lcp, c.cl, c.cr, c.first, c.cnt, c.height,
                 c.roff, c.scan_tmp, c.counters, c.sid, c.slot_of, c.sc,
                 c.sheight, c.bstart, c.bhist, c.st64, c.rec64, c.rec32, c.x64, c.x32, c.x64b, c.x32b, c.stage, c.ord,
-                c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg_flag, c.seg, c.seg_r, c.topv,
-                c.top_off, c.nseg, c.srw, c.xblk};
+                c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw, c.seg, c.seg_r, c.topv,
+                c.top_cnt, c.nseg, c.srw, c.xblk};
   for (void* p : ps)
     if (p) cudaFree(p);
   Ctx fresh;
@@ -112,11 +112,10 @@ zq_status ensure_capacity(Ctx& c, int64_t N, int64_t m, int64_t hist_words) {
     ZQ_TRY(grow(&c.proff, nodes));
     ZQ_TRY(grow(&c.ph, nodes));
     ZQ_TRY(grow(&c.prw, nodes + 1));
-    ZQ_TRY(grow(&c.seg_flag, nodes));
     ZQ_TRY(grow(&c.seg, nodes));
     ZQ_TRY(grow(&c.seg_r, nodes));
     ZQ_TRY(grow(&c.topv, nodes));
-    ZQ_TRY(grow(&c.top_off, m + 1));
+    ZQ_TRY(grow(&c.top_cnt, m));
     ZQ_TRY(grow(&c.nseg, 2));
     ZQ_TRY(grow(&c.srw, nodes));
     ZQ_CUDA_TRY(cudaMemsetAsync(c.counters, 0, 4 * sizeof(int32_t), c.stream));

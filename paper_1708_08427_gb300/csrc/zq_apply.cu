@@ -49,8 +49,9 @@ struct SweepArgs {
   const int32_t* seg_r;    // residue offset of each segment's first node
   const int32_t* nseg;     // device count of segments
   int64_t R;               // residues
-  const int32_t* topv;     // top nodes by body
-  const int32_t* top_off;  // [m + 1]
+  const int32_t* topv;     // top nodes of body j: [off[j] - j, off[j] - j + top_cnt[j])
+  const int64_t* off;      // [m + 1] body bead offsets
+  const int32_t* top_cnt;  // [m]
   const T* rec;
   T* xs;                   // Info-/Velocity-sets of segment roots and top nodes, by position
   const T* in;             // up: bead planes; down: residues
@@ -294,7 +295,7 @@ template <typename T, bool ROT>
 __global__ void __launch_bounds__(kTopThreads) k_up_top(SweepArgs<T> a) {
   __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
-  const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
+  const int32_t t0 = (int32_t)(a.off[j] - j), n = a.top_cnt[j];
   if (n <= kWarpTop) return;  // none, or few: k_up_top_warp
   const int32_t* list = a.topv + t0;
   const uint8_t* ph = a.ph;
@@ -329,7 +330,7 @@ struct TopPair {
 template <typename T>
 __device__ __forceinline__ bool warp_top_setup(const SweepArgs<T>& a, int32_t j, TopPair<T>& tp, bool down) {
   const int lane = threadIdx.x & 31;
-  const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
+  const int32_t t0 = (int32_t)(a.off[j] - j), n = a.top_cnt[j];
   if (n == 0 || n > kWarpTop) return false;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -411,7 +412,7 @@ template <typename T, bool ROT>
 __global__ void __launch_bounds__(kTopThreads) k_down_top(SweepArgs<T> a) {
   __shared__ HeightSort S;
   const int32_t j = blockIdx.x;
-  const int32_t t0 = a.top_off[j], n = a.top_off[j + 1] - t0;
+  const int32_t t0 = (int32_t)(a.off[j] - j), n = a.top_cnt[j];
   if (n <= kWarpTop) return;  // none, or few: k_down_top_warp
   const int32_t* list = a.topv + t0;
   const uint8_t* ph = a.ph;
@@ -515,7 +516,8 @@ struct BlockArgs {
   const int4* seg;
   const int32_t* nseg;
   const int32_t* topv;
-  const int32_t* top_off;
+  const int64_t* off;
+  const int32_t* top_cnt;
   const TC* rec;
   TC* xk;
   const TS* in;
@@ -655,7 +657,7 @@ template <typename TS, typename TC>
 __global__ void __launch_bounds__(kTopThreads) k_up_top_blk(BlockArgs<TS, TC> a) {
   __shared__ int lim[2];
   const int32_t j = blockIdx.x;
-  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  const int32_t t0 = (int32_t)(a.off[j] - j), t1 = t0 + a.top_cnt[j];
   if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
   const int32_t k = a.k, nt = t1 - t0;
   for (int h = lim[0]; h <= lim[1]; ++h) {
@@ -672,7 +674,7 @@ template <typename TS, typename TC>
 __global__ void __launch_bounds__(kTopThreads) k_down_top_blk(BlockArgs<TS, TC> a) {
   __shared__ int lim[2];
   const int32_t j = blockIdx.x;
-  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  const int32_t t0 = (int32_t)(a.off[j] - j), t1 = t0 + a.top_cnt[j];
   if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
   const int32_t k = a.k, nt = t1 - t0;
   for (int h = lim[1]; h >= lim[0]; --h) {
@@ -690,7 +692,7 @@ BlockArgs<TS, TC> make_block_args(const Ctx& c, int32_t k, const TC* rec, const 
   BlockArgs<TS, TC> a;
   a.N = c.N; a.k = k; a.perm = c.tree_order ? nullptr : c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
   a.prw = reinterpret_cast<const uint32_t*>(c.prw);
-  a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
+  a.seg = c.seg; a.nseg = c.nseg; a.topv = c.topv; a.off = c.off; a.top_cnt = c.top_cnt;
   a.rec = rec; a.xk = static_cast<TC*>(c.xblk); a.in = in; a.out = out;
   return a;
 }
@@ -978,7 +980,7 @@ __global__ void __launch_bounds__(32 * kTcWarps) k_up_top_tc(BlockArgs<TS, float
   __shared__ int lim[2];
   __shared__ TcTiles T[kTcWarps];
   const int32_t j = blockIdx.x, warp = threadIdx.x >> 5;
-  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  const int32_t t0 = (int32_t)(a.off[j] - j), t1 = t0 + a.top_cnt[j];
   if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
   for (int h = lim[0]; h <= lim[1]; ++h) {
     for (int32_t t = t0 + warp; t < t1; t += kTcWarps) {
@@ -994,7 +996,7 @@ __global__ void __launch_bounds__(32 * kTcWarps) k_down_top_tc(BlockArgs<TS, flo
   __shared__ int lim[2];
   __shared__ TcTiles T[kTcWarps];
   const int32_t j = blockIdx.x, warp = threadIdx.x >> 5;
-  const int32_t t0 = a.top_off[j], t1 = a.top_off[j + 1];
+  const int32_t t0 = (int32_t)(a.off[j] - j), t1 = t0 + a.top_cnt[j];
   if (!top_range(a.topv, a.ph, t0, t1, lim)) return;
   for (int h = lim[1]; h >= lim[0]; --h) {
     for (int32_t t = t0 + warp; t < t1; t += kTcWarps) {
@@ -1055,7 +1057,7 @@ SweepArgs<T> make_args(const Ctx& c, const T* rec, T* xs, const T* in, T* out) {
   SweepArgs<T> a;
   a.N = c.N; a.perm = c.tree_order ? nullptr : c.perm; a.pc = c.pc; a.proff = c.proff; a.ph = c.ph;
   a.prw = reinterpret_cast<const uint32_t*>(c.prw);
-  a.seg = c.seg; a.seg_r = c.seg_r; a.R = c.R; a.nseg = c.nseg; a.topv = c.topv; a.top_off = c.top_off;
+  a.seg = c.seg; a.seg_r = c.seg_r; a.R = c.R; a.nseg = c.nseg; a.topv = c.topv; a.off = c.off; a.top_cnt = c.top_cnt;
   a.rec = rec; a.xs = xs; a.in = in; a.out = out;
   a.bead_body = c.bead_body; a.root_out = nullptr; a.root_in = nullptr; a.rot = nullptr;
   a.cut = c.cut; a.seg_mode = 0;

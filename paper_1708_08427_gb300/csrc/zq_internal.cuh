@@ -142,13 +142,13 @@ struct Ctx {
   int32_t* proff = nullptr;      // [nodes] residue offset
   uint8_t* ph = nullptr;         // [nodes] height
   int32_t* prw = nullptr;        // [nodes + 1] record offset (4-word units, read as uint32)
-  int32_t* seg_flag = nullptr;   // [nodes] workspace: top-node counts and fill per body
   int32_t* seg_r = nullptr;      // [nodes] per segment: residue offset of its first node (its
                                  // residues are [seg_r, seg_r + 3 (nodes - 1)), contiguous)
   int4* seg = nullptr;           // [nodes] per segment: first position, nodes, first sorted
                                  // bead, 1 if its root is a body root (first nseg used)
-  int32_t* topv = nullptr;       // [nodes] top nodes (= positions), grouped by body
-  int32_t* top_off = nullptr;    // [m + 1] first top node of each body in topv
+  int32_t* topv = nullptr;       // [nodes] top nodes (= positions) of body j at
+                                 // [off[j] - j, off[j] - j + top_cnt[j]) (its node ids' range)
+  int32_t* top_cnt = nullptr;    // [m] top nodes per body
   int32_t* nseg = nullptr;       // [2] device counts: segments, top nodes
   int32_t* srw = nullptr;        // [nodes] record offset of each build slot (4-word units)
   // transforms, by slot

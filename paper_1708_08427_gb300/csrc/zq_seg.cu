@@ -12,17 +12,19 @@
 // sweeps then take a segment per thread block, height by height, and the
 // top nodes per body.
 //
-// Four kernels and two scans, all on the device (no host synchronisation:
+// Three kernels and a scan, all on the device (no host synchronisation:
 // the number of segments is a device value that the grid-stride kernels
 // read):
 //   classify     per node: parents list their children that are segment
 //                roots (and body roots list themselves) with the segment's
 //                node range, first bead and residue offset; top nodes are
-//                counted per body and get their per-position data here
-//                (a child segment root sits at the last position of its
-//                segment, which follows from its count alone);
-//   scan         top counts per body -> offsets;
-//   top_scatter  top nodes listed per body;
+//                listed per body (body j's list lies in its own node-id
+//                range [off[j] - j, ...), since a body has fewer top nodes
+//                than internal nodes; the order inside a list is free, the
+//                top-node sweeps order them by height) and get their
+//                per-position data here (a child segment root sits at the
+//                last position of its segment, which follows from its
+//                count alone);
 //   seg_order    one block per segment: height order, positions, and the
 //                per-position data of its nodes;
 //   scan         record sizes -> record offsets.
@@ -82,7 +84,7 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
                            const int32_t* __restrict__ first, const int32_t* __restrict__ bead_body,
                            const int32_t* __restrict__ roff, const uint8_t* __restrict__ height,
                            int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* __restrict__ seg_r,
-                           int32_t* __restrict__ top_cnt,
+                           int32_t* __restrict__ top_cnt, int32_t* __restrict__ topv,
                            int32_t* __restrict__ pos_of, int32_t* __restrict__ pnode, int2* __restrict__ pc,
                            int32_t* __restrict__ proff, uint8_t* __restrict__ ph, int32_t* __restrict__ units) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,7 +106,7 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
       right_root = b >= 0 && cnt[b] <= kSegMax;
       if (left_root) sa = segment_of(a, j, false, cnt, first, roff, &ra);
       if (right_root) sb = segment_of(b, j, false, cnt, first, roff, &rb);
-      atomicAdd(&top_cnt[j], 1);
+      topv[(int32_t)(off[j] - j) + atomicAdd(&top_cnt[j], 1)] = (int32_t)q;
       pos_of[q] = (int32_t)q;
       pnode[q] = (int32_t)q;
       pc[q] = make_int2(child_pos(a, cnt, first, bead_body), child_pos(b, cnt, first, bead_body));
@@ -116,15 +118,6 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
   warp_append(self_root, sq, rq, nseg, seg, seg_r);
   warp_append(left_root, sa, ra, nseg, seg, seg_r);
   warp_append(right_root, sb, rb, nseg, seg, seg_r);
-}
-
-__global__ void k_top_scatter(int64_t nodes, const int32_t* __restrict__ cnt, const int32_t* __restrict__ first,
-                              const int32_t* __restrict__ bead_body, const int32_t* __restrict__ top_off,
-                              int32_t* __restrict__ fill, int32_t* __restrict__ topv) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nodes || cnt[q] <= kSegMax) return;
-  const int32_t j = bead_body[first[q]];
-  topv[top_off[j] + atomicAdd(&fill[j], 1)] = (int32_t)q;
 }
 
 // One block per segment: range, height order, positions, per-position data
@@ -195,17 +188,12 @@ k_seg_order(const int32_t* __restrict__ nseg, const int4* __restrict__ seg, cons
 zq_status launch_segments(Ctx& c) {
   cudaStream_t s = c.stream;
   const int64_t n = c.nodes, m = c.m;
-  int32_t* top_cnt = c.seg_flag;  // [m], then the fill counters [m]
   ZQ_CUDA_TRY(cudaMemsetAsync(c.nseg, 0, 2 * sizeof(int32_t), s));
-  ZQ_CUDA_TRY(cudaMemsetAsync(top_cnt, 0, 2 * m * sizeof(int32_t), s));
+  ZQ_CUDA_TRY(cudaMemsetAsync(c.top_cnt, 0, m * sizeof(int32_t), s));
   time_begin(c, "segments");
   k_classify<<<blocks(n), kThreads, 0, s>>>(n, c.off, c.cl, c.cr, c.cnt, c.first, c.bead_body, c.roff,
-                                            c.height, c.nseg, c.seg, c.seg_r, top_cnt, c.pos_of, c.pnode, c.pc,
-                                            c.proff, c.ph, c.prw);
-  time_end(c, "segments");
-  ZQ_TRY_STATUS(launch_exclusive_scan(c, top_cnt, c.top_off, m, c.scan_tmp, c.top_off + m));
-  time_begin(c, "segments");
-  k_top_scatter<<<blocks(n), kThreads, 0, s>>>(n, c.cnt, c.first, c.bead_body, c.top_off, top_cnt + m, c.topv);
+                                            c.height, c.nseg, c.seg, c.seg_r, c.top_cnt, c.topv, c.pos_of,
+                                            c.pnode, c.pc, c.proff, c.ph, c.prw);
   k_seg_order<<<c.num_sms * 16, kOrderThreads, 0, s>>>(c.nseg, c.seg, c.cl, c.cr, c.roff, c.height, c.pos_of,
                                                  c.pnode, c.pc, c.proff, c.ph, c.prw);
   time_end(c, "segments");
