@@ -26,8 +26,10 @@
 //                last position of its segment, which follows from its
 //                count alone);
 //   seg_order    one block per segment: height order, positions, and the
-//                per-position data of its nodes;
-//   scan         record sizes -> record offsets.
+//                per-position data of its nodes.
+// Record offsets need no scan: at a top node or the first position of a
+// segment they have a closed form (rec_base), and inside a segment the
+// block adds its nodes' record sizes in position order.
 #include "zq_internal.cuh"
 
 namespace zq {
@@ -67,6 +69,23 @@ __device__ __forceinline__ int4 segment_of(int32_t c, int32_t j, bool whole, con
   return make_int4(f - j, k - 1, f, whole ? 1 : 0);
 }
 
+// Record offset (4-word units) of position a when the positions before a
+// are exactly the node ids before a (a top node keeps its id; a segment's
+// positions permute its own id range).  A node's record takes 3 + (its
+// internal children) units (rec_words).  A whole body j' of n beads
+// contributes 3 (n - 1) + (n - 2) units (every node but the root is an
+// internal child).  Inside body j, the splits g' < g (g = a - (off[j] - j))
+// have g - delta internal children among their 2 g children: leaf i hangs
+// from split i - 1 or split i, so the leaves 0..g-1, and leaf g when it is
+// the right child of split g - 1 (delta = 1), are children of those splits.
+// Together: 4 a - j - delta.
+__device__ __forceinline__ int32_t rec_base(int64_t a, int32_t j, const int64_t* __restrict__ off,
+                                            const int32_t* __restrict__ cr) {
+  const int64_t g = a - (off[j] - j);
+  const int delta = g > 0 && cr[a - 1] == (int32_t)(-1 - (off[j] + g));
+  return (int32_t)(4 * a - j - delta);
+}
+
 // Position of a child code as the sweeps see it: a leaf stays a leaf, a
 // top node keeps its id, a segment root is the last position of its range.
 __device__ __forceinline__ int32_t child_pos(int32_t c, const int32_t* __restrict__ cnt,
@@ -86,8 +105,10 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
                            int32_t* __restrict__ nseg, int4* __restrict__ seg, int32_t* __restrict__ seg_r,
                            int32_t* __restrict__ top_cnt, int32_t* __restrict__ topv,
                            int32_t* __restrict__ pos_of, int32_t* __restrict__ pnode, int2* __restrict__ pc,
-                           int32_t* __restrict__ proff, uint8_t* __restrict__ ph, int32_t* __restrict__ units) {
+                           int32_t* __restrict__ proff, uint8_t* __restrict__ ph, int32_t* __restrict__ prw,
+                           int32_t rec_total) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) prw[nodes] = rec_total;
   bool self_root = false, left_root = false, right_root = false;
   int32_t a = -1, b = -1;
   int4 sq = make_int4(0, 0, 0, 0), sa = sq, sb = sq;
@@ -112,7 +133,7 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
       pc[q] = make_int2(child_pos(a, cnt, first, bead_body), child_pos(b, cnt, first, bead_body));
       proff[q] = roff[q];
       ph[q] = height[q];
-      units[q] = rec_words((a >= 0) + (b >= 0)) / 4;
+      prw[q] = rec_base(q, j, off, cr);
     }
   }
   warp_append(self_root, sq, rq, nseg, seg, seg_r);
@@ -125,12 +146,15 @@ __global__ void k_classify(int64_t nodes, const int64_t* __restrict__ off, const
 constexpr int kOrderThreads = 128;
 
 __global__ void __launch_bounds__(kOrderThreads)
-k_seg_order(const int32_t* __restrict__ nseg, const int4* __restrict__ seg, const int32_t* __restrict__ cl,
-            const int32_t* __restrict__ cr,
+k_seg_order(const int32_t* __restrict__ nseg, const int4* __restrict__ seg, const int64_t* __restrict__ off,
+            const int32_t* __restrict__ bead_body, const int32_t* __restrict__ cl, const int32_t* __restrict__ cr,
             const int32_t* __restrict__ roff, const uint8_t* __restrict__ height, int32_t* __restrict__ pos_of,
             int32_t* __restrict__ pnode, int2* __restrict__ pc, int32_t* __restrict__ proff,
-            uint8_t* __restrict__ ph, int32_t* __restrict__ units) {
+            uint8_t* __restrict__ ph, int32_t* __restrict__ prw) {
+  constexpr int kPer = (kSegMax + kOrderThreads - 1) / kOrderThreads;
   __shared__ int32_t hist[kMaxHeight + 1];
+  __shared__ int32_t units[kPer * kOrderThreads];  // record sizes by local position
+  __shared__ int32_t wsum[kOrderThreads / 32];
   __shared__ int4 info;
   const int ns = *nseg;
   for (int i = blockIdx.x; i < ns; i += gridDim.x) {
@@ -177,7 +201,35 @@ k_seg_order(const int32_t* __restrict__ nseg, const int4* __restrict__ seg, cons
       pc[p] = make_int2(l >= 0 ? pos_of[l] : l, r >= 0 ? pos_of[r] : r);
       proff[p] = roff[q];
       ph[p] = height[q];
-      units[p] = rec_words((l >= 0) + (r >= 0)) / 4;
+      units[p - a] = rec_words((l >= 0) + (r >= 0)) / 4;
+    }
+    __syncthreads();
+    // record offsets: the closed form at the segment's first position, then
+    // the sizes in position order (kPer consecutive positions per thread)
+    {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const int b0 = threadIdx.x * kPer;
+      int32_t v[kPer], sum = 0;
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        v[e] = b0 + e < nn ? units[b0 + e] : 0;
+        sum += v[e];
+      }
+      int32_t inc = sum;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+      }
+      if (lane == 31) wsum[warp] = inc;
+      __syncthreads();
+      int32_t run = rec_base(a, bead_body[info.z], off, cr) + inc - sum;
+      for (int w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        if (b0 + e < nn) prw[a + b0 + e] = run;
+        run += v[e];
+      }
     }
     __syncthreads();
   }
@@ -193,11 +245,10 @@ zq_status launch_segments(Ctx& c) {
   time_begin(c, "segments");
   k_classify<<<blocks(n), kThreads, 0, s>>>(n, c.off, c.cl, c.cr, c.cnt, c.first, c.bead_body, c.roff,
                                             c.height, c.nseg, c.seg, c.seg_r, c.top_cnt, c.topv, c.pos_of,
-                                            c.pnode, c.pc, c.proff, c.ph, c.prw);
-  k_seg_order<<<c.num_sms * 16, kOrderThreads, 0, s>>>(c.nseg, c.seg, c.cl, c.cr, c.roff, c.height, c.pos_of,
-                                                 c.pnode, c.pc, c.proff, c.ph, c.prw);
+                                            c.pnode, c.pc, c.proff, c.ph, c.prw, (int32_t)(4 * n - m));
+  k_seg_order<<<c.num_sms * 16, kOrderThreads, 0, s>>>(c.nseg, c.seg, c.off, c.bead_body, c.cl, c.cr, c.roff,
+                                                       c.height, c.pos_of, c.pnode, c.pc, c.proff, c.ph, c.prw);
   time_end(c, "segments");
-  ZQ_TRY_STATUS(launch_exclusive_scan(c, c.prw, c.prw, n, c.scan_tmp, c.prw + n));
   ZQ_CUDA_TRY(cudaGetLastError());
   return ZQ_OK;
 }
