@@ -343,32 +343,26 @@ k_bucket_scatter(const uint8_t* __restrict__ height, const int32_t* __restrict__
 }
 
 
-// Per-slot data that depends on the tree and the slots only (it runs while
-// the segment schedule is still being made on its side stream).  Each slot
-// gets its children with their bead counts, and a leaf child as the index
-// of its bead's coordinates: the build then reads a child's state, its
-// count-table entries and a leaf's coordinates in one round of loads.
+// Per-slot data, once the build's slots and the segment schedule are both
+// made.  Each slot gets its children with their bead counts, and a leaf
+// child as the index of its bead's coordinates (the build then reads a
+// child's state, its count-table entries and a leaf's coordinates in one
+// round of loads), its height, and its node's record offset (position
+// order, from the segment schedule).
 __global__ void k_slot_data(int64_t nodes, const int32_t* __restrict__ sid,
                             const int32_t* __restrict__ slot_of, const int32_t* __restrict__ cl,
                             const int32_t* __restrict__ cr, const int32_t* __restrict__ perm,
                             const int32_t* __restrict__ cnt, const uint8_t* __restrict__ height,
-                            int4* __restrict__ sc, uint8_t* __restrict__ sheight) {
+                            const int32_t* __restrict__ pos_of, const int32_t* __restrict__ prw,
+                            int4* __restrict__ sc, uint8_t* __restrict__ sheight, int32_t* __restrict__ srw) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nodes) return;
   const int32_t q = sid[s];
   const int32_t a = cl[q], b = cr[q];
+  srw[s] = prw[pos_of[q]];
   sc[s] = make_int4(a >= 0 ? slot_of[a] : -1 - perm[leaf_pos(a)], b >= 0 ? slot_of[b] : -1 - perm[leaf_pos(b)],
                     a >= 0 ? cnt[a] : 1, b >= 0 ? cnt[b] : 1);
   sheight[s] = height[q];
-}
-
-// Record offset of each slot's node (position order, from the segment
-// schedule): the one part of the slot data that waits for it.
-__global__ void k_slot_records(int64_t nodes, const int32_t* __restrict__ sid, const int32_t* __restrict__ pos_of,
-                               const int32_t* __restrict__ prw, int32_t* __restrict__ srw) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nodes) return;
-  srw[s] = prw[pos_of[sid[s]]];
 }
 
 
@@ -472,13 +466,10 @@ zq_status launch_schedules(Ctx& c) {
   k_bucket_scatter<<<(unsigned)nblk, kThreads, 0, s>>>(c.height, c.cl, c.cr, c.nodes, c.cut, nb, hist, nblk,
                                                       c.sid, c.slot_of, c.bstart);
   time_end(c, "schedule");
-  time_begin(c, "schedule");
-  k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.perm, c.cnt,
-                                                   c.height, c.sc, c.sheight);
-  time_end(c, "schedule");
   ZQ_CUDA_TRY(cudaStreamWaitEvent(s, c.join_ev[1], 0));  // the segment schedule (positions, prw)
   time_begin(c, "schedule");
-  k_slot_records<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.pos_of, c.prw, c.srw);
+  k_slot_data<<<blocks(c.nodes), kThreads, 0, s>>>(c.nodes, c.sid, c.slot_of, c.cl, c.cr, c.perm, c.cnt,
+                                                   c.height, c.pos_of, c.prw, c.sc, c.sheight, c.srw);
   time_end(c, "schedule");
   ZQ_CUDA_TRY(cudaGetLastError());
   c.have_sched = true;
