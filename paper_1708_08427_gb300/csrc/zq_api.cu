@@ -474,12 +474,18 @@ zq_status zq_apply_rotated(zq_ctx* ctx, zq_prec prec, const double* R, const voi
 // 0 = the sweeps gather v and scatter Q~^T w through perm themselves;
 // 1 = v is gathered into the tree's order on a side stream next to the
 // transform build, so the upward sweep reads contiguous planes;
-// 2 = as 1, and the downward sweep also writes in tree order, scattered by a
-// separate pass after it.
+// 2 = as 1, and the downward sweep also writes in tree order, brought back to
+// the caller's order by a separate gather after it (through the inverse
+// permutation that the first gather writes).
 constexpr int kPipeOrder = 2;
 
-static int64_t pipe_order_bytes(int64_t N, size_t es) {
+// scratch: v in tree order, Q~^T w in tree order (mode 2), inverse permutation
+static int64_t pipe_order_planes(int64_t N, size_t es) {
   return (kPipeOrder == 2 ? 2 : 1) * 3 * N * (int64_t)es;
+}
+
+static int64_t pipe_order_bytes(int64_t N, size_t es) {
+  return pipe_order_planes(N, es) + N * (int64_t)sizeof(int32_t);
 }
 
 static bool pipe_reorders(const Ctx& c, const void* v, const void* w) {
@@ -577,13 +583,14 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
   // (it needs the tree's perm and, from host buffers, the copied v)
   char* vt = reorder ? static_cast<char*>(c.ord) : nullptr;
   char* qtt = reorder && kPipeOrder == 2 ? vt + 3 * N * es : nullptr;
+  int32_t* iperm = reorder ? reinterpret_cast<int32_t*>(vt + pipe_order_planes(N, es)) : nullptr;
   if (reorder) {
     ZQ_CUDA_TRY(cudaEventRecord(c.fork_ev, c.stream));
     ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[2], c.fork_ev, 0));
     if (host) ZQ_CUDA_TRY(cudaStreamWaitEvent(c.side[2], c.join_ev[3], 0));
     cudaStream_t main = c.stream;
     c.stream = c.side[2];
-    const zq_status st = zq::launch_to_tree(c, prec, dv, vt);
+    const zq_status st = zq::launch_to_tree(c, prec, dv, vt, iperm);
     c.stream = main;
     ZQ_TRY(st);
     ZQ_CUDA_TRY(cudaEventRecord(c.join_ev[2], c.side[2]));
@@ -626,7 +633,11 @@ static zq_status pipeline_body(zq_ctx* ctx, zq_prec prec, int64_t m, const int64
     c.tree_order = saved || qtt != nullptr;
     zq_status st = zq::launch_apply_QT(c, prec, dw, qtt ? qtt : dqtw, 3 * N);
     c.tree_order = saved;
-    if (st == ZQ_OK && qtt) st = zq::launch_from_tree(c, prec, qtt, dqtw);
+    if (st == ZQ_OK && qtt) {
+      // the inverse permutation comes from the gather into tree order
+      ZQ_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.join_ev[2], 0));
+      st = zq::launch_from_tree(c, prec, qtt, dqtw, iperm);
+    }
     return st;
   };
   // only the records of the precision the sweeps use

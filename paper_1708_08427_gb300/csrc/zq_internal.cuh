@@ -461,9 +461,10 @@ bool fused_step_possible(const Ctx& c);
 zq_status launch_fused_step(Ctx& c, zq_prec prec, const double* x, const double* y, const double* z,
                             const void* v, void* qv, const void* w, void* qtw);
 // zq_order.cu: bead planes (3 x N) to and from the tree's sorted-position
-// order (entry s = bead perm[s]), on c.stream
-zq_status launch_to_tree(Ctx& c, zq_prec prec, const void* v, void* vt);
-zq_status launch_from_tree(Ctx& c, zq_prec prec, const void* ut, void* u);
+// order (entry s = bead perm[s]), on c.stream; launch_to_tree also writes
+// the inverse permutation iperm[N], which launch_from_tree reads
+zq_status launch_to_tree(Ctx& c, zq_prec prec, const void* v, void* vt, int32_t* iperm);
+zq_status launch_from_tree(Ctx& c, zq_prec prec, const void* ut, void* u, const int32_t* iperm);
 // zq_apply.cu
 // root_out / root_in (6 m values, may be null): the root Info-set Q_Z v of
 // every body / the root Velocity-set fed to Q~^T (null: zero).  rot (9 m
