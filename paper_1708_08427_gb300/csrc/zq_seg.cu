@@ -12,7 +12,7 @@
 // sweeps then take a segment per thread block, height by height, and the
 // top nodes per body.
 //
-// Three kernels and a scan, all on the device (no host synchronisation:
+// Two kernels, both on the device (no host synchronisation:
 // the number of segments is a device value that the grid-stride kernels
 // read):
 //   classify     per node: parents list their children that are segment
