@@ -258,9 +258,11 @@ zq_status zq_apply_QT_block(zq_ctx *ctx, zq_prec prec, int64_t k, const void *W,
  * With both products and the vectors in the caller's order (the default
  * of zq_set_vector_order), the step moves the bead planes into the tree's
  * order around its sweeps: v is gathered through perm next to the
- * transform build and Q~^T w is scattered back after its sweep, through
- * two 3N-value planes the context owns (allocated on first use and when N
- * or the precision grows).  The results are the same numbers.
+ * transform build (which also records the inverse permutation) and Q~^T w
+ * is gathered back into the caller's order after its sweep, through two
+ * 3N-value planes and N int32 indices the context owns (allocated on first
+ * use and when N or the precision grows).  The results are the same
+ * numbers.
  * Only the transform copy of the requested precision is refreshed, so a
  * later zq_apply_Q / zq_apply_QT must use the same precision (else
  * ZQ_ESTATE).  Asynchronous; the results are ready after zq_sync.  When m,
